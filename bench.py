@@ -1,0 +1,294 @@
+"""Benchmark of the coupled multiphase LB step (MLUPS and HBM roofline).
+
+Default workload: the 3-D Rayleigh-Taylor case, D3Q27 cumulant flow + phase
+field, FP32 storage, 128 x 128 x 512 cells (8.4M), periodic in x and y,
+half-way bounce-back walls in z, At 0.5, sqrt(g L) = 0.04, Re 1024, W 5,
+M 0.02, with seeded velocity noise.  A step is one full coupled update of
+every cell; its populations (3.6 GB) exceed L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank advances its own replica of the workload (the
+update has no exchange between replicas); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "rt3d": dict(
+        desc="3-D Rayleigh-Taylor, D3Q27 cumulant flow + D3Q27 phase field, 128x128x512, periodic x,y, "
+             "walls z, At 0.5, sqrt(gL)=0.04, Re 1024, W 5, M 0.02",
+        D=3, dims=(128, 128, 512), periodic=(1, 1, 0),
+        phys=dict(atwood=0.5, nu_ratio=1.0, Re=1024.0, g_accel=1.25e-5, L_ref=128.0, mobility=0.02,
+                  width=5.0),
+        case="rt", args=[256.0, 12.8, 1e-4], seed=1,
+        cpu_sample=(128, 128, 16, 2)),
+    "splash3d": dict(
+        desc="3-D droplet impact on a thin sheet, D3Q27, 384x384x192, D 64, sheet 0.2D, U0 0.05, "
+             "rho ratio 1000, nu ratio 15, We 8000, Re 1000, W 4, M 0.02",
+        D=3, dims=(384, 384, 192), periodic=(1, 1, 0),
+        phys=dict(rho_ratio=1000.0, nu_ratio=15.0, We=8000.0, Re=1000.0, U0=0.05, L_ref=64.0,
+                  mobility=0.02, width=4.0),
+        case="drop_sheet", args=[64.0, 12.8, 0.05, 1e-4], seed=3,
+        cpu_sample=(96, 96, 48, 2)),
+    "rt2d": dict(
+        desc="2-D Rayleigh-Taylor, D2Q9, 64x256, periodic x, walls y, At 0.5, sqrt(gL)=0.04, Re 256, W 5, M 0.02",
+        D=2, dims=(64, 256, 1), periodic=(1, 0, 1),
+        phys=dict(atwood=0.5, nu_ratio=1.0, Re=256.0, g_accel=2.5e-5, L_ref=64.0, mobility=0.02, width=5.0),
+        case="rt", args=[128.0, 6.4, 1e-4], seed=1,
+        cpu_sample=(64, 256, 1, 50)),
+}
+
+BYTES_PER_CELL = {3: 2 * (27 + 27) * 4, 2: 2 * (9 + 9) * 4}  # populations read once + written once, FP32
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            j = json.load(fh)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(wl, threads=None):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of
+    the workload: a sub-box with the workload's parameters for a few steps."""
+    import oracle as O
+    nx, ny, nz, steps = wl["cpu_sample"]
+    if threads:
+        O.set_threads(threads)
+    cores = O.get_threads()
+    D = wl["D"]
+    args = list(wl["args"])
+    if wl["case"] == "rt":
+        args[0] = (nz if D == 3 else ny) / 2.0
+    o = O.Oracle(D, (nx, ny, nz), wl["periodic"], **wl["phys"])
+    o.init(wl["case"], args, seed=wl["seed"])
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    cells = nx * ny * nz
+    return {"value": cells * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{nx}x{ny}x{nz} sub-box of the workload, {steps} steps, FP64, {dt:.2f} s"}
+
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    per_step = []
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(wl)
+        if k >= args.warmup:
+            per_step.append(cb)
+    vals = [c["value"] for c in per_step]
+    value = statistics.median(vals)
+    nx, ny, nz, st = wl["cpu_sample"]
+    line = {"impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": nx * ny * nz / value / 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "grid": list(wl["dims"])},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": per_step[0]["cores"], "kind": "oracle",
+                             "sample": per_step[0]["sample"] + " per step of this run"},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rt3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--kernel", type=int, default=0, help="0 fused (default), 1 reference pair")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("no CUDA device: the benchmark measures the GPU path only")
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    from paper_2101_06769_gb300 import Domain
+
+    stream = torch.cuda.Stream()
+    D = wl["D"]
+    dom = Domain(D, wl["dims"], wl["periodic"], stream=stream.cuda_stream, **wl["phys"])
+    dom.set_kernel(args.kernel)
+    dom.init(wl["case"], wl["args"], seed=wl["seed"] + rank)
+    cells = dom.N
+    dom.step(args.warmup)
+    dom.sync()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    # timed region: K steps, each bracketed by events on the library's stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    time.sleep(0.3)
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        dom.step(1)
+        ev[k][1].record(stream)
+    t_end.record(stream)
+    stream.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    if pg is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    mlups = ws * cells * args.steps / (total_ms * 1e-3) / 1e6
+    launches_per_step = 2 if (args.kernel == 1) else 1
+
+    # roofline of the step kernel: algorithmic bytes per launch / event time
+    peak, peak_kind = load_peaks()
+    kern_ms = statistics.mean(step_ms)
+    bytes_launch = BYTES_PER_CELL[D] * cells
+    achieved = bytes_launch / (kern_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_kind": peak_kind, "traffic": None,
+            "kernel": "step_fused" if args.kernel == 0 else "step_simple + phi_pass",
+            "bytes_per_cell": BYTES_PER_CELL[D]}
+
+    # end to end through the public API with host buffers: per step upload the
+    # state from pinned host memory, advance one step, read the observables back
+    nbytes = dom.state_bytes()
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    dom.download(host.data_ptr(), nbytes)
+    dom.sync()
+    e2e_steps = max(1, args.e2e_steps)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dom.upload(host.data_ptr(), nbytes)
+        dom.step(1)
+        dom.observables()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if pg is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    obs_bytes = 96 + 8 * 2 * (wl["dims"][D - 1])
+    e2e = {"value": ws * cells * e2e_steps / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": obs_bytes}
+
+    ob = dom.observables()
+    line = {"metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "grid": list(wl["dims"]), "cells": cells,
+                       "storage": "fp32", "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"replicas{ws}"},
+            "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "health": ob.health, "mass_drift_rel": ob.mass_drift_rel}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    if pg is not None:
+        pg.barrier()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dom.close()
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * lbmp.h -- C ABI of the GB300 (sm_103a) multiphase lattice Boltzmann step.
+ *
+ * The library advances the coupled update of Hosseini, Safari & Thevenin,
+ * "Lattice Boltzmann solver for multi-phase flows: application to high Weber
+ * and Reynolds numbers" (arXiv 2101.06769):
+ *   - the conservative Allen-Cahn phase-field populations g (Sec. 2.2:
+ *     second-order equilibrium, sharpening source, BGK relaxation with
+ *     tau_phi = M/cs2, phi = sum g, isotropic finite differences);
+ *   - the pressure-based hydrodynamic populations f' (Sec. 2.3: modified
+ *     distribution, source Xi with pressure, surface-tension and body forces,
+ *     pre-conditioning, collision in cumulant space with the shear rate on
+ *     the second-order cumulants and unit rates elsewhere), with the density
+ *     interpolated linearly from phi (Sec. 2.3) and the viscosity
+ *     interpolated from phi (not stated in the paper: linear kinematic by
+ *     default, linear dynamic with LBMP_FLAG_DYNAMIC_VISC).
+ * Every step of the update runs in hand-written CUDA kernels; there is no CPU
+ * fallback.  All entry points return LBMP_OK (0) or a negative status and
+ * never throw; lbmp_last_error() describes the last failure of the calling
+ * thread.
+ *
+ * Exchange format shared with external code (get/set state):
+ *   direction a = (cx+1) + 3*(cy+1) + 9*(cz+1) with c in {-1,0,1}^D
+ *   (D2Q9: cz = 0, Q = 9; D3Q27: Q = 27), opposite(a) = Q-1-a;
+ *   arrays [a][z][y][x] with x fastest; FP64; the state is the post-streaming
+ *   population set f'(x,t), g(x,t) of Sec. 2.2/2.3.
+ *
+ * Geometry: horizontal axes (x, and y in 3-D) are periodic; the vertical
+ * axis (y in 2-D, z in 3-D) is periodic or closed by half-way bounce-back
+ * no-slip walls (Sec. 3.2).  Gravity acts along -vertical.
+ */
+#ifndef LBMP_H
+#define LBMP_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define LBMP_API __attribute__((visibility("default")))
+#else
+#define LBMP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { LBMP_D2Q9 = 0, LBMP_D3Q27 = 1 } lbmp_lattice;
+
+/* population storage: FP32, or FP16/BF16 scaled deviations from a reference
+ * state decoded to FP32 in registers (arithmetic is FP32 in every form) */
+typedef enum { LBMP_FP32 = 0, LBMP_FP16_SHIFTED = 1, LBMP_BF16_SHIFTED = 2 } lbmp_storage;
+
+enum {
+    LBMP_OK = 0,
+    LBMP_ERR_INVALID_ARG = -1,
+    LBMP_ERR_NOMEM = -2,
+    LBMP_ERR_CUDA = -3,
+    LBMP_ERR_TIMEOUT = -4,
+    LBMP_ERR_UNSTABLE = -5,
+    LBMP_ERR_UNSUPPORTED = -6
+};
+
+/* initial conditions of lbmp_init (tanh profiles phi = (1 + tanh(2d/W))/2
+ * with d the signed distance into the heavy fluid; u = 0 unless stated;
+ * f' = f'_eq(p_h, rho, u), g = g_eq(phi, u)).  "noise" adds a seeded uniform
+ * velocity perturbation of amplitude noise * U_ref * phi per component, drawn
+ * from splitmix64(seed, 3*cell + component). */
+enum {
+    LBMP_CASE_RT = 0,          /* args: h0, amplitude, noise. Heavy above
+                                  h = h0 + amp [cos(2 pi x/nx) (+ cos(2 pi y/ny) in 3-D)] */
+    LBMP_CASE_DROP_STATIC = 1, /* args: R, p_init, noise. Heavy drop of radius R at the
+                                  cell (nx/2, ny/2, nz/2); p_init != 0 starts
+                                  p_h = (D-1) sigma/R phi */
+    LBMP_CASE_FLAT = 2,        /* args: x0, x1, noise. Heavy slab x0 < x < x1 */
+    LBMP_CASE_POISEUILLE = 3,  /* args: noise. Heavy lower half of the vertical axis */
+    LBMP_CASE_DROP_SHEET = 4,  /* args: D, sheet_h, U0, noise. Heavy sheet below vertical
+                                  coordinate sheet_h and a drop of diameter D centred
+                                  sheet_h + D/2 + 2W above the bottom, falling at U0 */
+    LBMP_CASE_SHEAR_WAVE = 5,  /* args: U, noise. phi = 1, u_x = U sin(2 pi y/ny) */
+    LBMP_CASE_UNIFORM = 6      /* args: phi0, p0, ux, uy, uz */
+};
+
+/* switches for readings where the paper admits an alternative */
+enum {
+    LBMP_FLAG_WE_LIGHT = 1u << 0,     /* sigma = rho_l L U^2/We (the paper's printed We) */
+    LBMP_FLAG_DYNAMIC_VISC = 1u << 1, /* eta(phi) linear, nu = eta/rho */
+    LBMP_FLAG_UNIFORM_FORCE = 1u << 2 /* body force = force_x along x instead of gravity */
+};
+
+typedef struct {
+    int nx, ny, nz;  /* nz = 1 for D2Q9 */
+    int periodic[3]; /* 1 = periodic; 0 = half-way bounce-back walls (vertical axis only) */
+} lbmp_grid;
+
+/* problem statement (lattice units, heavy density rho_h = 1, Sec. 3) */
+typedef struct {
+    double rho_ratio, nu_ratio; /* rho_h/rho_l, nu_l/nu_h                                  */
+    double We, Re, atwood;      /* atwood > 0 overrides rho_ratio = (1+At)/(1-At)           */
+    double mobility, width;     /* M, W                                                     */
+    double g_accel, U0, L_ref;  /* gravity, impact speed, reference length (L_x or D)       */
+    double sigma, nu_h;         /* explicit overrides: sigma >= 0, nu_h > 0; else derived:
+                                   nu_h = U L/Re with U = U0 or sqrt(g L);
+                                   sigma = rho_h L U^2/We (0 when We = 0)                   */
+    double force_x;             /* with LBMP_FLAG_UNIFORM_FORCE                             */
+    int storage;                /* lbmp_storage                                             */
+    unsigned flags;             /* LBMP_FLAG_*                                              */
+} lbmp_params;
+
+/* derived lattice parameters: beta = 12 sigma/W, kappa = 3 sigma W/2 (Sec. 2.1),
+ * tau_phi = M/cs2 + 1/2, lambda_phi = 1 - 1/(2 tau_phi) (Sec. 2.2) */
+typedef struct {
+    double rho_h, rho_l, nu_h, nu_l, sigma, beta, kappa;
+    double M, W, tau_phi, lambda_phi, g_accel, U_ref, force_x;
+} lbmp_derived;
+
+/* FP64 observables (reductions on the device):
+ *   mass = sum phi; mass_drift_rel = (mass - mass at lbmp_init/set_state)/that;
+ *   kinetic_energy = sum rho |u|^2 / 2; max_u = max |u|;
+ *   p_in/p_out = mean p_h over the 3^D block at the probe cell (drop centre) and
+ *   at the origin, laplace_dp = p_in - p_out (Sec. 3.1);
+ *   tip_spike = lowest phi = 1/2 crossing on the vertical column through
+ *   (nx/2, ny/2), tip_bubble = highest crossing on the column through the
+ *   origin (Sec. 3.2/3.3; -1 when there is none); health != 0 when a
+ *   non-finite value was met. */
+typedef struct {
+    double mass, mass_drift_rel, kinetic_energy, max_u, p_in, p_out, laplace_dp;
+    double tip_spike, tip_bubble;
+    long step;
+    int health;
+} lbmp_obs;
+
+typedef struct lbmp_handle lbmp_handle;
+
+/* Create a domain.  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream); every later call of the handle is ordered on it.  Allocates the
+ * device state (two FP32/FP16/BF16 population sets for f' and g, and a phi
+ * field); no device work.  Errors: INVALID_ARG (bad grid or parameters),
+ * NOMEM, CUDA.  The caller owns *out and releases it with lbmp_destroy. */
+LBMP_API int lbmp_create(const lbmp_grid *grid, lbmp_lattice lattice, const lbmp_params *params,
+                void *cuda_stream, lbmp_handle **out);
+LBMP_API int lbmp_destroy(lbmp_handle *h);
+LBMP_API const char *lbmp_last_error(void);
+LBMP_API int lbmp_get_derived(const lbmp_handle *h, lbmp_derived *out);
+
+/* Set the initial state of one of the LBMP_CASE_* problems on the device
+ * (Sec. 3 set-ups; reading A18).  Asynchronous. */
+LBMP_API int lbmp_init(lbmp_handle *h, int case_id, const double *case_args, int nargs,
+              unsigned long long seed);
+
+/* Advance n time steps (Sec. 2.2/2.3), asynchronously on the handle's stream. */
+LBMP_API int lbmp_step(lbmp_handle *h, long n);
+
+/* Wait for the handle's stream; reports a device-side error status. */
+LBMP_API int lbmp_sync(lbmp_handle *h);
+
+/* FP64 observables (synchronises). */
+LBMP_API int lbmp_observables(lbmp_handle *h, lbmp_obs *out);
+
+/* Host copies of the state in the exchange format (synchronise).  f and g
+ * hold Q*N doubles, phi N doubles; any of them may be NULL in get_state. */
+LBMP_API int lbmp_get_state(lbmp_handle *h, double *f, double *g, double *phi);
+LBMP_API int lbmp_set_state(lbmp_handle *h, const double *f, const double *g);
+
+/* Raw transfers of the device state in its native storage layout (an opaque
+ * byte image, valid only for a handle of the same grid, lattice and
+ * storage).  Asynchronous on the handle's stream; host memory should be
+ * pinned.  bytes must equal lbmp_state_bytes(h). */
+LBMP_API size_t lbmp_state_bytes(const lbmp_handle *h);
+LBMP_API int lbmp_upload(lbmp_handle *h, const void *host, size_t bytes);
+LBMP_API int lbmp_download(lbmp_handle *h, void *host, size_t bytes);
+
+/* Kernel selection (for A/B tests and measurement): 0 = default fused
+ * kernel, 1 = simple reference pair (phi pass + one thread per cell). */
+enum { LBMP_OPT_KERNEL = 0 };
+LBMP_API int lbmp_set_option(lbmp_handle *h, int option, long value);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,402 @@
+// lbmp_api.cu -- extern "C" entry points of the library (include/lbmp.h):
+// argument validation, the parameter closure of the paper's problem statement,
+// device allocation, state transfer and error reporting.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "lbmp_internal.h"
+
+namespace {
+
+thread_local char g_msg[512] = "";
+
+int fail(int code, const char* fmt, const char* detail = nullptr)
+{
+    if (detail)
+        snprintf(g_msg, sizeof g_msg, fmt, detail);
+    else
+        snprintf(g_msg, sizeof g_msg, "%s", fmt);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where)
+{
+    snprintf(g_msg, sizeof g_msg, "%s: %s", where, cudaGetErrorString(e));
+    return LBMP_ERR_CUDA;
+}
+
+#define LBMP_CUDA(call, where)                         \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+// Problem statement -> lattice parameters (Sec. 2.1, 2.2, 3):
+//   rho_h = 1; rho_l = 1/ratio or (1-At)/(1+At);
+//   U = U0, or sqrt(g L) for gravity-driven cases; nu_h = U L / Re;
+//   sigma = rho_h L U^2 / We (rho_l with LBMP_FLAG_WE_LIGHT);
+//   beta = 12 sigma/W, kappa = 3 sigma W/2; tau_phi = M/cs2 + 1/2,
+//   lambda_phi = 1 - 1/(2 tau_phi).
+int derive(const lbmp_params& p, lbmp_derived& d)
+{
+    memset(&d, 0, sizeof d);
+    d.rho_h = 1.0;
+    if (p.atwood > 0.0) {
+        if (!(p.atwood < 1.0)) return fail(LBMP_ERR_INVALID_ARG, "atwood must lie in (0, 1)");
+        d.rho_l = (1.0 - p.atwood) / (1.0 + p.atwood);
+    } else {
+        if (!(p.rho_ratio > 0.0)) return fail(LBMP_ERR_INVALID_ARG, "rho_ratio must be > 0");
+        d.rho_l = 1.0 / p.rho_ratio;
+    }
+    d.U_ref = (p.U0 > 0.0) ? p.U0 : sqrt(p.g_accel > 0.0 ? p.g_accel * p.L_ref : 0.0);
+    if (p.nu_h > 0.0) {
+        d.nu_h = p.nu_h;
+    } else {
+        if (!(p.Re > 0.0 && p.L_ref > 0.0 && d.U_ref > 0.0))
+            return fail(LBMP_ERR_INVALID_ARG, "viscosity: give nu_h > 0, or Re, L_ref and U0 or g_accel");
+        d.nu_h = d.U_ref * p.L_ref / p.Re;
+    }
+    if (!(p.nu_ratio > 0.0)) return fail(LBMP_ERR_INVALID_ARG, "nu_ratio must be > 0");
+    d.nu_l = d.nu_h * p.nu_ratio;
+    if (p.sigma >= 0.0)
+        d.sigma = p.sigma;
+    else if (p.We > 0.0)
+        d.sigma = ((p.flags & LBMP_FLAG_WE_LIGHT) ? d.rho_l : d.rho_h) * p.L_ref * d.U_ref * d.U_ref / p.We;
+    else
+        d.sigma = 0.0;
+    if (!(p.width > 0.0)) return fail(LBMP_ERR_INVALID_ARG, "width W must be > 0");
+    if (!(p.mobility > 0.0)) return fail(LBMP_ERR_INVALID_ARG, "mobility M must be > 0");
+    d.W = p.width;
+    d.M = p.mobility;
+    d.beta = 12.0 * d.sigma / d.W;
+    d.kappa = 1.5 * d.sigma * d.W;
+    d.tau_phi = 3.0 * d.M + 0.5;
+    d.lambda_phi = 1.0 - 0.5 / d.tau_phi;
+    d.g_accel = p.g_accel;
+    d.force_x = p.force_x;
+    if (!isfinite(d.nu_h) || !isfinite(d.nu_l) || !isfinite(d.sigma))
+        return fail(LBMP_ERR_INVALID_ARG, "non-finite derived parameter");
+    return LBMP_OK;
+}
+
+void fill_devparams(lbmp_handle* h)
+{
+    lbmp::DevParams& q = h->dp;
+    const lbmp_derived& d = h->der;
+    q.nx = h->grid.nx;
+    q.ny = h->grid.ny;
+    q.nz = h->grid.nz;
+    q.vert_periodic = h->grid.periodic[h->D - 1] ? 1 : 0;
+    q.N = h->N;
+    q.rho_l = (float)d.rho_l;
+    q.drho = (float)(d.rho_h - d.rho_l);
+    q.rho_bar = (float)(0.5 * (d.rho_h + d.rho_l));
+    q.nu_h = (float)d.nu_h;
+    q.nu_l = (float)d.nu_l;
+    q.eta_h = (float)(d.rho_h * d.nu_h);
+    q.eta_l = (float)(d.rho_l * d.nu_l);
+    q.beta2 = (float)(2.0 * d.beta);
+    q.kappa = (float)d.kappa;
+    q.inv_tau_phi = (float)(1.0 / d.tau_phi);
+    q.lam_sharp = (float)(d.lambda_phi * 4.0 / d.W);
+    q.g_accel = (float)d.g_accel;
+    q.force_x = (float)d.force_x;
+    q.flags = h->params.flags;
+}
+
+void free_handle(lbmp_handle* h)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (h->f[k]) cudaFree(h->f[k]);
+        if (h->g[k]) cudaFree(h->g[k]);
+    }
+    if (h->phi) cudaFree(h->phi);
+    if (h->red) cudaFree(h->red);
+    if (h->red_out) cudaFree(h->red_out);
+    delete h;
+}
+
+int check_handle(const lbmp_handle* h)
+{
+    if (!h) return fail(LBMP_ERR_INVALID_ARG, "null handle");
+    return LBMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbmp_last_error(void) { return g_msg; }
+
+int lbmp_create(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* params, void* cuda_stream,
+                lbmp_handle** out)
+{
+    if (!grid || !params || !out) return fail(LBMP_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (lattice != LBMP_D2Q9 && lattice != LBMP_D3Q27) return fail(LBMP_ERR_INVALID_ARG, "unknown lattice");
+    const int D = (lattice == LBMP_D3Q27) ? 3 : 2;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return fail(LBMP_ERR_INVALID_ARG, "grid sizes must be >= 1");
+    if (D == 2 && grid->nz != 1) return fail(LBMP_ERR_INVALID_ARG, "D2Q9 needs nz = 1");
+    if (D == 3 && (grid->nx < 2 || grid->ny < 2 || grid->nz < 2))
+        return fail(LBMP_ERR_INVALID_ARG, "D3Q27 needs every size >= 2");
+    if (D == 2 && (grid->nx < 2 || grid->ny < 2)) return fail(LBMP_ERR_INVALID_ARG, "D2Q9 needs nx, ny >= 2");
+    for (int k = 0; k < D - 1; ++k)
+        if (!grid->periodic[k]) return fail(LBMP_ERR_INVALID_ARG, "horizontal axes must be periodic");
+    const long long N = (long long)grid->nx * grid->ny * grid->nz;
+    if (N > (1LL << 31) - 1) return fail(LBMP_ERR_INVALID_ARG, "more than 2^31-1 cells");
+    if (params->storage != LBMP_FP32) return fail(LBMP_ERR_UNSUPPORTED, "storage form not available in this build");
+    if (params->flags & ~7u) return fail(LBMP_ERR_INVALID_ARG, "unknown flag bits");
+
+    lbmp_handle* h = new (std::nothrow) lbmp_handle();
+    if (!h) return fail(LBMP_ERR_NOMEM, "host allocation failed");
+    memset(h, 0, sizeof *h);
+    h->grid = *grid;
+    h->D = D;
+    h->Q = (D == 3) ? 27 : 9;
+    h->params = *params;
+    h->N = N;
+    h->stream = (cudaStream_t)cuda_stream;
+    int rc = derive(*params, h->der);
+    if (rc != LBMP_OK) {
+        delete h;
+        return rc;
+    }
+    const double tau_min = 3.0 * fmin(h->der.nu_h, h->der.nu_l) + 0.5;
+    if (!(tau_min > 0.5)) {
+        delete h;
+        return fail(LBMP_ERR_INVALID_ARG, "viscosities must be > 0");
+    }
+    fill_devparams(h);
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    const size_t pop = sizeof(float) * (size_t)h->Q * (size_t)N;
+    for (int k = 0; k < 2; ++k) {
+        e = cudaMalloc(&h->f[k], pop);
+        if (e == cudaSuccess) e = cudaMalloc(&h->g[k], pop);
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&h->phi, sizeof(float) * (size_t)N);
+    h->red_blocks = 1024;
+    if (e == cudaSuccess) e = cudaMalloc(&h->red, sizeof(double) * 4 * h->red_blocks);
+    const int nv = (D == 3) ? grid->nz : grid->ny;
+    if (e == cudaSuccess) e = cudaMalloc(&h->red_out, sizeof(double) * (16 + 2 * (size_t)nv));
+    if (e != cudaSuccess) {
+        free_handle(h);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? fail(LBMP_ERR_NOMEM, "device allocation failed")
+                                              : cuda_fail(e, "cudaMalloc");
+    }
+    for (int k = 0; k < 3; ++k) h->probe[k] = (k < D) ? ((&grid->nx)[k] / 2) : 0;
+    h->kernel = 0;
+    *out = h;
+    return LBMP_OK;
+}
+
+int lbmp_destroy(lbmp_handle* h)
+{
+    if (!h) return LBMP_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_handle(h);
+    return LBMP_OK;
+}
+
+int lbmp_get_derived(const lbmp_handle* h, lbmp_derived* out)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!out) return fail(LBMP_ERR_INVALID_ARG, "null output");
+    *out = h->der;
+    return LBMP_OK;
+}
+
+int lbmp_set_option(lbmp_handle* h, int option, long value)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (option != LBMP_OPT_KERNEL || value < 0 || value > 1) return fail(LBMP_ERR_INVALID_ARG, "bad option");
+    h->kernel = (int)value;
+    return LBMP_OK;
+}
+
+int lbmp_init(lbmp_handle* h, int case_id, const double* case_args, int nargs, unsigned long long seed)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    static const int need[7] = {3, 3, 3, 1, 4, 2, 5};
+    if (case_id < 0 || case_id > 6) return fail(LBMP_ERR_INVALID_ARG, "unknown case");
+    if (nargs < need[case_id] || (nargs > 0 && !case_args)) return fail(LBMP_ERR_INVALID_ARG, "too few case arguments");
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < nargs && k < 8; ++k) {
+        if (!isfinite(case_args[k])) return fail(LBMP_ERR_INVALID_ARG, "non-finite case argument");
+        a[k] = case_args[k];
+    }
+    if (case_id == LBMP_CASE_DROP_STATIC && !(a[0] > 0.0)) return fail(LBMP_ERR_INVALID_ARG, "radius must be > 0");
+    h->parity = 0;
+    h->step = 0;
+    for (int k = 0; k < 3; ++k) h->probe[k] = (k < h->D) ? ((&h->grid.nx)[k] / 2) : 0;
+    if (case_id == LBMP_CASE_DROP_SHEET) {
+        const double zc = a[1] + 0.5 * a[0] + 2.0 * h->der.W;
+        int pv = (int)floor(zc + 0.5);
+        const int nv = (&h->grid.nx)[h->D - 1];
+        h->probe[h->D - 1] = pv < 0 ? 0 : (pv >= nv ? nv - 1 : pv);
+    }
+    LBMP_CUDA(lbmp::launch_init(h, case_id, a, seed), "init kernel");
+    LBMP_CUDA(lbmp::launch_mass(h, h->red_out + 12), "reference mass");
+    return LBMP_OK;
+}
+
+int lbmp_step(lbmp_handle* h, long n)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (n < 0) return fail(LBMP_ERR_INVALID_ARG, "negative step count");
+    for (long k = 0; k < n; ++k) {
+        cudaError_t e = (h->kernel == 1 || !lbmp::fused_supported(h)) ? lbmp::launch_step_simple(h)
+                                                                        : lbmp::launch_step_fused(h);
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel");
+        h->parity ^= 1;
+        h->step += 1;
+    }
+    return LBMP_OK;
+}
+
+int lbmp_sync(lbmp_handle* h)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    LBMP_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    return LBMP_OK;
+}
+
+int lbmp_observables(lbmp_handle* h, lbmp_obs* out)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!out) return fail(LBMP_ERR_INVALID_ARG, "null output");
+    const int nv = (h->D == 3) ? h->grid.nz : h->grid.ny;
+    LBMP_CUDA(lbmp::launch_observables(h, h->red_out), "observables kernels");
+    double* host = new (std::nothrow) double[16 + 2 * (size_t)nv];
+    if (!host) return fail(LBMP_ERR_NOMEM, "host allocation failed");
+    cudaError_t e = cudaMemcpyAsync(host, h->red_out, sizeof(double) * (16 + 2 * (size_t)nv), cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        delete[] host;
+        return cuda_fail(e, "observables copy");
+    }
+    memset(out, 0, sizeof *out);
+    out->mass = host[0];
+    out->kinetic_energy = host[1];
+    out->max_u = host[2];
+    out->health = host[3] != 0.0 ? 1 : 0;
+    out->p_in = host[4];
+    out->p_out = host[5];
+    out->laplace_dp = out->p_in - out->p_out;
+    const double m0 = host[12];  // mass recorded on the device by lbmp_init / lbmp_set_state
+    out->mass_drift_rel = (m0 != 0.0) ? (out->mass - m0) / m0 : 0.0;
+    // phi = 1/2 crossings: spike = lowest on the centre column, bubble = highest on the origin column
+    const double* cs = host + 16;
+    const double* cb = host + 16 + nv;
+    out->tip_spike = -1.0;
+    for (int k = 0; k < nv; ++k)
+        if (cs[k] >= 0.5) {
+            out->tip_spike = (k == 0) ? 0.0 : k - (cs[k] - 0.5) / (cs[k] - cs[k - 1]);
+            break;
+        }
+    out->tip_bubble = -1.0;
+    for (int k = nv - 1; k >= 0; --k)
+        if (cb[k] < 0.5) {
+            out->tip_bubble = (k == nv - 1) ? (double)k : k + (0.5 - cb[k]) / (cb[k + 1] - cb[k]);
+            break;
+        }
+    out->step = h->step;
+    delete[] host;
+    return out->health ? fail(LBMP_ERR_UNSTABLE, "non-finite values in the state") : LBMP_OK;
+}
+
+int lbmp_get_state(lbmp_handle* h, double* f, double* g, double* phi)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    const size_t n = (size_t)h->Q * (size_t)h->N;
+    double *df = nullptr, *dg = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (f) e = cudaMallocAsync(&df, n * sizeof(double), h->stream);
+    if (e == cudaSuccess && g) e = cudaMallocAsync(&dg, n * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = lbmp::launch_get_state(h, df, dg);
+    if (e == cudaSuccess && f) e = cudaMemcpyAsync(f, df, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && g) e = cudaMemcpyAsync(g, dg, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (df) cudaFreeAsync(df, h->stream);
+    if (dg) cudaFreeAsync(dg, h->stream);
+    if (e == cudaSuccess && phi) {
+        e = lbmp::launch_phi_pass(h);
+        float* tmp = new (std::nothrow) float[h->N];
+        if (!tmp) return fail(LBMP_ERR_NOMEM, "host allocation failed");
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, h->phi, sizeof(float) * h->N, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess)
+            for (long long i = 0; i < h->N; ++i) phi[i] = tmp[i];
+        delete[] tmp;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "get_state");
+    return LBMP_OK;
+}
+
+int lbmp_set_state(lbmp_handle* h, const double* f, const double* g)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!f || !g) return fail(LBMP_ERR_INVALID_ARG, "null state array");
+    const size_t n = (size_t)h->Q * (size_t)h->N;
+    double *df = nullptr, *dg = nullptr;
+    cudaError_t e = cudaMallocAsync(&df, n * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dg, n * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(df, f, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dg, g, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = lbmp::launch_set_state(h, df, dg);
+    if (e == cudaSuccess) e = lbmp::launch_mass(h, h->red_out + 12);
+    if (df) cudaFreeAsync(df, h->stream);
+    if (dg) cudaFreeAsync(dg, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "set_state");
+    return LBMP_OK;
+}
+
+size_t lbmp_state_bytes(const lbmp_handle* h)
+{
+    if (!h) return 0;
+    return 2 * sizeof(float) * (size_t)h->Q * (size_t)h->N;
+}
+
+int lbmp_upload(lbmp_handle* h, const void* host, size_t bytes)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!host || bytes != lbmp_state_bytes(h)) return fail(LBMP_ERR_INVALID_ARG, "bad upload size");
+    const size_t half = bytes / 2;
+    LBMP_CUDA(cudaMemcpyAsync(h->f[h->parity], host, half, cudaMemcpyHostToDevice, h->stream), "upload f");
+    LBMP_CUDA(cudaMemcpyAsync(h->g[h->parity], (const char*)host + half, half, cudaMemcpyHostToDevice, h->stream),
+              "upload g");
+    return LBMP_OK;
+}
+
+int lbmp_download(lbmp_handle* h, void* host, size_t bytes)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!host || bytes != lbmp_state_bytes(h)) return fail(LBMP_ERR_INVALID_ARG, "bad download size");
+    const size_t half = bytes / 2;
+    LBMP_CUDA(cudaMemcpyAsync(host, h->f[h->parity], half, cudaMemcpyDeviceToHost, h->stream), "download f");
+    LBMP_CUDA(cudaMemcpyAsync((char*)host + half, h->g[h->parity], half, cudaMemcpyDeviceToHost, h->stream),
+              "download g");
+    return LBMP_OK;
+}
+
+}  // extern "C"

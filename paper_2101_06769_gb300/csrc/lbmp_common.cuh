@@ -1,0 +1,389 @@
+// lbmp_common.cuh -- lattice traits, device parameters and the per-cell
+// arithmetic of the coupled update (Hosseini, Safari & Thevenin, arXiv
+// 2101.06769, Sec. 2.2 and 2.3), shared by every step kernel of the library.
+//
+// All arithmetic is FP32.  The flow collision is written in "deviation
+// form": every quantity that enters a stored population is formed as a small
+// deviation from the rest state, so that FP32 keeps full relative precision
+// on f' (whose values are O(p_h) and O(rho cs2 u), far below the O(1) rest
+// weights).  The form is algebraically identical to the general cumulant
+// path of Sec. 2.3 because every rate other than the shear rate is one:
+//   * the post-collision cumulants of order >= 3 vanish, so the post-collision
+//     central moments are the Gaussian (Isserlis) moments of the relaxed
+//     second-order tensor kappa* = cs2 I + delta*;
+//   * the product-form equilibrium E(u) has the Gaussian moments of cs2 I, so
+//     h* - E(u) is the per-axis (Kronecker) inverse of the 13 non-zero moment
+//     differences, and E(u) - w is a telescoped product of per-axis terms.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmp {
+
+__host__ __device__ constexpr double w1d(int c) { return c == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+
+// Velocity set {-1,0,1}^D in the exchange order a = (cx+1) + 3(cy+1) + 9(cz+1)
+// with the tensorised D1Q3 Gauss-Hermite weights (cs2 = 1/3, Sec. 2.2).
+template <int D>
+struct Lat;
+
+template <>
+struct Lat<3> {
+    static constexpr int Q = 27;
+    __host__ __device__ static constexpr int cx(int a) { return a % 3 - 1; }
+    __host__ __device__ static constexpr int cy(int a) { return (a / 3) % 3 - 1; }
+    __host__ __device__ static constexpr int cz(int a) { return a / 9 - 1; }
+    __host__ __device__ static constexpr float w(int a) { return (float)(w1d(cx(a)) * w1d(cy(a)) * w1d(cz(a))); }
+    __host__ __device__ static constexpr int opp(int a) { return 26 - a; }
+};
+
+template <>
+struct Lat<2> {
+    static constexpr int Q = 9;
+    __host__ __device__ static constexpr int cx(int a) { return a % 3 - 1; }
+    __host__ __device__ static constexpr int cy(int a) { return a / 3 - 1; }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
+    __host__ __device__ static constexpr float w(int a) { return (float)(w1d(cx(a)) * w1d(cy(a))); }
+    __host__ __device__ static constexpr int opp(int a) { return 8 - a; }
+};
+
+constexpr float kCs2 = 1.0f / 3.0f;
+
+enum : unsigned {
+    kFlagWeLight = 1u << 0,
+    kFlagDynamicVisc = 1u << 1,
+    kFlagUniformForce = 1u << 2,
+};
+
+// Everything a step kernel needs, by value (fits the kernel-parameter space).
+struct DevParams {
+    int nx, ny, nz;         // nz = 1 in 2-D
+    int vert_periodic;      // vertical axis periodic (1) or walled (0)
+    long long N;            // cells
+    float rho_l, drho, rho_bar;
+    float nu_h, nu_l, eta_h, eta_l;
+    float beta2, kappa;     // 2 beta, kappa of the chemical potential
+    float inv_tau_phi;      // 1/tau_bar_phi
+    float lam_sharp;        // lambda_phi * 4 / W
+    float g_accel, force_x;
+    unsigned flags;
+};
+
+// ----------------------------------------------------------- pull helpers
+// Post-streaming population a at cell (x,y,z) lives in the buffer written by
+// the previous step at the upstream cell x - c_a (pull); across a half-way
+// bounce-back wall it is the opposite population of the cell itself.
+template <int D>
+__device__ __forceinline__ long long pull_index(const DevParams& p, int a, int x, int y, int z, long long self)
+{
+    const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
+    int xs = x - cx;
+    xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
+    if (D == 3) {
+        int ys = y - cy;
+        ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
+        int zs = z - cz;
+        if (zs < 0 || zs >= p.nz) {
+            if (!p.vert_periodic) return (long long)Lat<D>::opp(a) * p.N + self;
+            zs = zs < 0 ? zs + p.nz : zs - p.nz;
+        }
+        return (long long)a * p.N + ((long long)zs * p.ny + ys) * p.nx + xs;
+    } else {
+        int ys = y - cy;
+        if (ys < 0 || ys >= p.ny) {
+            if (!p.vert_periodic) return (long long)Lat<D>::opp(a) * p.N + self;
+            ys = ys < 0 ? ys + p.ny : ys - p.ny;
+        }
+        return (long long)a * p.N + (long long)ys * p.nx + xs;
+    }
+}
+
+// Neighbour of the phi stencil: periodic wrap, or the mirrored ghost at a
+// wall (the ghost equals the wall cell, reading A17).
+__device__ __forceinline__ int wrap_h(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+__device__ __forceinline__ int wrap_v(int v, int n, int periodic)
+{
+    if (v >= 0 && v < n) return v;
+    if (periodic) return v < 0 ? v + n : v - n;
+    return v < 0 ? 0 : n - 1;
+}
+
+// ------------------------------------------------------- cells and stencil
+__device__ __forceinline__ void cell_xyz(const DevParams& p, long long i, int& x, int& y, int& z)
+{
+    x = (int)(i % p.nx);
+    long long r = i / p.nx;
+    y = (int)(r % p.ny);
+    z = (int)(r / p.ny);
+}
+
+// neighbour index of the phi stencil
+template <int D>
+__device__ __forceinline__ long long nbr_index(const DevParams& p, int a, int x, int y, int z)
+{
+    const int xx = wrap_h(x + Lat<D>::cx(a), p.nx);
+    if (D == 3) {
+        const int yy = wrap_h(y + Lat<D>::cy(a), p.ny);
+        const int zz = wrap_v(z + Lat<D>::cz(a), p.nz, p.vert_periodic);
+        return ((long long)zz * p.ny + yy) * p.nx + xx;
+    } else {
+        const int yy = wrap_v(y + Lat<D>::cy(a), p.ny, p.vert_periodic);
+        return (long long)yy * p.nx + xx;
+    }
+}
+
+// Isotropic differences (Sec. 2.2) from the Q neighbour values nb[a] =
+// phi(x + c_a): grad_i = 3 sum w c_i phi(x+c), lap = 6 sum w (phi(x+c) - phi(x)).
+// The gradient is summed over opposite pairs so that it is exactly zero on a
+// uniform field.
+template <int D>
+__device__ __forceinline__ void stencil_from_nb(const float* nb, float grad[3], float& lap)
+{
+    constexpr int Q = Lat<D>::Q;
+    constexpr int C = Q / 2;
+    const float pc = nb[C];
+    float gx = 0.f, gy = 0.f, gz = 0.f, ls = 0.f;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        if (a == C) continue;
+        ls += Lat<D>::w(a) * (nb[a] - pc);
+    }
+#pragma unroll
+    for (int a = 0; a < C; ++a) {
+        const float d = Lat<D>::w(a) * (nb[a] - nb[Q - 1 - a]);
+        if (Lat<D>::cx(a)) gx += Lat<D>::cx(a) * d;
+        if (Lat<D>::cy(a)) gy += Lat<D>::cy(a) * d;
+        if (Lat<D>::cz(a)) gz += Lat<D>::cz(a) * d;
+    }
+    grad[0] = 3.f * gx;
+    grad[1] = 3.f * gy;
+    grad[2] = (D == 3) ? 3.f * gz : 0.f;
+    lap = 6.f * ls;
+}
+
+
+// ------------------------------------------------------ flow collision
+// Moments of the pre-collision f': P, J, and the second moments Pi_ij.
+struct FlowMoments {
+    float P, J[3];
+    float Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;
+};
+
+template <int D>
+__device__ __forceinline__ void accumulate_moments(FlowMoments& m, int a, float v)
+{
+    const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
+    m.P += v;
+    if (cx) m.J[0] += cx * v;
+    if (cy) m.J[1] += cy * v;
+    if (cz) m.J[2] += cz * v;
+    if (cx) m.Pxx += v;
+    if (cy) m.Pyy += v;
+    if (cz) m.Pzz += v;
+    if (cx * cy) m.Pxy += (cx * cy) * v;
+    if (cx * cz) m.Pxz += (cx * cz) * v;
+    if (cy * cz) m.Pyz += (cy * cz) * v;
+}
+
+__device__ __forceinline__ void zero_moments(FlowMoments& m)
+{
+    m.P = m.J[0] = m.J[1] = m.J[2] = 0.f;
+    m.Pxx = m.Pyy = m.Pzz = m.Pxy = m.Pxz = m.Pyz = 0.f;
+}
+
+// Per-cell results of the collision set-up that the output loops need.
+struct CellState {
+    float u[3];        // velocity
+    float n[3];        // interface normal
+    float rcs2;        // rho cs2
+    float ph;          // p_h = P + sum(Xi)/2
+    float V[3], uV;    // V = cs2 grad(rho) + F
+    float G[3], uG;    // G = cs2 grad(rho)
+    float uu;          // |u|^2
+    float ew[3][3];    // per-axis product-equilibrium deviation e_d(c) - w1(c), [axis][c+1]
+    float ef[3][3];    // per-axis product-equilibrium e_d(c), [axis][c+1]
+    float phi, sharp;  // phi and lambda_phi 4 phi (1-phi)/W
+};
+
+// Local closure (Sec. 2.1/2.3; readings A1, A2, A7, A12, A13, A15) and the
+// relaxed second-order deviations.  Produces the 27-entry Kronecker inverse
+// of the post-collision moment differences in dh[] (h* - E(u)).
+template <int D>
+__device__ __forceinline__ void flow_collide(const DevParams& p, float phi, const float grad[3], float lap,
+                                             const FlowMoments& m, CellState& s, float dh[27])
+{
+    const float rho = p.rho_l + p.drho * phi;
+    const float inv_rho = 1.0f / rho;
+    float nu;
+    if (p.flags & kFlagDynamicVisc)
+        nu = (p.eta_l + (p.eta_h - p.eta_l) * phi) * inv_rho;
+    else
+        nu = p.nu_h + (p.nu_l - p.nu_h) * (1.0f - phi);
+    const float omega = 1.0f / (3.0f * nu + 0.5f);
+    const float om1 = 1.0f - omega;
+
+    // interface normal, chemical potential, force
+    const float g2 = grad[0] * grad[0] + grad[1] * grad[1] + (D == 3 ? grad[2] * grad[2] : 0.f);
+    const float inv_g = 1.0f / fmaxf(sqrtf(g2), 1e-12f);
+    const float mu = p.beta2 * phi * (phi - 1.0f) * (2.0f * phi - 1.0f) - p.kappa * lap;
+    float F[3];
+    F[0] = mu * grad[0];
+    F[1] = mu * grad[1];
+    F[2] = (D == 3) ? mu * grad[2] : 0.f;
+    if (p.flags & kFlagUniformForce)
+        F[0] += p.force_x;
+    else
+        F[D - 1] -= (rho - p.rho_bar) * p.g_accel;
+
+    // u = J/(rho cs2) + F/(2 rho)
+    for (int i = 0; i < 3; ++i) {
+        s.u[i] = (D == 2 && i == 2) ? 0.f : (3.0f * m.J[i] + 0.5f * F[i]) * inv_rho;
+        s.n[i] = (D == 2 && i == 2) ? 0.f : grad[i] * inv_g;
+        s.G[i] = (D == 2 && i == 2) ? 0.f : kCs2 * p.drho * grad[i];
+        s.V[i] = s.G[i] + F[i];
+    }
+    const float ux = s.u[0], uy = s.u[1], uz = s.u[2];
+    s.uG = ux * s.G[0] + uy * s.G[1] + uz * s.G[2];
+    s.uV = ux * s.V[0] + uy * s.V[1] + uz * s.V[2];
+    s.uu = ux * ux + uy * uy + uz * uz;
+    s.rcs2 = kCs2 * rho;
+    s.ph = m.P + 0.5f * s.uG;
+    s.phi = phi;
+    s.sharp = p.lam_sharp * phi * (1.0f - phi);
+
+    // second moments of f^p minus theta cs2 delta, times rho cs2:
+    // Pi_ij - cs2 P delta_ij + [cs2 (u_i V_j + u_j V_i) - u_i u_j u.V]/2
+    const float hV = 0.5f * s.uV;
+    const float c3 = 3.0f * inv_rho;  // 1/(rho cs2)
+    float dxx = c3 * (m.Pxx - kCs2 * m.P + kCs2 * ux * s.V[0] - ux * ux * hV) - ux * ux;
+    float dyy = c3 * (m.Pyy - kCs2 * m.P + kCs2 * uy * s.V[1] - uy * uy * hV) - uy * uy;
+    float dxy = c3 * (m.Pxy + 0.5f * kCs2 * (ux * s.V[1] + uy * s.V[0]) - ux * uy * hV) - ux * uy;
+    float dzz = 0.f, dxz = 0.f, dyz = 0.f;
+    if (D == 3) {
+        dzz = c3 * (m.Pzz - kCs2 * m.P + kCs2 * uz * s.V[2] - uz * uz * hV) - uz * uz;
+        dxz = c3 * (m.Pxz + 0.5f * kCs2 * (ux * s.V[2] + uz * s.V[0]) - ux * uz * hV) - ux * uz;
+        dyz = c3 * (m.Pyz + 0.5f * kCs2 * (uy * s.V[2] + uz * s.V[1]) - uy * uz * hV) - uy * uz;
+    }
+    // cumulant relaxation: shear rate on off-diagonal and deviatoric parts,
+    // trace to D cs2 (rate one), every higher cumulant to zero (rate one)
+    const float tr = (D == 3) ? (dxx + dyy + dzz) * (1.0f / 3.0f) : (dxx + dyy) * 0.5f;
+    const float a = om1 * (dxx - tr), b = om1 * (dyy - tr), c = (D == 3) ? om1 * (dzz - tr) : 0.f;
+    const float pq = om1 * dxy, qq = om1 * dxz, rr = om1 * dyz;
+
+    // per-axis product equilibrium and its deviation from w1
+    for (int i = 0; i < 3; ++i) {
+        const float ui = s.u[i], u2 = ui * ui;
+        s.ew[i][0] = 0.5f * (u2 - ui);
+        s.ew[i][1] = -u2;
+        s.ew[i][2] = 0.5f * (u2 + ui);
+        s.ef[i][0] = (float)(1.0 / 6.0) + s.ew[i][0];
+        s.ef[i][1] = (float)(2.0 / 3.0) + s.ew[i][1];
+        s.ef[i][2] = (float)(1.0 / 6.0) + s.ew[i][2];
+    }
+
+    // post-collision central-moment differences (Gaussian closure minus the
+    // Gaussian of cs2 I), index ia + 3 ib + 9 ic
+    float k[27];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) k[i] = 0.f;
+    const float cs2 = kCs2;
+    k[2] = a;            // 200
+    k[6] = b;            // 020
+    k[4] = pq;           // 110
+    k[8] = cs2 * (a + b) + a * b + 2.f * pq * pq;  // 220
+    if (D == 3) {
+        k[18] = c;       // 002
+        k[10] = qq;      // 101
+        k[12] = rr;      // 011
+        k[20] = cs2 * (a + c) + a * c + 2.f * qq * qq;           // 202
+        k[24] = cs2 * (b + c) + b * c + 2.f * rr * rr;           // 022
+        k[14] = (cs2 + a) * rr + 2.f * pq * qq;                  // 211
+        k[16] = (cs2 + b) * qq + 2.f * pq * rr;                  // 121
+        k[22] = (cs2 + c) * pq + 2.f * qq * rr;                  // 112
+        k[26] = cs2 * cs2 * (a + b + c) + cs2 * (a * b + b * c + c * a) + a * b * c +
+                2.f * ((cs2 + a) * rr * rr + (cs2 + b) * qq * qq + (cs2 + c) * pq * pq) + 8.f * pq * qq * rr;  // 222
+    }
+    // Kronecker inverse about u: per axis (k0,k1,k2) -> (c=-1, 0, +1)
+    // m1 = k1 + u k0, m2 = k2 + 2u k1 + u^2 k0; f(0) = k0 - m2, f(+-1) = (m2 +- m1)/2
+    constexpr int NZ = (D == 3) ? 3 : 1;
+#pragma unroll
+    for (int ic = 0; ic < NZ; ++ic)
+#pragma unroll
+        for (int ib = 0; ib < 3; ++ib) {
+            const int o = 3 * ib + 9 * ic;
+            const float k0 = k[o], k1 = k[o + 1], k2 = k[o + 2];
+            const float m1 = k1 + ux * k0, m2 = k2 + 2.f * ux * k1 + ux * ux * k0;
+            k[o] = 0.5f * (m2 - m1);
+            k[o + 1] = k0 - m2;
+            k[o + 2] = 0.5f * (m2 + m1);
+        }
+#pragma unroll
+    for (int ic = 0; ic < NZ; ++ic)
+#pragma unroll
+        for (int ia = 0; ia < 3; ++ia) {
+            const int o = ia + 9 * ic;
+            const float k0 = k[o], k1 = k[o + 3], k2 = k[o + 6];
+            const float m1 = k1 + uy * k0, m2 = k2 + 2.f * uy * k1 + uy * uy * k0;
+            k[o] = 0.5f * (m2 - m1);
+            k[o + 3] = k0 - m2;
+            k[o + 6] = 0.5f * (m2 + m1);
+        }
+    if (D == 3) {
+#pragma unroll
+        for (int ib = 0; ib < 3; ++ib)
+#pragma unroll
+            for (int ia = 0; ia < 3; ++ia) {
+                const int o = ia + 3 * ib;
+                const float k0 = k[o], k1 = k[o + 9], k2 = k[o + 18];
+                const float m1 = k1 + uz * k0, m2 = k2 + 2.f * uz * k1 + uz * uz * k0;
+                k[o] = 0.5f * (m2 - m1);
+                k[o + 9] = k0 - m2;
+                k[o + 18] = 0.5f * (m2 + m1);
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < 27; ++i) dh[i] = k[i];
+}
+
+// Second-order Hermite equilibrium f_eq/rho (App. A) for direction a.
+template <int D>
+__device__ __forceinline__ float gamma_eq(const CellState& s, int a)
+{
+    const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
+    const float cu = cx * s.u[0] + cy * s.u[1] + cz * s.u[2];
+    return Lat<D>::w(a) * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * s.uu);
+}
+
+// Post-collision f'*_a = rho cs2 (h*_a - w_a) + w_a p_h + Xi_a/2 with
+// h* - w = (E(u) - w) + dh and Xi_a = Gamma_a (c_a - u).V - w_a (c_a - u).G.
+template <int D>
+__device__ __forceinline__ float flow_post(const CellState& s, const float dh[27], int a, float gam)
+{
+    const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
+    const float w = Lat<D>::w(a);
+    const float cV = cx * s.V[0] + cy * s.V[1] + cz * s.V[2] - s.uV;
+    const float cG = cx * s.G[0] + cy * s.G[1] + cz * s.G[2] - s.uG;
+    const float xi = gam * cV - w * cG;
+    // telescoped E - w = e_x e_y e_z - w_x w_y w_z
+    const float wx = (float)w1d(cx), wy = (float)w1d(cy), wz = (float)w1d(cz);
+    const float ex = s.ef[0][cx + 1], ey = s.ef[1][cy + 1];
+    float ew;
+    if (D == 3)
+        ew = s.ew[0][cx + 1] * wy * wz + ex * s.ew[1][cy + 1] * wz + ex * ey * s.ew[2][cz + 1];
+    else
+        ew = s.ew[0][cx + 1] * wy + ex * s.ew[1][cy + 1];
+    return s.rcs2 * (ew + dh[a]) + w * s.ph + 0.5f * xi;
+}
+
+// Phase-field BGK with the sharpening source (Sec. 2.2, readings A3-A5):
+// g* = g - (g - phi Gamma)/tau + lambda w (c.n) 4 phi (1-phi)/W
+template <int D>
+__device__ __forceinline__ float phase_post(const DevParams& p, const CellState& s, int a, float g, float gam)
+{
+    const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
+    const float cn = cx * s.n[0] + cy * s.n[1] + cz * s.n[2];
+    return g + p.inv_tau_phi * (s.phi * gam - g) + Lat<D>::w(a) * cn * s.sharp;
+}
+
+}  // namespace lbmp

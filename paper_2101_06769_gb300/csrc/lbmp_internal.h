@@ -1,0 +1,49 @@
+// lbmp_internal.h -- host-side handle of the C ABI and the kernel launchers
+// shared between the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/lbmp.h"
+#include "lbmp_common.cuh"
+
+struct lbmp_handle {
+    lbmp_grid grid;
+    int D, Q;
+    lbmp_params params;
+    lbmp_derived der;
+    lbmp::DevParams dp;
+    cudaStream_t stream;
+    int device;
+    long long N;
+    // ping-pong population sets; buffers hold post-collision values of the
+    // previous step (pull streaming reads them upstream)
+    float* f[2];
+    float* g[2];
+    float* phi;        // phi = sum g, refreshed by the phi pass
+    int parity;        // f[parity], g[parity] hold the current state
+    long step;
+    int kernel;        // LBMP_OPT_KERNEL
+    int probe[3];
+    // observables scratch (partial sums per block) and result slot
+    double* red;
+    int red_blocks;
+    double* red_out;
+};
+
+namespace lbmp {
+
+// kernel launchers (return cudaError_t of the launch)
+cudaError_t launch_phi_pass(lbmp_handle* h);
+cudaError_t launch_step_simple(lbmp_handle* h);
+cudaError_t launch_step_fused(lbmp_handle* h);
+cudaError_t launch_init(lbmp_handle* h, int case_id, const double* args, unsigned long long seed);
+cudaError_t launch_set_state(lbmp_handle* h, const double* dev_f, const double* dev_g);
+cudaError_t launch_get_state(lbmp_handle* h, double* dev_f, double* dev_g);
+// dev_out: [0..3] mass, kinetic energy, max|u|, non-finite count; [4..5] probe
+// pressures; [16..16+2nv) phi on the spike and bubble columns
+cudaError_t launch_observables(lbmp_handle* h, double* dev_out);
+cudaError_t launch_mass(lbmp_handle* h, double* dev_out4);  // writes 4 doubles, [0] = mass
+bool fused_supported(const lbmp_handle* h);
+
+}  // namespace lbmp

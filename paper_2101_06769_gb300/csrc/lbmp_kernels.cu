@@ -1,0 +1,446 @@
+// lbmp_kernels.cu -- the reference step pair (phi pass + one thread per cell),
+// initial conditions, state conversion and the FP64 observables.
+//
+// Streaming is "pull" with two population sets: step t reads set t&1 at the
+// upstream cell x - c_a and writes its post-collision values to set 1-(t&1)
+// at x.  Across a half-way bounce-back wall the upstream value is the
+// opposite population of the cell itself (Sec. 3.2 boundary treatment).
+#include <math.h>
+
+#include "lbmp_internal.h"
+
+namespace lbmp {
+
+// ------------------------------------------------------------- phi pass
+template <int D>
+__global__ void phi_pass_kernel(DevParams p, const float* __restrict__ g, float* __restrict__ phi)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= p.N) return;
+    int x, y, z;
+    cell_xyz(p, i, x, y, z);
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < Lat<D>::Q; ++a) s += g[pull_index<D>(p, a, x, y, z, i)];
+    phi[i] = s;  // phi = sum_a g_a (Sec. 2.2)
+}
+
+// ----------------------------------------------------- reference step
+template <int D>
+__global__ void __launch_bounds__(128) step_simple_kernel(DevParams p, const float* __restrict__ fin,
+                                                          const float* __restrict__ gin, float* __restrict__ fout,
+                                                          float* __restrict__ gout, const float* __restrict__ phi)
+{
+    constexpr int Q = Lat<D>::Q;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= p.N) return;
+    int x, y, z;
+    cell_xyz(p, i, x, y, z);
+    float nb[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) nb[a] = phi[nbr_index<D>(p, a, x, y, z)];
+    float grad[3], lap;
+    stencil_from_nb<D>(nb, grad, lap);
+    FlowMoments m;
+    zero_moments(m);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) accumulate_moments<D>(m, a, fin[pull_index<D>(p, a, x, y, z, i)]);
+    CellState s;
+    float dh[27];
+    flow_collide<D>(p, nb[Q / 2], grad, lap, m, s, dh);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) fout[(long long)a * p.N + i] = flow_post<D>(s, dh, a, gamma_eq<D>(s, a));
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const float gv = gin[pull_index<D>(p, a, x, y, z, i)];
+        gout[(long long)a * p.N + i] = phase_post<D>(p, s, a, gv, gamma_eq<D>(s, a));
+    }
+}
+
+static unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
+
+cudaError_t launch_phi_pass(lbmp_handle* h)
+{
+    const int B = 256;
+    if (h->D == 3)
+        phi_pass_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->g[h->parity], h->phi);
+    else
+        phi_pass_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->g[h->parity], h->phi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_simple(lbmp_handle* h)
+{
+    cudaError_t e = launch_phi_pass(h);
+    if (e != cudaSuccess) return e;
+    const int B = 128;
+    const int s = h->parity, d = 1 - h->parity;
+    if (h->D == 3)
+        step_simple_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->f[s], h->g[s], h->f[d], h->g[d],
+                                                                      h->phi);
+    else
+        step_simple_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->f[s], h->g[s], h->f[d], h->g[d],
+                                                                      h->phi);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------- initial conditions
+// splitmix64 (Steele, Lea & Flood 2014): output of the (counter+1)-th call of
+// the generator whose state starts at seed.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long counter)
+{
+    unsigned long long z = seed + (counter + 1ULL) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+struct InitArgs {
+    double a[8];
+    double W, rho_l, rho_h, sigma, U_ref;
+    unsigned long long seed;
+    int case_id;
+};
+
+__device__ __forceinline__ double tanh_prof(double d, double W) { return 0.5 * (1.0 + tanh(2.0 * d / W)); }
+
+// Initial conditions (reading A18): tanh phi profiles, f' = f'_eq(p, rho, u),
+// g = g_eq(phi, u), written to the slots the next step pulls from.
+template <int D>
+__global__ void init_kernel(DevParams p, InitArgs A, float* __restrict__ f, float* __restrict__ g)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= p.N) return;
+    int x, y, z;
+    cell_xyz(p, i, x, y, z);
+    const int n[3] = {p.nx, p.ny, p.nz};
+    const double pos[3] = {(double)x, (double)y, (double)z};
+    const int v = D - 1;
+    const double hv = pos[v];
+    const double PI = 3.14159265358979323846;
+    double phi = 0.0, pr = 0.0, u[3] = {0.0, 0.0, 0.0}, noise = 0.0;
+    switch (A.case_id) {
+    case LBMP_CASE_RT: {
+        double hh = A.a[0] + A.a[1] * cos(2.0 * PI * x / n[0]);
+        if (D == 3) hh += A.a[1] * cos(2.0 * PI * y / n[1]);
+        phi = tanh_prof(hv - hh, A.W);
+        noise = A.a[2];
+        break;
+    }
+    case LBMP_CASE_DROP_STATIC: {
+        double r2 = 0.0;
+        for (int k = 0; k < D; ++k) {
+            const double dx = pos[k] - (double)(n[k] / 2);
+            r2 += dx * dx;
+        }
+        phi = tanh_prof(A.a[0] - sqrt(r2), A.W);
+        if (A.a[1] != 0.0) pr = (D == 3 ? 2.0 : 1.0) * A.sigma / A.a[0] * phi;
+        noise = A.a[2];
+        break;
+    }
+    case LBMP_CASE_FLAT:
+        phi = tanh_prof(fmin(pos[0] - A.a[0], A.a[1] - pos[0]), A.W);
+        noise = A.a[2];
+        break;
+    case LBMP_CASE_POISEUILLE:
+        phi = tanh_prof(0.5 * (n[v] - 1) - hv, A.W);
+        noise = A.a[0];
+        break;
+    case LBMP_CASE_DROP_SHEET: {
+        const double Dd = A.a[0], sheet = A.a[1], U0 = A.a[2];
+        const double zc = sheet + 0.5 * Dd + 2.0 * A.W;
+        double r2 = 0.0;
+        for (int k = 0; k < D; ++k) {
+            const double c0 = (k == v) ? zc : (double)(n[k] / 2);
+            const double dx = pos[k] - c0;
+            r2 += dx * dx;
+        }
+        const double d_drop = 0.5 * Dd - sqrt(r2);
+        phi = tanh_prof(fmax(d_drop, sheet - hv), A.W);
+        u[v] = -U0 * tanh_prof(d_drop, A.W);
+        noise = A.a[3];
+        break;
+    }
+    case LBMP_CASE_SHEAR_WAVE:
+        phi = 1.0;
+        u[0] = A.a[0] * sin(2.0 * PI * y / n[1]);
+        noise = A.a[1];
+        break;
+    default:  // LBMP_CASE_UNIFORM
+        phi = A.a[0];
+        pr = A.a[1];
+        u[0] = A.a[2];
+        u[1] = A.a[3];
+        u[2] = (D == 3) ? A.a[4] : 0.0;
+        break;
+    }
+    if (noise != 0.0) {
+        for (int k = 0; k < D; ++k) {
+            const double r = (double)(splitmix64(A.seed, 3ULL * (unsigned long long)i + k) >> 11) *
+                             (1.0 / 9007199254740992.0);
+            u[k] += noise * A.U_ref * (2.0 * r - 1.0) * phi;
+        }
+    }
+    const double rho = A.rho_l + (A.rho_h - A.rho_l) * phi;
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+    for (int a = 0; a < Lat<D>::Q; ++a) {
+        const double w = w1d(Lat<D>::cx(a)) * w1d(Lat<D>::cy(a)) * (D == 3 ? w1d(Lat<D>::cz(a)) : 1.0);
+        const double cu = Lat<D>::cx(a) * u[0] + Lat<D>::cy(a) * u[1] + Lat<D>::cz(a) * u[2];
+        // Gamma - w = w [c.u/cs2 + ((c.u)^2 - cs2 u^2)/(2 cs4)]
+        const double gdev = w * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+        const long long slot = pull_index<D>(p, a, x, y, z, i);
+        f[slot] = (float)(w * pr + rho * (1.0 / 3.0) * gdev);  // f'_eq (Sec. 2.3)
+        g[slot] = (float)(phi * (w + gdev));                   // g_eq (Sec. 2.2)
+    }
+}
+
+cudaError_t launch_init(lbmp_handle* h, int case_id, const double* args, unsigned long long seed)
+{
+    InitArgs A;
+    for (int k = 0; k < 8; ++k) A.a[k] = args[k];
+    A.W = h->der.W;
+    A.rho_l = h->der.rho_l;
+    A.rho_h = h->der.rho_h;
+    A.sigma = h->der.sigma;
+    A.U_ref = h->der.U_ref;
+    A.seed = seed;
+    A.case_id = case_id;
+    const int B = 128;
+    if (h->D == 3)
+        init_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, A, h->f[h->parity], h->g[h->parity]);
+    else
+        init_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, A, h->f[h->parity], h->g[h->parity]);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ state exchange
+template <int D>
+__global__ void state_io_kernel(DevParams p, float* f, float* g, double* cf, double* cg, int to_canonical)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= p.N) return;
+    int x, y, z;
+    cell_xyz(p, i, x, y, z);
+#pragma unroll
+    for (int a = 0; a < Lat<D>::Q; ++a) {
+        const long long slot = pull_index<D>(p, a, x, y, z, i);
+        const long long c = (long long)a * p.N + i;
+        if (to_canonical) {
+            if (cf) cf[c] = (double)f[slot];
+            if (cg) cg[c] = (double)g[slot];
+        } else {
+            f[slot] = (float)cf[c];
+            g[slot] = (float)cg[c];
+        }
+    }
+}
+
+cudaError_t launch_set_state(lbmp_handle* h, const double* dev_f, const double* dev_g)
+{
+    const int B = 256;
+    if (h->D == 3)
+        state_io_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->f[h->parity], h->g[h->parity],
+                                                                   (double*)dev_f, (double*)dev_g, 0);
+    else
+        state_io_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->f[h->parity], h->g[h->parity],
+                                                                   (double*)dev_f, (double*)dev_g, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_state(lbmp_handle* h, double* dev_f, double* dev_g)
+{
+    const int B = 256;
+    if (h->D == 3)
+        state_io_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->f[h->parity], h->g[h->parity], dev_f,
+                                                                   dev_g, 1);
+    else
+        state_io_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->f[h->parity], h->g[h->parity], dev_f,
+                                                                   dev_g, 1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- observables
+// rho, u and p_h = P + cs2 u.grad(rho)/2 of one cell, as in the step.
+template <int D>
+__device__ void cell_macro(const DevParams& p, const float* __restrict__ f, const float* __restrict__ phi, int x,
+                           int y, int z, long long i, float& rho, float u[3], float& ph)
+{
+    constexpr int Q = Lat<D>::Q;
+    float nb[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) nb[a] = phi[nbr_index<D>(p, a, x, y, z)];
+    float grad[3], lap;
+    stencil_from_nb<D>(nb, grad, lap);
+    FlowMoments m;
+    zero_moments(m);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) accumulate_moments<D>(m, a, f[pull_index<D>(p, a, x, y, z, i)]);
+    CellState s;
+    float dh[27];
+    flow_collide<D>(p, nb[Q / 2], grad, lap, m, s, dh);
+    rho = p.rho_l + p.drho * nb[Q / 2];
+    for (int k = 0; k < 3; ++k) u[k] = s.u[k];
+    ph = s.ph;
+}
+
+// per-block partial sums: mass, kinetic energy, max|u|, non-finite count
+template <int D>
+__global__ void __launch_bounds__(256) obs_partial_kernel(DevParams p, const float* __restrict__ f,
+                                                          const float* __restrict__ phi, double* __restrict__ part)
+{
+    __shared__ double sm[4][256];
+    double mass = 0.0, ke = 0.0, um = 0.0, bad = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.N;
+         i += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        cell_xyz(p, i, x, y, z);
+        float rho, u[3], ph;
+        cell_macro<D>(p, f, phi, x, y, z, i, rho, u, ph);
+        const double uu = (double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2];
+        const double ph_i = phi[i];
+        mass += ph_i;
+        ke += 0.5 * rho * uu;
+        const double un = sqrt(uu);
+        if (!(un <= um)) um = un;
+        if (!isfinite(ph_i) || !isfinite(uu) || !isfinite(ph)) bad += 1.0;
+    }
+    const int t = threadIdx.x;
+    sm[0][t] = mass;
+    sm[1][t] = ke;
+    sm[2][t] = um;
+    sm[3][t] = bad;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (t < s) {
+            sm[0][t] += sm[0][t + s];
+            sm[1][t] += sm[1][t + s];
+            const double o = sm[2][t + s];
+            if (!(o <= sm[2][t])) sm[2][t] = o;
+            sm[3][t] += sm[3][t + s];
+        }
+        __syncthreads();
+    }
+    if (t == 0)
+        for (int k = 0; k < 4; ++k) part[4 * blockIdx.x + k] = sm[k][0];
+}
+
+// fixed-order final reduction of the partials (deterministic for a fixed grid)
+__global__ void __launch_bounds__(256) obs_final_kernel(const double* __restrict__ part, int nblocks,
+                                                        double* __restrict__ out)
+{
+    __shared__ double sm[4][256];
+    const int t = threadIdx.x;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = t; b < nblocks; b += 256) {
+        acc[0] += part[4 * b];
+        acc[1] += part[4 * b + 1];
+        const double o = part[4 * b + 2];
+        if (!(o <= acc[2])) acc[2] = o;
+        acc[3] += part[4 * b + 3];
+    }
+    for (int k = 0; k < 4; ++k) sm[k][t] = acc[k];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (t < s) {
+            sm[0][t] += sm[0][t + s];
+            sm[1][t] += sm[1][t + s];
+            const double o = sm[2][t + s];
+            if (!(o <= sm[2][t])) sm[2][t] = o;
+            sm[3][t] += sm[3][t + s];
+        }
+        __syncthreads();
+    }
+    if (t == 0)
+        for (int k = 0; k < 4; ++k) out[k] = sm[k][0];
+}
+
+// mean p_h over the 3^D block at a probe cell (one block of threads per probe)
+template <int D>
+__global__ void probe_kernel(DevParams p, const float* __restrict__ f, const float* __restrict__ phi, int px, int py,
+                             int pz, int qx, int qy, int qz, double* __restrict__ out)
+{
+    __shared__ double sm[32];
+    const int t = threadIdx.x;
+    const int npts = (D == 3) ? 27 : 9;
+    const int cx = blockIdx.x == 0 ? px : qx, cy = blockIdx.x == 0 ? py : qy, cz = blockIdx.x == 0 ? pz : qz;
+    double v = 0.0;
+    if (t < npts) {
+        const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = (D == 3) ? t / 9 - 1 : 0;
+        const int x = wrap_h(cx + dx, p.nx);
+        int y, z;
+        if (D == 3) {
+            y = wrap_h(cy + dy, p.ny);
+            z = wrap_v(cz + dz, p.nz, p.vert_periodic);
+        } else {
+            y = wrap_v(cy + dy, p.ny, p.vert_periodic);
+            z = 0;
+        }
+        const long long i = ((long long)z * p.ny + y) * p.nx + x;
+        float rho, u[3], ph;
+        cell_macro<D>(p, f, phi, x, y, z, i, rho, u, ph);
+        v = ph;
+    }
+    sm[t] = v;
+    __syncthreads();
+    if (t == 0) {
+        double s = 0.0;
+        for (int k = 0; k < npts; ++k) s += sm[k];
+        out[blockIdx.x] = s / npts;
+    }
+}
+
+// phi on the spike column (nx/2, ny/2) and the bubble column (0, 0)
+template <int D>
+__global__ void column_kernel(DevParams p, const float* __restrict__ phi, double* __restrict__ out)
+{
+    const int nv = (D == 3) ? p.nz : p.ny;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nv) return;
+    long long is, ib;
+    if (D == 3) {
+        is = ((long long)k * p.ny + p.ny / 2) * p.nx + p.nx / 2;
+        ib = (long long)k * p.ny * p.nx;
+    } else {
+        is = (long long)k * p.nx + p.nx / 2;
+        ib = (long long)k * p.nx;
+    }
+    out[k] = phi[is];
+    out[nv + k] = phi[ib];
+}
+
+cudaError_t launch_observables(lbmp_handle* h, double* dev_out)
+{
+    cudaError_t e = launch_phi_pass(h);
+    if (e != cudaSuccess) return e;
+    const float* f = h->f[h->parity];
+    const int nv = (h->D == 3) ? h->grid.nz : h->grid.ny;
+    const int* pr = h->probe;
+    if (h->D == 3) {
+        obs_partial_kernel<3><<<h->red_blocks, 256, 0, h->stream>>>(h->dp, f, h->phi, h->red);
+        obs_final_kernel<<<1, 256, 0, h->stream>>>(h->red, h->red_blocks, dev_out);
+        probe_kernel<3><<<2, 32, 0, h->stream>>>(h->dp, f, h->phi, pr[0], pr[1], pr[2], 0, 0, 0, dev_out + 4);
+        column_kernel<3><<<grid_for(nv, 128), 128, 0, h->stream>>>(h->dp, h->phi, dev_out + 16);
+    } else {
+        obs_partial_kernel<2><<<h->red_blocks, 256, 0, h->stream>>>(h->dp, f, h->phi, h->red);
+        obs_final_kernel<<<1, 256, 0, h->stream>>>(h->red, h->red_blocks, dev_out);
+        probe_kernel<2><<<2, 32, 0, h->stream>>>(h->dp, f, h->phi, pr[0], pr[1], 0, 0, 0, 0, dev_out + 4);
+        column_kernel<2><<<grid_for(nv, 128), 128, 0, h->stream>>>(h->dp, h->phi, dev_out + 16);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mass(lbmp_handle* h, double* dev_out4)
+{
+    cudaError_t e = launch_phi_pass(h);
+    if (e != cudaSuccess) return e;
+    const float* f = h->f[h->parity];
+    if (h->D == 3)
+        obs_partial_kernel<3><<<h->red_blocks, 256, 0, h->stream>>>(h->dp, f, h->phi, h->red);
+    else
+        obs_partial_kernel<2><<<h->red_blocks, 256, 0, h->stream>>>(h->dp, f, h->phi, h->red);
+    obs_final_kernel<<<1, 256, 0, h->stream>>>(h->red, h->red_blocks, dev_out4);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmp

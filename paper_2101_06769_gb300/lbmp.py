@@ -1,0 +1,195 @@
+"""ctypes binding of the C ABI in include/lbmp.h (argument marshalling only).
+
+Every step of the multiphase update runs in the CUDA library
+``_build/liblbmp.so``; this module converts Python arguments to the C
+structures and back.  There is no CPU fallback: if the library is missing or
+no GPU is present the calls raise.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblbmp.so")
+
+D2Q9, D3Q27 = 0, 1
+FP32, FP16_SHIFTED, BF16_SHIFTED = 0, 1, 2
+CASE = {"rt": 0, "drop_static": 1, "flat": 2, "poiseuille": 3, "drop_sheet": 4, "shear_wave": 5,
+        "uniform": 6}
+FLAG_WE_LIGHT, FLAG_DYNAMIC_VISC, FLAG_UNIFORM_FORCE = 1, 2, 4
+OPT_KERNEL = 0
+ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5: "UNSTABLE",
+          -6: "UNSUPPORTED"}
+
+# every entry point declared in include/lbmp.h
+EXPORTS = ("lbmp_create", "lbmp_destroy", "lbmp_last_error", "lbmp_get_derived", "lbmp_init",
+           "lbmp_step", "lbmp_sync", "lbmp_observables", "lbmp_get_state", "lbmp_set_state",
+           "lbmp_state_bytes", "lbmp_upload", "lbmp_download", "lbmp_set_option")
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("periodic", C.c_int * 3)]
+
+
+class Params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in
+                ("rho_ratio", "nu_ratio", "We", "Re", "atwood", "mobility", "width", "g_accel",
+                 "U0", "L_ref", "sigma", "nu_h", "force_x")] + [("storage", C.c_int),
+                                                                ("flags", C.c_uint)]
+
+
+class Derived(C.Structure):
+    _fields_ = [(n, C.c_double) for n in
+                ("rho_h", "rho_l", "nu_h", "nu_l", "sigma", "beta", "kappa", "M", "W", "tau_phi",
+                 "lambda_phi", "g_accel", "U_ref", "force_x")]
+
+
+class Obs(C.Structure):
+    _fields_ = [(n, C.c_double) for n in
+                ("mass", "mass_drift_rel", "kinetic_energy", "max_u", "p_in", "p_out", "laplace_dp",
+                 "tip_spike", "tip_bubble")] + [("step", C.c_long), ("health", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LbmpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = C.CDLL(path)
+    vp = C.c_void_p
+    L.lbmp_create.argtypes = [C.POINTER(Grid), C.c_int, C.POINTER(Params), vp, C.POINTER(vp)]
+    L.lbmp_destroy.argtypes = [vp]
+    L.lbmp_last_error.restype = C.c_char_p
+    L.lbmp_get_derived.argtypes = [vp, C.POINTER(Derived)]
+    L.lbmp_init.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.c_int, C.c_ulonglong]
+    L.lbmp_step.argtypes = [vp, C.c_long]
+    L.lbmp_sync.argtypes = [vp]
+    L.lbmp_observables.argtypes = [vp, C.POINTER(Obs)]
+    L.lbmp_get_state.argtypes = [vp, vp, vp, vp]
+    L.lbmp_set_state.argtypes = [vp, vp, vp]
+    L.lbmp_state_bytes.restype = C.c_size_t
+    L.lbmp_state_bytes.argtypes = [vp]
+    L.lbmp_upload.argtypes = [vp, vp, C.c_size_t]
+    L.lbmp_download.argtypes = [vp, vp, C.c_size_t]
+    L.lbmp_set_option.argtypes = [vp, C.c_int, C.c_long]
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise LbmpError(rc, load().lbmp_last_error().decode())
+    return rc
+
+
+def make_params(**kw):
+    p = Params(rho_ratio=1.0, nu_ratio=1.0, We=0.0, Re=0.0, atwood=0.0, mobility=0.02, width=5.0,
+               g_accel=0.0, U0=0.0, L_ref=0.0, sigma=-1.0, nu_h=-1.0, force_x=0.0, storage=FP32,
+               flags=0)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Domain:
+    """One simulation domain on the current CUDA device.
+
+    dims = (nx, ny, nz) with nz = 1 for D = 2; periodic = (px, py, pz).
+    ``stream`` is a raw cudaStream_t handle (int) or None for the default stream.
+    """
+
+    def __init__(self, D, dims, periodic=(1, 1, 1), stream=None, **params):
+        L = load()
+        self.D = D
+        self.dims = tuple(int(v) for v in dims)
+        self.Q = 27 if D == 3 else 9
+        self.N = self.dims[0] * self.dims[1] * self.dims[2]
+        g = Grid(self.dims[0], self.dims[1], self.dims[2], (C.c_int * 3)(*[int(v) for v in periodic]))
+        h = C.c_void_p()
+        _check(L.lbmp_create(C.byref(g), D3Q27 if D == 3 else D2Q9, C.byref(make_params(**params)),
+                             C.c_void_p(stream) if stream else None, C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def shape(self):
+        nx, ny, nz = self.dims
+        return (self.Q, nz, ny, nx)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lbmp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def derived(self):
+        d = Derived()
+        _check(load().lbmp_get_derived(self._h, C.byref(d)))
+        return d
+
+    def set_kernel(self, k):
+        _check(load().lbmp_set_option(self._h, OPT_KERNEL, int(k)))
+
+    def init(self, case, args, seed=0):
+        cid = CASE[case] if isinstance(case, str) else int(case)
+        a = (C.c_double * max(1, len(args)))(*args)
+        _check(load().lbmp_init(self._h, cid, a, len(args), int(seed)))
+
+    def step(self, n=1):
+        _check(load().lbmp_step(self._h, int(n)))
+
+    def sync(self):
+        _check(load().lbmp_sync(self._h))
+
+    def observables(self):
+        o = Obs()
+        rc = load().lbmp_observables(self._h, C.byref(o))
+        if rc not in (0, -5):
+            _check(rc)
+        return o
+
+    def get_state(self):
+        f = np.empty(self.shape)
+        g = np.empty(self.shape)
+        phi = np.empty(self.shape[1:])
+        _check(load().lbmp_get_state(self._h, f.ctypes.data, g.ctypes.data, phi.ctypes.data))
+        return f, g, phi
+
+    def set_state(self, f, g):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        assert f.size == self.Q * self.N and g.size == self.Q * self.N
+        _check(load().lbmp_set_state(self._h, f.ctypes.data, g.ctypes.data))
+
+    def state_bytes(self):
+        return int(load().lbmp_state_bytes(self._h))
+
+    def upload(self, host_ptr, nbytes):
+        _check(load().lbmp_upload(self._h, C.c_void_p(host_ptr), nbytes))
+
+    def download(self, host_ptr, nbytes):
+        _check(load().lbmp_download(self._h, C.c_void_p(host_ptr), nbytes))

@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+identical seeded inputs.
+
+Tolerance: err(X) = max|X_gpu - X_ref| / max|X_ref| <= 1e-5 on f', g and phi
+after 100 steps (FP32 arithmetic against FP64; reading A24 of the design
+notes for the norm-wise measure).  Shapes span several thread blocks and
+ragged tails; walls and periodic boundaries, odd and even step counts, and
+both step kernels (fused default, reference pair) are covered.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2101_06769_gb300 import Domain, LbmpError
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+CASES = {
+    # the 2-D Rayleigh-Taylor workload: 64 x 256, At 0.5, Re 256, sqrt(g L) = 0.04, W 5, M 0.02
+    "rt2d": dict(D=2, dims=(64, 256, 1), periodic=(1, 0, 1),
+                 phys=dict(atwood=0.5, nu_ratio=1.0, Re=256.0, g_accel=2.5e-5, L_ref=64.0,
+                           mobility=0.02, width=5.0),
+                 case="rt", args=[128.0, 6.4, 1e-4], seed=1),
+    # reduced 3-D Rayleigh-Taylor (same non-dimensional set-up, 32 x 32 x 64)
+    "rt3d": dict(D=3, dims=(32, 32, 64), periodic=(1, 1, 0),
+                 phys=dict(atwood=0.5, nu_ratio=1.0, Re=1024.0, g_accel=5e-5, L_ref=32.0,
+                           mobility=0.02, width=5.0),
+                 case="rt", args=[32.0, 3.2, 1e-4], seed=2),
+    # reduced droplet-on-sheet splash, density ratio 1000, viscosity ratio 15, We 8000, Re 1000
+    "splash3d": dict(D=3, dims=(64, 64, 32), periodic=(1, 1, 0),
+                     phys=dict(rho_ratio=1000.0, nu_ratio=15.0, We=8000.0, Re=1000.0, U0=0.05,
+                               L_ref=16.0, mobility=0.02, width=4.0),
+                     case="drop_sheet", args=[16.0, 3.2, 0.05, 1e-4], seed=3),
+    # 2-D static drop with surface tension at density ratio 1000
+    "drop2d": dict(D=2, dims=(48, 48, 1), periodic=(1, 1, 1),
+                   phys=dict(rho_ratio=1000.0, nu_ratio=1.0, nu_h=0.1, sigma=1e-3, mobility=0.02,
+                             width=5.0),
+                   case="drop_static", args=[12.0, 0.0, 1e-3], seed=4),
+    # ragged sizes (no multiple of any tile), fully periodic 3-D drop
+    "ragged3d": dict(D=3, dims=(37, 29, 23), periodic=(1, 1, 1),
+                     phys=dict(rho_ratio=20.0, nu_ratio=2.0, nu_h=0.05, sigma=1e-2, mobility=0.02,
+                               width=4.0),
+                     case="drop_static", args=[7.0, 1.0, 1e-2], seed=5),
+    # ragged 2-D with walls and the dynamic-viscosity reading
+    "ragged2d": dict(D=2, dims=(33, 47, 1), periodic=(1, 0, 1),
+                     phys=dict(rho_ratio=10.0, nu_ratio=5.0, nu_h=0.02, sigma=5e-3, g_accel=1e-5,
+                               mobility=0.03, width=4.0, flags=2),
+                     case="rt", args=[23.0, 3.0, 1e-2], seed=6),
+    # thin 3-D with walls: every thread block touches a wall plane
+    "thin3d": dict(D=3, dims=(8, 6, 5), periodic=(1, 1, 0),
+                   phys=dict(rho_ratio=3.0, nu_ratio=1.0, nu_h=0.05, sigma=1e-2, g_accel=1e-4,
+                             mobility=0.02, width=3.0),
+                   case="rt", args=[2.0, 0.5, 1e-2], seed=7),
+}
+
+
+def rel_err(a, b):
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
+
+
+def make_pair(name):
+    c = CASES[name]
+    o = O.Oracle(c["D"], c["dims"], c["periodic"], **c["phys"])
+    d = Domain(c["D"], c["dims"], c["periodic"], **c["phys"])
+    return c, o, d
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_init_matches_oracle(name):
+    c, o, d = make_pair(name)
+    o.init(c["case"], c["args"], seed=c["seed"])
+    d.init(c["case"], c["args"], seed=c["seed"])
+    fo, go, po = o.get_state()
+    fg, gg, pg = d.get_state()
+    assert rel_err(gg, go) < 1e-6
+    assert rel_err(pg, po) < 1e-6
+    if np.abs(fo).max() > 0:
+        assert rel_err(fg, fo) < 1e-6
+    else:
+        assert np.abs(fg).max() == 0.0
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_step_parity_100(name, kernel):
+    c, o, d = make_pair(name)
+    o.init(c["case"], c["args"], seed=c["seed"])
+    f0, g0, _ = o.get_state()
+    d.set_state(f0, g0)
+    d.set_kernel(kernel)
+    o.step(100)
+    d.step(100)
+    fo, go, po = o.get_state()
+    fg, gg, pg = d.get_state()
+    ef, eg, ep = rel_err(fg, fo), rel_err(gg, go), rel_err(pg, po)
+    assert ef <= TOL and eg <= TOL and ep <= TOL, (name, kernel, ef, eg, ep)
+
+
+@pytest.mark.parametrize("steps", [1, 2, 7])
+@pytest.mark.parametrize("name", ["rt2d", "thin3d", "ragged3d"])
+def test_step_parity_odd_even(name, steps):
+    c, o, d = make_pair(name)
+    o.init(c["case"], c["args"], seed=c["seed"])
+    d.init(c["case"], c["args"], seed=c["seed"])
+    o.step(steps)
+    d.step(steps)
+    fo, go, po = o.get_state()
+    fg, gg, pg = d.get_state()
+    assert rel_err(fg, fo) <= TOL and rel_err(gg, go) <= TOL and rel_err(pg, po) <= TOL
+
+
+def test_kernels_agree_bitwise():
+    """The fused kernel and the reference pair perform the same FP32 operations
+    in the same order, so their states agree exactly."""
+    c = CASES["splash3d"]
+    a = Domain(c["D"], c["dims"], c["periodic"], **c["phys"])
+    b = Domain(c["D"], c["dims"], c["periodic"], **c["phys"])
+    for dm, k in ((a, 0), (b, 1)):
+        dm.init(c["case"], c["args"], seed=c["seed"])
+        dm.set_kernel(k)
+        dm.step(25)
+    fa, ga, pa = a.get_state()
+    fb, gb, pb = b.get_state()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb) and np.array_equal(pa, pb)
+
+
+def test_set_get_round_trip_is_exact():
+    c = CASES["ragged3d"]
+    d = Domain(c["D"], c["dims"], c["periodic"], **c["phys"])
+    rng = np.random.default_rng(0)
+    f = rng.normal(size=d.shape)
+    g = rng.normal(size=d.shape)
+    d.set_state(f, g)
+    fg, gg, pg = d.get_state()
+    assert np.array_equal(fg, f.astype(np.float32).astype(np.float64))
+    assert np.array_equal(gg, g.astype(np.float32).astype(np.float64))
+    assert np.allclose(pg, gg.sum(0), rtol=0, atol=1e-5)
+
+
+def test_observables_match_oracle():
+    c, o, d = make_pair("drop2d")
+    o.init(c["case"], c["args"], seed=c["seed"])
+    f0, g0, _ = o.get_state()
+    d.set_state(f0, g0)
+    o.step(100)
+    d.step(100)
+    ob, og = o.observables(), d.observables()
+    assert og.health == 0 and og.step == 100
+    assert abs(og.mass / ob.mass - 1) < 1e-6
+    assert abs(og.mass_drift_rel) < 1e-6
+    assert abs(og.kinetic_energy / ob.kinetic_energy - 1) < 1e-3
+    assert abs(og.max_u / ob.max_u - 1) < 1e-3
+    scale = max(abs(ob.p_in), abs(ob.p_out))
+    assert abs(og.p_in - ob.p_in) < 1e-4 * scale
+    assert abs(og.p_out - ob.p_out) < 1e-4 * scale
+    c, o, d = make_pair("rt2d")
+    o.init(c["case"], c["args"], seed=c["seed"])
+    d.init(c["case"], c["args"], seed=c["seed"])
+    o.step(100)
+    d.step(100)
+    ob, og = o.observables(), d.observables()
+    assert abs(og.tip_spike - ob.tip_spike) < 1e-3
+    assert abs(og.tip_bubble - ob.tip_bubble) < 1e-3
+
+
+def test_full_size_rt3d_init_and_two_steps():
+    """The 3-D Rayleigh-Taylor workload at its full size (128 x 128 x 512,
+    8.4M cells), in the launch configuration the benchmark times: the
+    device-generated initial state and two steps against the oracle."""
+    dims = (128, 128, 512)
+    phys = dict(atwood=0.5, nu_ratio=1.0, Re=1024.0, g_accel=1.25e-5, L_ref=128.0, mobility=0.02,
+                width=5.0)
+    args = [256.0, 12.8, 1e-4]
+    o = O.Oracle(3, dims, (1, 1, 0), **phys)
+    o.init("rt", args, seed=11)
+    d = Domain(3, dims, (1, 1, 0), **phys)
+    d.init("rt", args, seed=11)
+    fo, go, po = o.get_state()
+    fg, gg, pg = d.get_state()
+    assert rel_err(gg, go) < 1e-6 and rel_err(pg, po) < 1e-6
+    del fo, go, po, fg, gg, pg
+    o.step(2)
+    d.step(2)
+    fo, go, po = o.get_state()
+    fg, gg, pg = d.get_state()
+    assert rel_err(fg, fo) <= TOL and rel_err(gg, go) <= TOL and rel_err(pg, po) <= TOL
+    ob = d.observables()
+    assert ob.health == 0 and abs(ob.mass_drift_rel) < 1e-6
+
+
+def test_uniform_rest_state_is_stationary():
+    d = Domain(3, (40, 24, 30), (1, 1, 0), rho_ratio=50.0, nu_ratio=3.0, nu_h=0.01, sigma=1e-3,
+               mobility=0.02, width=4.0)
+    for phi0 in (0.0, 1.0, 0.3):
+        d.init("uniform", [phi0, 0.02, 0.0, 0.0, 0.0])
+        f0, g0, _ = d.get_state()
+        d.step(20)
+        f1, g1, p1 = d.get_state()
+        assert np.abs(f1 - f0).max() <= 1e-8
+        assert np.abs(g1 - g0).max() <= 1e-7
+        assert np.abs(p1 - phi0).max() <= 1e-6
+
+
+def test_errors_are_reported():
+    with pytest.raises(LbmpError):
+        Domain(3, (8, 8, 8), (1, 1, 0), rho_ratio=-2.0, nu_h=0.1)
+    d = Domain(2, (16, 16, 1), (1, 1, 1), rho_ratio=2.0, nu_h=0.1)
+    with pytest.raises(LbmpError):
+        d.init("rt", [1.0])
+    with pytest.raises(LbmpError):
+        d.step(-1)
