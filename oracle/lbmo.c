@@ -23,7 +23,7 @@
  *   A9  corrected 6th-order cumulant relation (Pi_yz Pi_x2yz, + cubic group)
  *   A10/A11 all rates other than the shear rate equal to one
  *   A12 linear kinematic viscosity nu(phi)
- *   A13 n = grad(phi)/max(|grad(phi)|, 1e-12)
+ *   A13 n = grad(phi)/max(|grad(phi)|, 1e-4)
  *   A15 F_b = -(rho - (rho_h+rho_l)/2) g e_vertical
  *   A16 We = rho_h L U^2/sigma   A17 half-way bounce-back, mirrored phi ghosts
  *   A18 tanh initial profiles    A21 D2Q9 restriction of the 3-D relations
@@ -471,7 +471,7 @@ static void local_closure(const lbmo *s, const double *f, double phi, const doub
         c->nu = d->nu_h + (d->nu_l - d->nu_h) * (1.0 - phi);
     c->omega = (s->rate_shear > 0.0) ? s->rate_shear : 1.0 / (c->nu / CS2 + 0.5);
     double gn = sqrt(grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2]);
-    double den = fmax(gn, 1e-12);
+    double den = fmax(gn, 1e-4);
     for (int i = 0; i < 3; ++i) c->n[i] = grad[i] / den;
     c->mu = 2.0 * d->beta * phi * (phi - 1.0) * (2.0 * phi - 1.0) - d->kappa * lap;
     for (int i = 0; i < 3; ++i) c->F[i] = c->mu * grad[i];
@@ -700,6 +700,13 @@ int lbmo_init(lbmo *s, int case_id, const double *args, int nargs, unsigned long
             double h = A[0] + A[1] * cos(2.0 * PI * x / s->n[0]);
             if (D == 3) h += A[1] * cos(2.0 * PI * y / s->n[1]);
             phi = tanh_profile(hv - h, d->W);
+            /* optional hydrostatic start: dp/dz = -(rho - rho_bar) g along each column,
+             * i.e. p = -g (rho_h - rho_l) (W/4) ln cosh(2 (z - h)/W), zero at the interface */
+            if (nargs > 3 && A[3] != 0.0) {
+                double t = 2.0 * (hv - h) / d->W, at = fabs(t);
+                double lncosh = at + log1p(exp(-2.0 * at)) - log(2.0);
+                p = -d->g_accel * (d->rho_h - d->rho_l) * 0.25 * d->W * lncosh;
+            }
             break;
         }
         case LBMO_CASE_DROP_STATIC: {

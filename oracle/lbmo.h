@@ -30,7 +30,7 @@ extern "C" {
 
 /* initial-condition cases (reading A18 of the design notes) */
 enum {
-    LBMO_CASE_RT = 0,          /* args: h0, amplitude, noise                 */
+    LBMO_CASE_RT = 0,          /* args: h0, amplitude, noise [, hydrostatic] */
     LBMO_CASE_DROP_STATIC = 1, /* args: R, p_init(0/1), noise                */
     LBMO_CASE_FLAT = 2,        /* args: x0, x1, noise   (heavy slab x0<x<x1)  */
     LBMO_CASE_POISEUILLE = 3,  /* args: noise           (heavy lower half)   */
