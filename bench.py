@@ -31,22 +31,19 @@ WORKLOADS = {
         D=3, dims=(128, 128, 512), periodic=(1, 1, 0),
         phys=dict(atwood=0.5, nu_ratio=1.0, Re=1024.0, g_accel=1.25e-5, L_ref=128.0, mobility=0.02,
                   width=5.0),
-        case="rt", args=[256.0, 12.8, 1e-4], seed=1,
-        cpu_sample=(128, 128, 16, 2)),
+        case="rt", args=[256.0, 12.8, 1e-4, 1.0], seed=1),
     "splash3d": dict(
         desc="3-D droplet impact on a thin sheet, D3Q27, 384x384x192, D 64, sheet 0.2D, U0 0.05, "
              "rho ratio 1000, nu ratio 15, We 8000, Re 1000, W 4, M 0.02",
         D=3, dims=(384, 384, 192), periodic=(1, 1, 0),
         phys=dict(rho_ratio=1000.0, nu_ratio=15.0, We=8000.0, Re=1000.0, U0=0.05, L_ref=64.0,
                   mobility=0.02, width=4.0),
-        case="drop_sheet", args=[64.0, 12.8, 0.05, 1e-4], seed=3,
-        cpu_sample=(96, 96, 48, 2)),
+        case="drop_sheet", args=[64.0, 12.8, 0.05, 1e-4], seed=3),
     "rt2d": dict(
         desc="2-D Rayleigh-Taylor, D2Q9, 64x256, periodic x, walls y, At 0.5, sqrt(gL)=0.04, Re 256, W 5, M 0.02",
         D=2, dims=(64, 256, 1), periodic=(1, 0, 1),
         phys=dict(atwood=0.5, nu_ratio=1.0, Re=256.0, g_accel=2.5e-5, L_ref=64.0, mobility=0.02, width=5.0),
-        case="rt", args=[128.0, 6.4, 1e-4], seed=1,
-        cpu_sample=(64, 256, 1, 50)),
+        case="rt", args=[128.0, 6.4, 1e-4, 1.0], seed=1),
 }
 
 BYTES_PER_CELL = {3: 2 * (27 + 27) * 4, 2: 2 * (9 + 9) * 4}  # populations read once + written once, FP32
@@ -122,47 +119,71 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_baseline(wl, threads=None):
-    """The FP64 oracle as it stands on the host cores, on a bounded sample of
-    the workload: a sub-box with the workload's parameters for a few steps."""
+def _oracle_rate(wl, depth, steps):
+    """oracle MLUPS on a (nx, ny, depth) sub-box of the workload"""
     import oracle as O
-    nx, ny, nz, steps = wl["cpu_sample"]
-    if threads:
-        O.set_threads(threads)
-    cores = O.get_threads()
+    nx, ny = wl["dims"][0], wl["dims"][1]
     D = wl["D"]
     args = list(wl["args"])
     if wl["case"] == "rt":
-        args[0] = (nz if D == 3 else ny) / 2.0
-    o = O.Oracle(D, (nx, ny, nz), wl["periodic"], **wl["phys"])
+        args[0] = depth / 2.0 if D == 3 else ny / 2.0
+    dims = (nx, ny, depth) if D == 3 else (nx, ny, 1)
+    o = O.Oracle(D, dims, wl["periodic"], **wl["phys"])
     o.init(wl["case"], args, seed=wl["seed"])
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
-    cells = nx * ny * nz
-    return {"value": cells * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{nx}x{ny}x{nz} sub-box of the workload, {steps} steps, FP64, {dt:.2f} s"}
+    cells = dims[0] * dims[1] * dims[2]
+    return cells * steps / dt / 1e6, dims, dt
+
+
+def cpu_baseline(wl, budget_s=15.0):
+    """The FP64 oracle as it stands, on all host cores, on a bounded sample of
+    the workload: a horizontal slab of the domain (full x and y extent) with
+    the workload's parameters, stepped for about budget_s seconds."""
+    import oracle as O
+    cores = O.get_threads()
+    depth = min(wl["dims"][2], 64) if wl["D"] == 3 else 1
+    rate, dims, dt = _oracle_rate(wl, depth, 1)
+    steps = max(1, int(budget_s * rate * 1e6 / (dims[0] * dims[1] * dims[2])))
+    rate, dims, dt = _oracle_rate(wl, depth, steps)
+    return {"value": rate, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{dims[0]}x{dims[1]}x{dims[2]} slab of the workload, {steps} steps, FP64, {dt:.1f} s"}
 
 
 def run_reference(args, wl):
+    """The reference arm: the FP64 oracle on the host cores, one bounded
+    sample of the workload per step, sized so that the whole run takes about
+    two minutes."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    per_step = []
+    import oracle as O
+    cores = O.get_threads()
+    depth0 = 8 if wl["D"] == 3 else 1
+    rate, dims, dt = _oracle_rate(wl, depth0, 1)
+    per_sample = 120.0 / max(1, args.steps + args.warmup)
+    cells_target = per_sample * rate * 1e6
+    if wl["D"] == 3:
+        depth = int(max(2, min(wl["dims"][2], cells_target // (wl["dims"][0] * wl["dims"][1]))))
+    else:
+        depth = 1
+    vals, dts = [], []
     for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(wl)
+        r, dims, dt = _oracle_rate(wl, depth, 1)
         if k >= args.warmup:
-            per_step.append(cb)
-    vals = [c["value"] for c in per_step]
+            vals.append(r)
+            dts.append(dt)
     value = statistics.median(vals)
-    nx, ny, nz, st = wl["cpu_sample"]
+    cells = dims[0] * dims[1] * dims[2]
+    sample = f"{dims[0]}x{dims[1]}x{dims[2]} slab of the workload, 1 step per timed step, FP64"
     line = {"impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": nx * ny * nz / value / 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * statistics.median(dts), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl["desc"], "grid": list(wl["dims"])},
-            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": per_step[0]["cores"], "kind": "oracle",
-                             "sample": per_step[0]["sample"] + " per step of this run"},
+            "config": {"workload": args.workload, "desc": wl["desc"], "grid": list(wl["dims"]),
+                       "sample_cells": cells},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -178,8 +199,15 @@ def main():
     ap.add_argument("--kernel", type=int, default=0, help="0 fused (default), 1 reference pair")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--grid", default=None, help="override nx,ny,nz (profiling on a smaller case)")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.grid:
+        dims = tuple(int(v) for v in args.grid.split(","))
+        if wl["case"] == "rt":
+            wl["args"] = [dims[wl["D"] - 1] / 2.0] + list(wl["args"][1:])
+        wl["dims"] = dims
+        wl["desc"] = wl["desc"] + f" (grid overridden to {dims[0]}x{dims[1]}x{dims[2]})"
     if args.impl == "reference":
         return run_reference(args, wl)
 

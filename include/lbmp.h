@@ -66,8 +66,10 @@ enum {
  * velocity perturbation of amplitude noise * U_ref * phi per component, drawn
  * from splitmix64(seed, 3*cell + component). */
 enum {
-    LBMP_CASE_RT = 0,          /* args: h0, amplitude, noise. Heavy above
-                                  h = h0 + amp [cos(2 pi x/nx) (+ cos(2 pi y/ny) in 3-D)] */
+    LBMP_CASE_RT = 0,          /* args: h0, amplitude, noise [, hydrostatic]. Heavy above
+                                  h = h0 + amp [cos(2 pi x/nx) (+ cos(2 pi y/ny) in 3-D)];
+                                  hydrostatic != 0 starts p_h in column-wise balance with
+                                  the body force: p = -g (rho_h - rho_l)(W/4) ln cosh(2(z-h)/W) */
     LBMP_CASE_DROP_STATIC = 1, /* args: R, p_init, noise. Heavy drop of radius R at the
                                   cell (nx/2, ny/2, nz/2); p_init != 0 starts
                                   p_h = (D-1) sigma/R phi */

@@ -181,7 +181,7 @@ int lbmp_create(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* 
         if (e == cudaSuccess) e = cudaMalloc(&h->g[k], pop);
         if (e != cudaSuccess) break;
     }
-    if (e == cudaSuccess) e = cudaMalloc(&h->phi, sizeof(float) * (size_t)N);
+    if (e == cudaSuccess) e = cudaMalloc(&h->phi, 2 * sizeof(float) * (size_t)N);
     h->red_blocks = 1024;
     if (e == cudaSuccess) e = cudaMalloc(&h->red, sizeof(double) * 4 * h->red_blocks);
     const int nv = (D == 3) ? grid->nz : grid->ny;
@@ -336,12 +336,13 @@ int lbmp_get_state(lbmp_handle* h, double* f, double* g, double* phi)
     if (dg) cudaFreeAsync(dg, h->stream);
     if (e == cudaSuccess && phi) {
         e = lbmp::launch_phi_pass(h);
-        float* tmp = new (std::nothrow) float[h->N];
+        float* tmp = new (std::nothrow) float[2 * h->N];
         if (!tmp) return fail(LBMP_ERR_NOMEM, "host allocation failed");
-        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, h->phi, sizeof(float) * h->N, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(tmp, h->phi, 2 * sizeof(float) * h->N, cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e == cudaSuccess)
-            for (long long i = 0; i < h->N; ++i) phi[i] = tmp[i];
+            for (long long i = 0; i < h->N; ++i) phi[i] = (double)tmp[i] + (double)tmp[h->N + i];
         delete[] tmp;
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

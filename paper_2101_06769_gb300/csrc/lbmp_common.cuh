@@ -133,25 +133,44 @@ __device__ __forceinline__ long long nbr_index(const DevParams& p, int a, int x,
     }
 }
 
-// Isotropic differences (Sec. 2.2) from the Q neighbour values nb[a] =
-// phi(x + c_a): grad_i = 3 sum w c_i phi(x+c), lap = 6 sum w (phi(x+c) - phi(x)).
-// The gradient is summed over opposite pairs so that it is exactly zero on a
-// uniform field.
+// phi = sum_a g_a (Sec. 2.2) is accumulated with an error-free transformation
+// (Knuth's TwoSum) and kept as an unevaluated pair hi + lo: the stencil below
+// differences neighbouring values of phi, and the chemical potential of a
+// near-equilibrium interface is a near-cancelling difference of its two
+// terms, so the half-ulp rounding of a plain FP32 sum would dominate the
+// FP32 error of the whole step.
+__device__ __forceinline__ void phi_add(float& hi, float& lo, float v)
+{
+    const float s = hi + v;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (v - bb);
+    hi = s;
+}
+__device__ __forceinline__ void phi_finish(float& hi, float& lo)
+{
+    const float s = hi + lo;
+    lo = lo - (s - hi);
+    hi = s;
+}
+
+// Isotropic differences (Sec. 2.2) from the Q neighbour values
+// phi(x + c_a) = nh[a] + nl[a]: grad_i = 3 sum w c_i phi(x+c),
+// lap = 6 sum w (phi(x+c) - phi(x)).  The gradient is summed over opposite
+// pairs so that it is exactly zero on a uniform field.
 template <int D>
-__device__ __forceinline__ void stencil_from_nb(const float* nb, float grad[3], float& lap)
+__device__ __forceinline__ void stencil_from_nb(const float* nh, const float* nl, float grad[3], float& lap)
 {
     constexpr int Q = Lat<D>::Q;
     constexpr int C = Q / 2;
-    const float pc = nb[C];
     float gx = 0.f, gy = 0.f, gz = 0.f, ls = 0.f;
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         if (a == C) continue;
-        ls += Lat<D>::w(a) * (nb[a] - pc);
+        ls += Lat<D>::w(a) * ((nh[a] - nh[C]) + (nl[a] - nl[C]));
     }
 #pragma unroll
     for (int a = 0; a < C; ++a) {
-        const float d = Lat<D>::w(a) * (nb[a] - nb[Q - 1 - a]);
+        const float d = Lat<D>::w(a) * ((nh[a] - nh[Q - 1 - a]) + (nl[a] - nl[Q - 1 - a]));
         if (Lat<D>::cx(a)) gx += Lat<D>::cx(a) * d;
         if (Lat<D>::cy(a)) gy += Lat<D>::cy(a) * d;
         if (Lat<D>::cz(a)) gz += Lat<D>::cz(a) * d;
@@ -162,35 +181,46 @@ __device__ __forceinline__ void stencil_from_nb(const float* nb, float grad[3], 
     lap = 6.f * ls;
 }
 
-
 // ------------------------------------------------------ flow collision
 // Moments of the pre-collision f': P, J, and the second moments Pi_ij.
 struct FlowMoments {
-    float P, J[3];
+    float P, Plo, J[3];  // P + Plo: compensated sum of the populations
     float Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;
 };
 
+// Moments of the Q pre-collision values f[a].  J is summed over opposite
+// pairs, c_a (f_a - f_opp(a)): the O(w p_h) part common to both members of a
+// pair cancels exactly before the sum, so the small momentum of a light phase
+// (density ratio up to 1000) is not buried under the pressure in FP32.
 template <int D>
-__device__ __forceinline__ void accumulate_moments(FlowMoments& m, int a, float v)
+__device__ __forceinline__ void flow_moments(FlowMoments& m, const float* f)
 {
-    const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
-    m.P += v;
-    if (cx) m.J[0] += cx * v;
-    if (cy) m.J[1] += cy * v;
-    if (cz) m.J[2] += cz * v;
-    if (cx) m.Pxx += v;
-    if (cy) m.Pyy += v;
-    if (cz) m.Pzz += v;
-    if (cx * cy) m.Pxy += (cx * cy) * v;
-    if (cx * cz) m.Pxz += (cx * cz) * v;
-    if (cy * cz) m.Pyz += (cy * cz) * v;
+    constexpr int Q = Lat<D>::Q;
+    constexpr int C = Q / 2;
+    m.P = 0.f;
+    m.Plo = 0.f;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) phi_add(m.P, m.Plo, f[a]);
+    phi_finish(m.P, m.Plo);
+    m.J[0] = m.J[1] = m.J[2] = 0.f;
+    m.Pxx = m.Pyy = m.Pzz = m.Pxy = m.Pxz = m.Pyz = 0.f;
+#pragma unroll
+    for (int a = 0; a < C; ++a) {
+        const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
+        const float d = f[a] - f[Q - 1 - a];
+        const float s = f[a] + f[Q - 1 - a];
+        if (cx) m.J[0] += cx * d;
+        if (cy) m.J[1] += cy * d;
+        if (cz) m.J[2] += cz * d;
+        if (cx) m.Pxx += s;
+        if (cy) m.Pyy += s;
+        if (cz) m.Pzz += s;
+        if (cx * cy) m.Pxy += (cx * cy) * s;
+        if (cx * cz) m.Pxz += (cx * cz) * s;
+        if (cy * cz) m.Pyz += (cy * cz) * s;
+    }
 }
 
-__device__ __forceinline__ void zero_moments(FlowMoments& m)
-{
-    m.P = m.J[0] = m.J[1] = m.J[2] = 0.f;
-    m.Pxx = m.Pyy = m.Pzz = m.Pxy = m.Pxz = m.Pyz = 0.f;
-}
 
 // Per-cell results of the collision set-up that the output loops need.
 struct CellState {
@@ -198,11 +228,10 @@ struct CellState {
     float n[3];        // interface normal
     float rcs2;        // rho cs2
     float ph;          // p_h = P + sum(Xi)/2
-    float V[3], uV;    // V = cs2 grad(rho) + F
+    float F[3], uF;    // force density F = F_s + F_b
     float G[3], uG;    // G = cs2 grad(rho)
     float uu;          // |u|^2
     float ew[3][3];    // per-axis product-equilibrium deviation e_d(c) - w1(c), [axis][c+1]
-    float ef[3][3];    // per-axis product-equilibrium e_d(c), [axis][c+1]
     float phi, sharp;  // phi and lambda_phi 4 phi (1-phi)/W
 };
 
@@ -225,7 +254,7 @@ __device__ __forceinline__ void flow_collide(const DevParams& p, float phi, cons
 
     // interface normal, chemical potential, force
     const float g2 = grad[0] * grad[0] + grad[1] * grad[1] + (D == 3 ? grad[2] * grad[2] : 0.f);
-    const float inv_g = 1.0f / fmaxf(sqrtf(g2), 1e-12f);
+    const float inv_g = 1.0f / fmaxf(sqrtf(g2), 1e-4f);
     const float mu = p.beta2 * phi * (phi - 1.0f) * (2.0f * phi - 1.0f) - p.kappa * lap;
     float F[3];
     F[0] = mu * grad[0];
@@ -237,33 +266,36 @@ __device__ __forceinline__ void flow_collide(const DevParams& p, float phi, cons
         F[D - 1] -= (rho - p.rho_bar) * p.g_accel;
 
     // u = J/(rho cs2) + F/(2 rho)
+    float V[3];
     for (int i = 0; i < 3; ++i) {
         s.u[i] = (D == 2 && i == 2) ? 0.f : (3.0f * m.J[i] + 0.5f * F[i]) * inv_rho;
         s.n[i] = (D == 2 && i == 2) ? 0.f : grad[i] * inv_g;
-        s.G[i] = (D == 2 && i == 2) ? 0.f : kCs2 * p.drho * grad[i];
-        s.V[i] = s.G[i] + F[i];
+        s.G[i] = (D == 2 && i == 2) ? 0.f : p.drho * grad[i] / 3.0f;
+        s.F[i] = F[i];
+        V[i] = s.G[i] + F[i];
     }
     const float ux = s.u[0], uy = s.u[1], uz = s.u[2];
     s.uG = ux * s.G[0] + uy * s.G[1] + uz * s.G[2];
-    s.uV = ux * s.V[0] + uy * s.V[1] + uz * s.V[2];
+    s.uF = ux * F[0] + uy * F[1] + uz * F[2];
+    const float uV = s.uG + s.uF;
     s.uu = ux * ux + uy * uy + uz * uz;
-    s.rcs2 = kCs2 * rho;
+    s.rcs2 = rho / 3.0f;
     s.ph = m.P + 0.5f * s.uG;
     s.phi = phi;
     s.sharp = p.lam_sharp * phi * (1.0f - phi);
 
-    // second moments of f^p minus theta cs2 delta, times rho cs2:
-    // Pi_ij - cs2 P delta_ij + [cs2 (u_i V_j + u_j V_i) - u_i u_j u.V]/2
-    const float hV = 0.5f * s.uV;
-    const float c3 = 3.0f * inv_rho;  // 1/(rho cs2)
-    float dxx = c3 * (m.Pxx - kCs2 * m.P + kCs2 * ux * s.V[0] - ux * ux * hV) - ux * ux;
-    float dyy = c3 * (m.Pyy - kCs2 * m.P + kCs2 * uy * s.V[1] - uy * uy * hV) - uy * uy;
-    float dxy = c3 * (m.Pxy + 0.5f * kCs2 * (ux * s.V[1] + uy * s.V[0]) - ux * uy * hV) - ux * uy;
+    // second moments of f^p minus theta cs2 delta, i.e. with 1/cs2 = 3:
+    // [3 Pi_ij - P delta_ij + (u_i V_j + u_j V_i)/2 - 3 u_i u_j u.V/2] / rho - u_i u_j
+    // (cs2 itself never enters as a rounded constant)
+    const float hV3 = 1.5f * uV;
+    float dxx = (3.0f * m.Pxx - m.P + ux * V[0] - ux * ux * hV3) * inv_rho - ux * ux;
+    float dyy = (3.0f * m.Pyy - m.P + uy * V[1] - uy * uy * hV3) * inv_rho - uy * uy;
+    float dxy = (3.0f * m.Pxy + 0.5f * (ux * V[1] + uy * V[0]) - ux * uy * hV3) * inv_rho - ux * uy;
     float dzz = 0.f, dxz = 0.f, dyz = 0.f;
     if (D == 3) {
-        dzz = c3 * (m.Pzz - kCs2 * m.P + kCs2 * uz * s.V[2] - uz * uz * hV) - uz * uz;
-        dxz = c3 * (m.Pxz + 0.5f * kCs2 * (ux * s.V[2] + uz * s.V[0]) - ux * uz * hV) - ux * uz;
-        dyz = c3 * (m.Pyz + 0.5f * kCs2 * (uy * s.V[2] + uz * s.V[1]) - uy * uz * hV) - uy * uz;
+        dzz = (3.0f * m.Pzz - m.P + uz * V[2] - uz * uz * hV3) * inv_rho - uz * uz;
+        dxz = (3.0f * m.Pxz + 0.5f * (ux * V[2] + uz * V[0]) - ux * uz * hV3) * inv_rho - ux * uz;
+        dyz = (3.0f * m.Pyz + 0.5f * (uy * V[2] + uz * V[1]) - uy * uz * hV3) * inv_rho - uy * uz;
     }
     // cumulant relaxation: shear rate on off-diagonal and deviatoric parts,
     // trace to D cs2 (rate one), every higher cumulant to zero (rate one)
@@ -277,9 +309,6 @@ __device__ __forceinline__ void flow_collide(const DevParams& p, float phi, cons
         s.ew[i][0] = 0.5f * (u2 - ui);
         s.ew[i][1] = -u2;
         s.ew[i][2] = 0.5f * (u2 + ui);
-        s.ef[i][0] = (float)(1.0 / 6.0) + s.ew[i][0];
-        s.ef[i][1] = (float)(2.0 / 3.0) + s.ew[i][1];
-        s.ef[i][2] = (float)(1.0 / 6.0) + s.ew[i][2];
     }
 
     // post-collision central-moment differences (Gaussian closure minus the
@@ -346,28 +375,31 @@ __device__ __forceinline__ void flow_collide(const DevParams& p, float phi, cons
     for (int i = 0; i < 27; ++i) dh[i] = k[i];
 }
 
-// Second-order Hermite equilibrium f_eq/rho (App. A) for direction a.
+// Deviation of the second-order Hermite equilibrium f_eq/rho (App. A) from
+// its rest value: Gamma_a - w_a = w_a [c.u/cs2 + ((c.u)^2 - cs2 u^2)/(2 cs4)].
 template <int D>
-__device__ __forceinline__ float gamma_eq(const CellState& s, int a)
+__device__ __forceinline__ float gamma_dev(const CellState& s, int a)
 {
     const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
     const float cu = cx * s.u[0] + cy * s.u[1] + cz * s.u[2];
-    return Lat<D>::w(a) * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * s.uu);
+    return Lat<D>::w(a) * (3.0f * cu + 4.5f * cu * cu - 1.5f * s.uu);
 }
 
 // Post-collision f'*_a = rho cs2 (h*_a - w_a) + w_a p_h + Xi_a/2 with
-// h* - w = (E(u) - w) + dh and Xi_a = Gamma_a (c_a - u).V - w_a (c_a - u).G.
+// h* - w = (E(u) - w) + dh and the source (Sec. 2.3, reading A6)
+//   Xi_a = cs2 (Gamma_a - w_a)(c_a - u).grad(rho) + Gamma_a (c_a - u).F,
+// both terms formed from small factors (no O(w |grad rho|) cancellation).
 template <int D>
-__device__ __forceinline__ float flow_post(const CellState& s, const float dh[27], int a, float gam)
+__device__ __forceinline__ float flow_post(const CellState& s, const float dh[27], int a, float gdev)
 {
     const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
     const float w = Lat<D>::w(a);
-    const float cV = cx * s.V[0] + cy * s.V[1] + cz * s.V[2] - s.uV;
     const float cG = cx * s.G[0] + cy * s.G[1] + cz * s.G[2] - s.uG;
-    const float xi = gam * cV - w * cG;
+    const float cF = cx * s.F[0] + cy * s.F[1] + cz * s.F[2] - s.uF;
+    const float xi = gdev * cG + (w + gdev) * cF;
     // telescoped E - w = e_x e_y e_z - w_x w_y w_z
-    const float wx = (float)w1d(cx), wy = (float)w1d(cy), wz = (float)w1d(cz);
-    const float ex = s.ef[0][cx + 1], ey = s.ef[1][cy + 1];
+    const float wy = (float)w1d(cy), wz = (float)w1d(cz);
+    const float ex = (float)w1d(cx) + s.ew[0][cx + 1], ey = wy + s.ew[1][cy + 1];
     float ew;
     if (D == 3)
         ew = s.ew[0][cx + 1] * wy * wz + ex * s.ew[1][cy + 1] * wz + ex * ey * s.ew[2][cz + 1];
@@ -377,13 +409,65 @@ __device__ __forceinline__ float flow_post(const CellState& s, const float dh[27
 }
 
 // Phase-field BGK with the sharpening source (Sec. 2.2, readings A3-A5):
-// g* = g - (g - phi Gamma)/tau + lambda w (c.n) 4 phi (1-phi)/W
+// g* = g + (phi Gamma - g)/tau + lambda w (c.n) 4 phi (1-phi)/W
 template <int D>
-__device__ __forceinline__ float phase_post(const DevParams& p, const CellState& s, int a, float g, float gam)
+__device__ __forceinline__ float phase_post(const DevParams& p, const CellState& s, int a, float g, float gdev)
 {
     const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
+    const float w = Lat<D>::w(a);
     const float cn = cx * s.n[0] + cy * s.n[1] + cz * s.n[2];
-    return g + p.inv_tau_phi * (s.phi * gam - g) + Lat<D>::w(a) * cn * s.sharp;
+    return g + p.inv_tau_phi * (s.phi * (w + gdev) - g) + w * cn * s.sharp;
+}
+
+// All post-collision populations of one cell.  The moving populations follow
+// the formulas above; the rest population (a = Q/2) is formed last from the
+// exact conservation identities of the collision,
+//   sum_a g*_a = sum_a g_a                     (sum S_bar = 0, sum g_eq = phi)
+//   sum_a f'*_a = sum_a f'_a + cs2 u.grad(rho)  (sum Xi = cs2 u.grad(rho)),
+// with compensated sums, so that the FP32 rounding of the weights (their
+// float values sum to 1 + 7.45e-9) cannot bias mass or pressure step after
+// step.  In exact arithmetic this is the same value as the formula.
+// Sources of the pre-collision g (register array, or a strided shared-memory
+// column) and destinations of the post-collision values (strided SoA).
+struct GFromArray {
+    const float* v;
+    __device__ __forceinline__ float operator()(int a) const { return v[a]; }
+};
+struct GFromStrided {
+    const float* base;
+    int stride;
+    __device__ __forceinline__ float operator()(int a) const { return base[a * stride]; }
+};
+struct SoAOut {
+    float* base;
+    long long stride;
+    __device__ __forceinline__ void operator()(int a, float v) const { base[a * stride] = v; }
+};
+
+template <int D, class GSrc, class Out>
+__device__ __forceinline__ void collide_outputs(const DevParams& p, const CellState& s, const float dh[27],
+                                                const FlowMoments& m, const GSrc& gin, float gsum_hi,
+                                                float gsum_lo, const Out& fout, const Out& gout)
+{
+    constexpr int Q = Lat<D>::Q;
+    constexpr int C = Q / 2;
+    float fh = 0.f, fl = 0.f, gh = 0.f, gl = 0.f;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        if (a == C) continue;
+        const float gd = gamma_dev<D>(s, a);
+        const float fv = flow_post<D>(s, dh, a, gd);
+        const float gv = phase_post<D>(p, s, a, gin(a), gd);
+        fout(a, fv);
+        gout(a, gv);
+        phi_add(fh, fl, fv);
+        phi_add(gh, gl, gv);
+    }
+    // target totals: P + u.G (flow) and the incoming sum (phase field)
+    float th = m.P, tl = m.Plo;
+    phi_add(th, tl, s.uG);
+    fout(C, (th - fh) + (tl - fl));
+    gout(C, (gsum_hi - gh) + (gsum_lo - gl));
 }
 
 }  // namespace lbmp

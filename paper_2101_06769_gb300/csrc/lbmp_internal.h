@@ -20,7 +20,7 @@ struct lbmp_handle {
     // previous step (pull streaming reads them upstream)
     float* f[2];
     float* g[2];
-    float* phi;        // phi = sum g, refreshed by the phi pass
+    float* phi;        // phi = sum g as hi [0, N) + lo [N, 2N), refreshed by the phi pass
     int parity;        // f[parity], g[parity] hold the current state
     long step;
     int kernel;        // LBMP_OPT_KERNEL

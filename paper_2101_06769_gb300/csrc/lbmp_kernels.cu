@@ -19,10 +19,12 @@ __global__ void phi_pass_kernel(DevParams p, const float* __restrict__ g, float*
     if (i >= p.N) return;
     int x, y, z;
     cell_xyz(p, i, x, y, z);
-    float s = 0.f;
+    float hi = 0.f, lo = 0.f;
 #pragma unroll
-    for (int a = 0; a < Lat<D>::Q; ++a) s += g[pull_index<D>(p, a, x, y, z, i)];
-    phi[i] = s;  // phi = sum_a g_a (Sec. 2.2)
+    for (int a = 0; a < Lat<D>::Q; ++a) phi_add(hi, lo, g[pull_index<D>(p, a, x, y, z, i)]);
+    phi_finish(hi, lo);
+    phi[i] = hi;  // phi = sum_a g_a (Sec. 2.2), as hi + lo
+    phi[p.N + i] = lo;
 }
 
 // ----------------------------------------------------- reference step
@@ -36,25 +38,28 @@ __global__ void __launch_bounds__(128) step_simple_kernel(DevParams p, const flo
     if (i >= p.N) return;
     int x, y, z;
     cell_xyz(p, i, x, y, z);
-    float nb[Q];
-#pragma unroll
-    for (int a = 0; a < Q; ++a) nb[a] = phi[nbr_index<D>(p, a, x, y, z)];
-    float grad[3], lap;
-    stencil_from_nb<D>(nb, grad, lap);
-    FlowMoments m;
-    zero_moments(m);
-#pragma unroll
-    for (int a = 0; a < Q; ++a) accumulate_moments<D>(m, a, fin[pull_index<D>(p, a, x, y, z, i)]);
-    CellState s;
-    float dh[27];
-    flow_collide<D>(p, nb[Q / 2], grad, lap, m, s, dh);
-#pragma unroll
-    for (int a = 0; a < Q; ++a) fout[(long long)a * p.N + i] = flow_post<D>(s, dh, a, gamma_eq<D>(s, a));
+    float nh[Q], nl[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        const float gv = gin[pull_index<D>(p, a, x, y, z, i)];
-        gout[(long long)a * p.N + i] = phase_post<D>(p, s, a, gv, gamma_eq<D>(s, a));
+        const long long j = nbr_index<D>(p, a, x, y, z);
+        nh[a] = phi[j];
+        nl[a] = phi[p.N + j];
     }
+    float grad[3], lap;
+    stencil_from_nb<D>(nh, nl, grad, lap);
+    float fr[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) fr[a] = fin[pull_index<D>(p, a, x, y, z, i)];
+    FlowMoments m;
+    flow_moments<D>(m, fr);
+    CellState s;
+    float dh[27];
+    flow_collide<D>(p, nh[Q / 2], grad, lap, m, s, dh);
+    float gr[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) gr[a] = gin[pull_index<D>(p, a, x, y, z, i)];
+    collide_outputs<D>(p, s, dh, m, GFromArray{gr}, nh[Q / 2], nl[Q / 2], SoAOut{fout + i, p.N},
+                       SoAOut{gout + i, p.N});
 }
 
 static unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
@@ -97,7 +102,7 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed
 
 struct InitArgs {
     double a[8];
-    double W, rho_l, rho_h, sigma, U_ref;
+    double W, rho_l, rho_h, sigma, U_ref, g;
     unsigned long long seed;
     int case_id;
 };
@@ -125,6 +130,13 @@ __global__ void init_kernel(DevParams p, InitArgs A, float* __restrict__ f, floa
         if (D == 3) hh += A.a[1] * cos(2.0 * PI * y / n[1]);
         phi = tanh_prof(hv - hh, A.W);
         noise = A.a[2];
+        if (A.a[3] != 0.0) {
+            // hydrostatic start: dp/dz = -(rho - rho_bar) g along the column, i.e.
+            // p = -g (rho_h - rho_l) (W/4) ln cosh(2 (z - h)/W), zero at the interface
+            const double t = fabs(2.0 * (hv - hh) / A.W);
+            const double lncosh = t + log1p(exp(-2.0 * t)) - log(2.0);
+            pr = -A.g * (A.rho_h - A.rho_l) * 0.25 * A.W * lncosh;
+        }
         break;
     }
     case LBMP_CASE_DROP_STATIC: {
@@ -204,6 +216,7 @@ cudaError_t launch_init(lbmp_handle* h, int case_id, const double* args, unsigne
     A.rho_h = h->der.rho_h;
     A.sigma = h->der.sigma;
     A.U_ref = h->der.U_ref;
+    A.g = h->der.g_accel;
     A.seed = seed;
     A.case_id = case_id;
     const int B = 128;
@@ -267,19 +280,24 @@ __device__ void cell_macro(const DevParams& p, const float* __restrict__ f, cons
                            int y, int z, long long i, float& rho, float u[3], float& ph)
 {
     constexpr int Q = Lat<D>::Q;
-    float nb[Q];
+    float nh[Q], nl[Q];
 #pragma unroll
-    for (int a = 0; a < Q; ++a) nb[a] = phi[nbr_index<D>(p, a, x, y, z)];
+    for (int a = 0; a < Q; ++a) {
+        const long long j = nbr_index<D>(p, a, x, y, z);
+        nh[a] = phi[j];
+        nl[a] = phi[p.N + j];
+    }
     float grad[3], lap;
-    stencil_from_nb<D>(nb, grad, lap);
-    FlowMoments m;
-    zero_moments(m);
+    stencil_from_nb<D>(nh, nl, grad, lap);
+    float fr[Q];
 #pragma unroll
-    for (int a = 0; a < Q; ++a) accumulate_moments<D>(m, a, f[pull_index<D>(p, a, x, y, z, i)]);
+    for (int a = 0; a < Q; ++a) fr[a] = f[pull_index<D>(p, a, x, y, z, i)];
+    FlowMoments m;
+    flow_moments<D>(m, fr);
     CellState s;
     float dh[27];
-    flow_collide<D>(p, nb[Q / 2], grad, lap, m, s, dh);
-    rho = p.rho_l + p.drho * nb[Q / 2];
+    flow_collide<D>(p, nh[Q / 2], grad, lap, m, s, dh);
+    rho = p.rho_l + p.drho * nh[Q / 2];
     for (int k = 0; k < 3; ++k) u[k] = s.u[k];
     ph = s.ph;
 }
@@ -298,7 +316,7 @@ __global__ void __launch_bounds__(256) obs_partial_kernel(DevParams p, const flo
         float rho, u[3], ph;
         cell_macro<D>(p, f, phi, x, y, z, i, rho, u, ph);
         const double uu = (double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2];
-        const double ph_i = phi[i];
+        const double ph_i = (double)phi[i] + (double)phi[p.N + i];
         mass += ph_i;
         ke += 0.5 * rho * uu;
         const double un = sqrt(uu);
@@ -405,8 +423,8 @@ __global__ void column_kernel(DevParams p, const float* __restrict__ phi, double
         is = (long long)k * p.nx + p.nx / 2;
         ib = (long long)k * p.nx;
     }
-    out[k] = phi[is];
-    out[nv + k] = phi[ib];
+    out[k] = (double)phi[is] + (double)phi[p.N + is];
+    out[nv + k] = (double)phi[ib] + (double)phi[p.N + ib];
 }
 
 cudaError_t launch_observables(lbmp_handle* h, double* dev_out)

@@ -22,12 +22,12 @@ CASES = {
     "rt2d": dict(D=2, dims=(64, 256, 1), periodic=(1, 0, 1),
                  phys=dict(atwood=0.5, nu_ratio=1.0, Re=256.0, g_accel=2.5e-5, L_ref=64.0,
                            mobility=0.02, width=5.0),
-                 case="rt", args=[128.0, 6.4, 1e-4], seed=1),
+                 case="rt", args=[128.0, 6.4, 1e-4, 1.0], seed=1),
     # reduced 3-D Rayleigh-Taylor (same non-dimensional set-up, 32 x 32 x 64)
     "rt3d": dict(D=3, dims=(32, 32, 64), periodic=(1, 1, 0),
                  phys=dict(atwood=0.5, nu_ratio=1.0, Re=1024.0, g_accel=5e-5, L_ref=32.0,
                            mobility=0.02, width=5.0),
-                 case="rt", args=[32.0, 3.2, 1e-4], seed=2),
+                 case="rt", args=[32.0, 3.2, 1e-4, 1.0], seed=2),
     # reduced droplet-on-sheet splash, density ratio 1000, viscosity ratio 15, We 8000, Re 1000
     "splash3d": dict(D=3, dims=(64, 64, 32), periodic=(1, 1, 0),
                      phys=dict(rho_ratio=1000.0, nu_ratio=15.0, We=8000.0, Re=1000.0, U0=0.05,
@@ -47,12 +47,12 @@ CASES = {
     "ragged2d": dict(D=2, dims=(33, 47, 1), periodic=(1, 0, 1),
                      phys=dict(rho_ratio=10.0, nu_ratio=5.0, nu_h=0.02, sigma=5e-3, g_accel=1e-5,
                                mobility=0.03, width=4.0, flags=2),
-                     case="rt", args=[23.0, 3.0, 1e-2], seed=6),
+                     case="rt", args=[23.0, 3.0, 1e-2, 1.0], seed=6),
     # thin 3-D with walls: every thread block touches a wall plane
     "thin3d": dict(D=3, dims=(8, 6, 5), periodic=(1, 1, 0),
                    phys=dict(rho_ratio=3.0, nu_ratio=1.0, nu_h=0.05, sigma=1e-2, g_accel=1e-4,
                              mobility=0.02, width=3.0),
-                   case="rt", args=[2.0, 0.5, 1e-2], seed=7),
+                   case="rt", args=[2.0, 0.5, 1e-2, 1.0], seed=7),
 }
 
 
@@ -173,7 +173,7 @@ def test_full_size_rt3d_init_and_two_steps():
     dims = (128, 128, 512)
     phys = dict(atwood=0.5, nu_ratio=1.0, Re=1024.0, g_accel=1.25e-5, L_ref=128.0, mobility=0.02,
                 width=5.0)
-    args = [256.0, 12.8, 1e-4]
+    args = [256.0, 12.8, 1e-4, 1.0]
     o = O.Oracle(3, dims, (1, 1, 0), **phys)
     o.init("rt", args, seed=11)
     d = Domain(3, dims, (1, 1, 0), **phys)
