@@ -176,6 +176,22 @@ LBMP_API int lbmp_download(lbmp_handle *h, void *host, size_t bytes);
 enum { LBMP_OPT_KERNEL = 0 };
 LBMP_API int lbmp_set_option(lbmp_handle *h, int option, long value);
 
+/* Mass without allocation (the paper has no counterpart: this is a service
+ * of the library).  For callers that cannot allocate device memory, e.g. a
+ * host framework that owns every byte of device memory and hands out only
+ * views into its pool, or a fixed-budget real-time loop: returns in *mass_out
+ * the FP64 sum of n_values FP32 device values g_dev, the total mass
+ * sum_x phi(x) when g_dev holds a phase-field population set (the total over
+ * all populations of all cells does not depend on their layout).  Uses a
+ * fixed 32 KiB device array compiled into the library instead of scratch
+ * memory and calls no allocating routine.  At most 2^33 values (else
+ * LBMP_ERR_INVALID_ARG).  Ordered on cuda_stream (NULL = legacy default
+ * stream) and synchronises it.  The first call on a device looks up the
+ * array's address with that device current: make it before any stream
+ * capture.  Every call on a device shares the array, so calls that overlap on
+ * the GPU race: serialise them. */
+LBMP_API int lbmp_mass_noalloc(const float *g_dev, long long n_values, double *mass_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -127,6 +127,10 @@ int check_handle(const lbmp_handle* h)
 
 }  // namespace
 
+namespace lbmp {
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace lbmp
+
 extern "C" {
 
 const char* lbmp_last_error(void) { return g_msg; }

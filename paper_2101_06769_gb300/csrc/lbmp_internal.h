@@ -45,5 +45,7 @@ cudaError_t launch_get_state(lbmp_handle* h, double* dev_f, double* dev_g);
 cudaError_t launch_observables(lbmp_handle* h, double* dev_out);
 cudaError_t launch_mass(lbmp_handle* h, double* dev_out4);  // writes 4 doubles, [0] = mass
 bool fused_supported(const lbmp_handle* h);
+// record a message for lbmp_last_error() and return code
+int set_error(int code, const char* msg);
 
 }  // namespace lbmp

@@ -25,7 +25,7 @@ ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5
 # every entry point declared in include/lbmp.h
 EXPORTS = ("lbmp_create", "lbmp_destroy", "lbmp_last_error", "lbmp_get_derived", "lbmp_init",
            "lbmp_step", "lbmp_sync", "lbmp_observables", "lbmp_get_state", "lbmp_set_state",
-           "lbmp_state_bytes", "lbmp_upload", "lbmp_download", "lbmp_set_option")
+           "lbmp_state_bytes", "lbmp_upload", "lbmp_download", "lbmp_set_option", "lbmp_mass_noalloc")
 
 
 class Grid(C.Structure):
@@ -88,6 +88,7 @@ def load(path=None):
     L.lbmp_upload.argtypes = [vp, vp, C.c_size_t]
     L.lbmp_download.argtypes = [vp, vp, C.c_size_t]
     L.lbmp_set_option.argtypes = [vp, C.c_int, C.c_long]
+    L.lbmp_mass_noalloc.argtypes = [vp, C.c_longlong, C.POINTER(C.c_double), vp]
     _lib = L
     return L
 
