@@ -133,22 +133,30 @@ __device__ __forceinline__ long long nbr_index(const DevParams& p, int a, int x,
     }
 }
 
-// phi = sum_a g_a (Sec. 2.2) is accumulated with an error-free transformation
-// (Knuth's TwoSum) and kept as an unevaluated pair hi + lo: the stencil below
-// differences neighbouring values of phi, and the chemical potential of a
-// near-equilibrium interface is a near-cancelling difference of its two
-// terms, so the half-ulp rounding of a plain FP32 sum would dominate the
-// FP32 error of the whole step.
-__device__ __forceinline__ void phi_add(float& hi, float& lo, float v)
+// phi = sum_a g_a (Sec. 2.2) is accumulated as an unevaluated pair hi + lo:
+// the stencil below differences neighbouring values of phi, and the chemical
+// potential of a near-equilibrium interface is a near-cancelling difference
+// of its two terms, so the half-ulp rounding of a plain FP32 sum would
+// dominate the FP32 error of the whole step.  The rest population (the
+// largest, w = 8/27 or 4/9 of phi) is added first and every later term is
+// smaller than the running sum, so Dekker's Fast2Sum recovers each rounding
+// error exactly with three additions.
+template <int D, class Get>
+__device__ __forceinline__ void phi_sum(const Get& get, float& hi, float& lo)
 {
-    const float s = hi + v;
-    const float bb = s - hi;
-    lo += (hi - (s - bb)) + (v - bb);
-    hi = s;
-}
-__device__ __forceinline__ void phi_finish(float& hi, float& lo)
-{
-    const float s = hi + lo;
+    constexpr int Q = Lat<D>::Q;
+    constexpr int C = Q / 2;
+    hi = get(C);
+    lo = 0.f;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        if (a == C) continue;
+        const float v = get(a);
+        const float s = hi + v;
+        lo += v - (s - hi);
+        hi = s;
+    }
+    const float s = hi + lo;  // renormalise: |lo| <= ulp(hi)/2
     lo = lo - (s - hi);
     hi = s;
 }
@@ -184,7 +192,7 @@ __device__ __forceinline__ void stencil_from_nb(const float* nh, const float* nl
 // ------------------------------------------------------ flow collision
 // Moments of the pre-collision f': P, J, and the second moments Pi_ij.
 struct FlowMoments {
-    float P, Plo, J[3];  // P + Plo: compensated sum of the populations
+    float P, J[3];
     float Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;
 };
 
@@ -197,11 +205,7 @@ __device__ __forceinline__ void flow_moments(FlowMoments& m, const float* f)
 {
     constexpr int Q = Lat<D>::Q;
     constexpr int C = Q / 2;
-    m.P = 0.f;
-    m.Plo = 0.f;
-#pragma unroll
-    for (int a = 0; a < Q; ++a) phi_add(m.P, m.Plo, f[a]);
-    phi_finish(m.P, m.Plo);
+    m.P = f[C];
     m.J[0] = m.J[1] = m.J[2] = 0.f;
     m.Pxx = m.Pyy = m.Pzz = m.Pxy = m.Pxz = m.Pyz = 0.f;
 #pragma unroll
@@ -209,6 +213,7 @@ __device__ __forceinline__ void flow_moments(FlowMoments& m, const float* f)
         const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
         const float d = f[a] - f[Q - 1 - a];
         const float s = f[a] + f[Q - 1 - a];
+        m.P += s;
         if (cx) m.J[0] += cx * d;
         if (cy) m.J[1] += cy * d;
         if (cz) m.J[2] += cz * d;
@@ -424,9 +429,9 @@ __device__ __forceinline__ float phase_post(const DevParams& p, const CellState&
 // exact conservation identities of the collision,
 //   sum_a g*_a = sum_a g_a                     (sum S_bar = 0, sum g_eq = phi)
 //   sum_a f'*_a = sum_a f'_a + cs2 u.grad(rho)  (sum Xi = cs2 u.grad(rho)),
-// with compensated sums, so that the FP32 rounding of the weights (their
-// float values sum to 1 + 7.45e-9) cannot bias mass or pressure step after
-// step.  In exact arithmetic this is the same value as the formula.
+// so that the FP32 rounding of the weights (their float values sum to
+// 1 + 7.45e-9) cannot bias mass or pressure step after step; what remains
+// is unbiased round-off.  In exact arithmetic this is the value of the formula.
 // Sources of the pre-collision g (register array, or a strided shared-memory
 // column) and destinations of the post-collision values (strided SoA).
 struct GFromArray {
@@ -437,6 +442,11 @@ struct GFromStrided {
     const float* base;
     int stride;
     __device__ __forceinline__ float operator()(int a) const { return base[a * stride]; }
+};
+struct PtrOut {  // per-direction array bases, one cell index
+    float* const* base;
+    int self;
+    __device__ __forceinline__ void operator()(int a, float v) const { base[a][self] = v; }
 };
 struct SoAOut {
     float* base;
@@ -451,7 +461,7 @@ __device__ __forceinline__ void collide_outputs(const DevParams& p, const CellSt
 {
     constexpr int Q = Lat<D>::Q;
     constexpr int C = Q / 2;
-    float fh = 0.f, fl = 0.f, gh = 0.f, gl = 0.f;
+    float fs = 0.f, gs = 0.f, gl = 0.f;
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         if (a == C) continue;
@@ -460,14 +470,17 @@ __device__ __forceinline__ void collide_outputs(const DevParams& p, const CellSt
         const float gv = phase_post<D>(p, s, a, gin(a), gd);
         fout(a, fv);
         gout(a, gv);
-        phi_add(fh, fl, fv);
-        phi_add(gh, gl, gv);
+        fs += fv;
+        // TwoSum (Knuth): the mass sum keeps its rounding error exactly, so a
+        // uniform field, whose every cell would round the same way, cannot drift
+        const float t = gs + gv;
+        const float bb = t - gs;
+        gl += (gs - (t - bb)) + (gv - bb);
+        gs = t;
     }
     // target totals: P + u.G (flow) and the incoming sum (phase field)
-    float th = m.P, tl = m.Plo;
-    phi_add(th, tl, s.uG);
-    fout(C, (th - fh) + (tl - fl));
-    gout(C, (gsum_hi - gh) + (gsum_lo - gl));
+    fout(C, (m.P + s.uG) - fs);
+    gout(C, ((gsum_hi - gs) + (gsum_lo - gl)));
 }
 
 }  // namespace lbmp

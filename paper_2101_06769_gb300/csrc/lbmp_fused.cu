@@ -11,12 +11,17 @@
 // shared memory, summed for phi and kept for the collision of plane z+1; the
 // ring cells' g are loaded and summed by the first threads.  Because the step
 // reads one population set and writes the other, the ring reads cannot race
-// with the neighbouring tile's writes.  No phi field is stored, no separate
-// phi pass runs; the only bytes beyond "every population read once and
-// written once" are ring reads, which the neighbouring tiles fetch at about
-// the same time (mostly L2 hits), and one extra plane per chunk.
+// with the neighbouring tile's writes.  No phi field is stored and no
+// separate phi pass runs; the only bytes beyond "every population read once
+// and written once" are ring reads, which the neighbouring tiles fetch at
+// about the same time (mostly L2 hits), and one extra plane per chunk.
 //
-// The per-cell arithmetic (lbmp_common.cuh) and the summation orders are the
+// Addressing: the 27 per-direction array bases of the four population sets
+// are kernel parameters (constant bank); a pulled value is base[a] plus a
+// 32-bit cell index assembled from three per-axis neighbour offsets, so each
+// load costs an add and a wide multiply-add.
+//
+// The per-cell arithmetic (lbmp_common.cuh) and its summation orders are the
 // ones of the reference pair in lbmp_kernels.cu, so the two paths agree.
 #include "lbmp_internal.h"
 
@@ -26,18 +31,20 @@ namespace {
 
 constexpr int TX = 32, TY = 8, NT = TX * TY;
 constexpr int RX = TX + 2, RY = TY + 2;
+constexpr int PLANE = RY * RX;
 constexpr int NRING = 2 * RX + 2 * TY;
 constexpr int Q3 = 27;
-constexpr int PLANE = RY * RX;
-constexpr size_t kSmemBytes = sizeof(float) * (2 * Q3 * NT + 2 * 3 * PLANE);
+constexpr size_t kSmemBytes = sizeof(float) * (2 * Q3 * NT + Q3 * NRING + 2 * 3 * PLANE);
+
+struct DirPtrs {
+    const float* fin[Q3];
+    const float* gin[Q3];
+    float* fout[Q3];
+    float* gout[Q3];
+};
 
 struct FusedArgs {
-    const float* fin;
-    const float* gin;
-    float* fout;
-    float* gout;
-    int tiles_x, tiles_y, chunk, nchunks;
-    int nitems;
+    int tiles_x, tiles_y, chunk, nitems;
 };
 
 __device__ __forceinline__ void cp_async4(float* smem, const float* gmem)
@@ -54,6 +61,68 @@ __device__ __forceinline__ int pmod(int v, int n)
     return r < 0 ? r + n : r;
 }
 
+// A column (x, y) and its upstream neighbours: xs[c+1] = x - c and
+// ys[c+1] = (y - c) nx, wrapped periodically.
+struct Column {
+    int xs[3], ys[3];
+};
+
+__device__ __forceinline__ void set_column(Column& C, const DevParams& p, int x, int y)
+{
+    C.xs[0] = x + 1 == p.nx ? 0 : x + 1;
+    C.xs[1] = x;
+    C.xs[2] = x == 0 ? p.nx - 1 : x - 1;
+    C.ys[0] = (y + 1 == p.ny ? 0 : y + 1) * p.nx;
+    C.ys[1] = y * p.nx;
+    C.ys[2] = (y == 0 ? p.ny - 1 : y - 1) * p.nx;
+}
+
+// A plane z and its upstream planes zs[c+1] = (z - c) nx ny; lo/hi flag the
+// bottom/top plane of a walled domain, where the population arriving across
+// the wall is the opposite population of the cell itself (half-way
+// bounce-back).
+struct Plane {
+    int zs[3];
+    bool lo, hi;
+};
+
+__device__ __forceinline__ void set_plane(Plane& P, const DevParams& p, int z)
+{
+    const int nxy = p.nx * p.ny;
+    P.lo = !p.vert_periodic && z == 0;
+    P.hi = !p.vert_periodic && z == p.nz - 1;
+    P.zs[0] = (z + 1 == p.nz ? 0 : z + 1) * nxy;
+    P.zs[1] = z * nxy;
+    P.zs[2] = (z == 0 ? p.nz - 1 : z - 1) * nxy;
+}
+
+// pointer to the post-streaming population a of the cell (column C, plane P)
+template <int a>
+__device__ __forceinline__ const float* pulled(const float* const* base, const Column& C, const Plane& P)
+{
+    constexpr int cx = Lat<3>::cx(a), cy = Lat<3>::cy(a), cz = Lat<3>::cz(a);
+    if ((cz == 1 && P.lo) || (cz == -1 && P.hi)) return base[Lat<3>::opp(a)] + (P.zs[1] + C.ys[1] + C.xs[1]);
+    return base[a] + (P.zs[cz + 1] + C.ys[cy + 1] + C.xs[cx + 1]);
+}
+
+// compile-time loop over the directions (keeps base[a] a constant-bank operand)
+template <int N>
+struct Unroll {
+    template <class F>
+    __device__ __forceinline__ static void run(const F& f)
+    {
+        Unroll<N - 1>::run(f);
+        f.template step<N - 1>();
+    }
+};
+template <>
+struct Unroll<0> {
+    template <class F>
+    __device__ __forceinline__ static void run(const F&)
+    {
+    }
+};
+
 // plane whose phi stands for plane zz: periodic wrap, or the mirrored ghost
 // at a wall (reading A17)
 __device__ __forceinline__ int plane_src(const DevParams& p, int zz)
@@ -63,57 +132,88 @@ __device__ __forceinline__ int plane_src(const DevParams& p, int zz)
     return zz < 0 ? 0 : p.nz - 1;
 }
 
-struct Geo {
-    int tid, tx, ty, ox, oy;  // own column (wrapped for ragged tiles)
-    int rx, ry, rslot;        // ring column (tid < NRING) and its smem slot
+struct StageCopy {
+    const DirPtrs& D;
+    const Column& C;
+    const Plane& P;
+    float* gbuf;
+    template <int a>
+    __device__ __forceinline__ void step() const
+    {
+        cp_async4(gbuf + a * NT, pulled<a>(D.gin, C, P));
+    }
 };
 
-// phi on plane zz for the tile and its ring into phi_plane (hi at [0, PLANE),
-// lo at [3 PLANE, 4 PLANE)); the tile's own g(zz) lands in gbuf (kept for the
-// collision when zz is processed next).
-__device__ __forceinline__ void stage_plane(const DevParams& p, const FusedArgs& A, const Geo& G, int zz,
-                                            float* __restrict__ gbuf, float* __restrict__ phi_plane)
-{
-    const int zs = plane_src(p, zz);
-    const long long self = ((long long)zs * p.ny + G.oy) * p.nx + G.ox;
-#pragma unroll
-    for (int a = 0; a < Q3; ++a) cp_async4(gbuf + a * NT + G.tid, A.gin + pull_index<3>(p, a, G.ox, G.oy, zs, self));
-    cp_async_commit();
-    if (G.tid < NRING) {
-        const long long rself = ((long long)zs * p.ny + G.ry) * p.nx + G.rx;
-        float v[Q3];
-#pragma unroll
-        for (int a = 0; a < Q3; ++a) v[a] = __ldg(A.gin + pull_index<3>(p, a, G.rx, G.ry, zs, rself));
-        float hi = 0.f, lo = 0.f;
-#pragma unroll
-        for (int a = 0; a < Q3; ++a) phi_add(hi, lo, v[a]);
-        phi_finish(hi, lo);
-        phi_plane[G.rslot] = hi;
-        phi_plane[3 * PLANE + G.rslot] = lo;
+struct PullLoad {
+    const float* const* base;
+    const Column& C;
+    const Plane& P;
+    float* v;
+    template <int a>
+    __device__ __forceinline__ void step() const
+    {
+        v[a] = __ldg(pulled<a>(base, C, P));
     }
-    cp_async_wait_all();
-    float hi = 0.f, lo = 0.f;
-#pragma unroll
-    for (int a = 0; a < Q3; ++a) phi_add(hi, lo, gbuf[a * NT + G.tid]);
-    phi_finish(hi, lo);
-    const int own = (G.ty + 1) * RX + (G.tx + 1);
-    phi_plane[own] = hi;
-    phi_plane[3 * PLANE + own] = lo;
+};
+
+struct RingCopy {
+    const DirPtrs& D;
+    const Column& C;
+    const Plane& P;
+    float* rbuf;
+    template <int a>
+    __device__ __forceinline__ void step() const
+    {
+        cp_async4(rbuf + a * NRING, pulled<a>(D.gin, C, P));
+    }
+};
+
+// Staging of plane zz, in two halves so that other loads can be issued while
+// the copies are in flight.  issue: the tile's own g(zz) into gbuf (kept for
+// the collision of plane zz) and the ring cells' g(zz) into rbuf, both by
+// cp.async.  finish: wait, then phi (hi at [0, PLANE), lo at [3 PLANE,
+// 4 PLANE)) of every tile and ring cell into phi_plane.  Each thread sums
+// only the values it copied itself, so no barrier is needed in between.
+__device__ __forceinline__ void stage_issue(const DevParams& p, const DirPtrs& D, const Column& own,
+                                            const Column& ring, int tid, int zz, float* __restrict__ gbuf,
+                                            float* __restrict__ rbuf)
+{
+    Plane P;
+    set_plane(P, p, plane_src(p, zz));
+    Unroll<Q3>::run(StageCopy{D, own, P, gbuf + tid});
+    if (tid < NRING) Unroll<Q3>::run(RingCopy{D, ring, P, rbuf + tid});
+    cp_async_commit();
 }
 
-__global__ void __launch_bounds__(NT, 2) step_fused3_kernel(DevParams p, FusedArgs A)
+__device__ __forceinline__ void stage_finish(int tid, int oslot, int rslot, const float* __restrict__ gbuf,
+                                             const float* __restrict__ rbuf, float* __restrict__ phi_plane)
+{
+    cp_async_wait_all();
+    if (tid < NRING) {
+        float hi, lo;
+        phi_sum<3>([&](int a) { return rbuf[a * NRING + tid]; }, hi, lo);
+        phi_plane[rslot] = hi;
+        phi_plane[3 * PLANE + rslot] = lo;
+    }
+    float hi, lo;
+    phi_sum<3>([&](int a) { return gbuf[a * NT + tid]; }, hi, lo);
+    phi_plane[oslot] = hi;
+    phi_plane[3 * PLANE + oslot] = lo;
+}
+
+__global__ void __launch_bounds__(NT, 2) step_fused3_kernel(DevParams p, FusedArgs A, DirPtrs Dp)
 {
     extern __shared__ float smem[];
-    float* gS = smem;                  // [2][27][NT]
-    float* phiS = smem + 2 * Q3 * NT;  // hi [3][RY][RX], then lo [3][RY][RX]
+    float* gS = smem;                     // [2][27][NT]
+    float* rS = smem + 2 * Q3 * NT;       // [27][NRING] ring cells' g of the plane being staged
+    float* phiS = rS + Q3 * NRING;        // hi [3][RY][RX], then lo [3][RY][RX]
 
-    Geo G;
-    G.tid = threadIdx.x;
-    G.tx = G.tid % TX;
-    G.ty = G.tid / TX;
-    int lx = 0, ly = 0;
-    if (G.tid < NRING) {
-        const int r = G.tid;
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int oslot = (ty + 1) * RX + (tx + 1);
+    int lx = 0, ly = 0, rslot = 0;
+    if (tid < NRING) {
+        const int r = tid;
         if (r < RX) {
             lx = r - 1;
             ly = -1;
@@ -127,7 +227,7 @@ __global__ void __launch_bounds__(NT, 2) step_fused3_kernel(DevParams p, FusedAr
             lx = TX;
             ly = r - 2 * RX - TY;
         }
-        G.rslot = (ly + 1) * RX + (lx + 1);
+        rslot = (ly + 1) * RX + (lx + 1);
     }
 
     for (int item = blockIdx.x; item < A.nitems; item += gridDim.x) {
@@ -136,23 +236,24 @@ __global__ void __launch_bounds__(NT, 2) step_fused3_kernel(DevParams p, FusedAr
         const int x0 = (tile % A.tiles_x) * TX, y0 = (tile / A.tiles_x) * TY;
         const int z0 = chunk * A.chunk;
         const int z1 = min(z0 + A.chunk, p.nz);
-        G.ox = pmod(x0 + G.tx, p.nx);
-        G.oy = pmod(y0 + G.ty, p.ny);
-        const bool valid = (x0 + G.tx < p.nx) && (y0 + G.ty < p.ny);
-        if (G.tid < NRING) {
-            G.rx = pmod(x0 + lx, p.nx);
-            G.ry = pmod(y0 + ly, p.ny);
-        }
+        Column own, ring;
+        set_column(own, p, pmod(x0 + tx, p.nx), pmod(y0 + ty, p.ny));
+        set_column(ring, p, pmod(x0 + lx, p.nx), pmod(y0 + ly, p.ny));
+        const bool valid = (x0 + tx < p.nx) && (y0 + ty < p.ny);
         int sP = 0, sC = 1, sN = 2;
-        stage_plane(p, A, G, z0 - 1, gS + Q3 * NT, phiS + sP * PLANE);
-        stage_plane(p, A, G, z0, gS, phiS + sC * PLANE);
+        stage_issue(p, Dp, own, ring, tid, z0 - 1, gS + Q3 * NT, rS);
+        stage_finish(tid, oslot, rslot, gS + Q3 * NT, rS, phiS + sP * PLANE);
+        stage_issue(p, Dp, own, ring, tid, z0, gS, rS);
+        stage_finish(tid, oslot, rslot, gS, rS, phiS + sC * PLANE);
         for (int z = z0; z < z1; ++z) {
             const int cur = (z - z0) & 1;
-            const long long self = ((long long)z * p.ny + G.oy) * p.nx + G.ox;
+            // g(z+1) and the ring copies in flight while f'(z) is loaded
+            stage_issue(p, Dp, own, ring, tid, z + 1, gS + (cur ^ 1) * Q3 * NT, rS);
+            Plane P;
+            set_plane(P, p, z);
             float fr[Q3];
-#pragma unroll
-            for (int a = 0; a < Q3; ++a) fr[a] = __ldg(A.fin + pull_index<3>(p, a, G.ox, G.oy, z, self));
-            stage_plane(p, A, G, z + 1, gS + (cur ^ 1) * Q3 * NT, phiS + sN * PLANE);
+            Unroll<Q3>::run(PullLoad{Dp.fin, own, P, fr});
+            stage_finish(tid, oslot, rslot, gS + (cur ^ 1) * Q3 * NT, rS, phiS + sN * PLANE);
             FlowMoments m;
             flow_moments<3>(m, fr);
             __syncthreads();
@@ -162,7 +263,7 @@ __global__ void __launch_bounds__(NT, 2) step_fused3_kernel(DevParams p, FusedAr
                 for (int a = 0; a < Q3; ++a) {
                     const int cz = Lat<3>::cz(a);
                     const float* pl = phiS + (cz < 0 ? sP : (cz == 0 ? sC : sN)) * PLANE;
-                    const int o = (G.ty + 1 + Lat<3>::cy(a)) * RX + (G.tx + 1 + Lat<3>::cx(a));
+                    const int o = oslot + Lat<3>::cy(a) * RX + Lat<3>::cx(a);
                     nh[a] = pl[o];
                     nl[a] = pl[3 * PLANE + o];
                 }
@@ -171,8 +272,9 @@ __global__ void __launch_bounds__(NT, 2) step_fused3_kernel(DevParams p, FusedAr
                 CellState s;
                 float dh[27];
                 flow_collide<3>(p, nh[13], grad, lap, m, s, dh);
-                collide_outputs<3>(p, s, dh, m, GFromStrided{gS + cur * Q3 * NT + G.tid, NT}, nh[13], nl[13],
-                                   SoAOut{A.fout + self, p.N}, SoAOut{A.gout + self, p.N});
+                const int self = P.zs[1] + own.ys[1] + own.xs[1];
+                collide_outputs<3>(p, s, dh, m, GFromStrided{gS + cur * Q3 * NT + tid, NT}, nh[13], nl[13],
+                                   PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self});
             }
             __syncthreads();
             const int t = sP;
@@ -207,12 +309,16 @@ cudaError_t launch_step_fused(lbmp_handle* h)
         g_cfg.grid_cap = (per_sm > 0 ? per_sm : 1) * sms;
         g_cfg.device = h->device;
     }
-    FusedArgs A;
+    DirPtrs D;
     const int s = h->parity, d = 1 - h->parity;
-    A.fin = h->f[s];
-    A.gin = h->g[s];
-    A.fout = h->f[d];
-    A.gout = h->g[d];
+    for (int a = 0; a < Q3; ++a) {
+        const size_t off = (size_t)a * (size_t)h->N;
+        D.fin[a] = h->f[s] + off;
+        D.gin[a] = h->g[s] + off;
+        D.fout[a] = h->f[d] + off;
+        D.gout[a] = h->g[d] + off;
+    }
+    FusedArgs A;
     A.tiles_x = (h->grid.nx + TX - 1) / TX;
     A.tiles_y = (h->grid.ny + TY - 1) / TY;
     const int tiles = A.tiles_x * A.tiles_y;
@@ -220,10 +326,9 @@ cudaError_t launch_step_fused(lbmp_handle* h)
     int chunk = h->grid.nz;
     while (chunk > 8 && (long long)tiles * ((h->grid.nz + chunk - 1) / chunk) < 4LL * g_cfg.grid_cap) chunk /= 2;
     A.chunk = chunk;
-    A.nchunks = (h->grid.nz + chunk - 1) / chunk;
-    A.nitems = tiles * A.nchunks;
+    A.nitems = tiles * ((h->grid.nz + chunk - 1) / chunk);
     const int grid = A.nitems < g_cfg.grid_cap ? A.nitems : g_cfg.grid_cap;
-    step_fused3_kernel<<<grid, NT, kSmemBytes, h->stream>>>(h->dp, A);
+    step_fused3_kernel<<<grid, NT, kSmemBytes, h->stream>>>(h->dp, A, D);
     return cudaGetLastError();
 }
 

@@ -19,10 +19,8 @@ __global__ void phi_pass_kernel(DevParams p, const float* __restrict__ g, float*
     if (i >= p.N) return;
     int x, y, z;
     cell_xyz(p, i, x, y, z);
-    float hi = 0.f, lo = 0.f;
-#pragma unroll
-    for (int a = 0; a < Lat<D>::Q; ++a) phi_add(hi, lo, g[pull_index<D>(p, a, x, y, z, i)]);
-    phi_finish(hi, lo);
+    float hi, lo;
+    phi_sum<D>([&](int a) { return g[pull_index<D>(p, a, x, y, z, i)]; }, hi, lo);
     phi[i] = hi;  // phi = sum_a g_a (Sec. 2.2), as hi + lo
     phi[p.N + i] = lo;
 }
