@@ -29,12 +29,23 @@ namespace lbmp {
 
 namespace {
 
-constexpr int TX = 32, TY = 8, NT = TX * TY;
+// tile shape and CTAs per SM (compile-time; the defaults are the measured best)
+#ifndef LBMP_FUSED_TX
+#define LBMP_FUSED_TX 32
+#endif
+#ifndef LBMP_FUSED_TY
+#define LBMP_FUSED_TY 4
+#endif
+#ifndef LBMP_FUSED_MINB
+#define LBMP_FUSED_MINB 4
+#endif
+constexpr int TX = LBMP_FUSED_TX, TY = LBMP_FUSED_TY, NT = TX * TY;
 constexpr int RX = TX + 2, RY = TY + 2;
 constexpr int PLANE = RY * RX;
 constexpr int NRING = 2 * RX + 2 * TY;
 constexpr int Q3 = 27;
-constexpr size_t kSmemBytes = sizeof(float) * (2 * Q3 * NT + Q3 * NRING + 2 * 3 * PLANE);
+constexpr size_t kSmemBytes = sizeof(float) * (2 * Q3 * NT + Q3 * NRING) + sizeof(float2) * 3 * PLANE;
+static_assert(NRING <= NT, "one thread per ring cell");
 
 struct DirPtrs {
     const float* fin[Q3];
@@ -43,6 +54,11 @@ struct DirPtrs {
     float* gout[Q3];
 };
 
+// Work items: (tile, chunk of z planes), tile index fastest, so the CTAs
+// running at any moment hold neighbouring tiles of the same z range and the
+// ring reads of one tile are the own reads of another (L2 hits).  A
+// contiguous split of the plane-columns per CTA, which balances better on
+// paper, measured slower for that reason.
 struct FusedArgs {
     int tiles_x, tiles_y, chunk, nitems;
 };
@@ -96,12 +112,14 @@ __device__ __forceinline__ void set_plane(Plane& P, const DevParams& p, int z)
     P.zs[2] = (z == 0 ? p.nz - 1 : z - 1) * nxy;
 }
 
-// pointer to the post-streaming population a of the cell (column C, plane P)
-template <int a>
+// pointer to the post-streaming population a of the cell (column C, plane P);
+// Walls = false is the path of every plane that does not touch a wall
+template <bool Walls, int a>
 __device__ __forceinline__ const float* pulled(const float* const* base, const Column& C, const Plane& P)
 {
     constexpr int cx = Lat<3>::cx(a), cy = Lat<3>::cy(a), cz = Lat<3>::cz(a);
-    if ((cz == 1 && P.lo) || (cz == -1 && P.hi)) return base[Lat<3>::opp(a)] + (P.zs[1] + C.ys[1] + C.xs[1]);
+    if (Walls && ((cz == 1 && P.lo) || (cz == -1 && P.hi)))
+        return base[Lat<3>::opp(a)] + (P.zs[1] + C.ys[1] + C.xs[1]);
     return base[a] + (P.zs[cz + 1] + C.ys[cy + 1] + C.xs[cx + 1]);
 }
 
@@ -132,6 +150,7 @@ __device__ __forceinline__ int plane_src(const DevParams& p, int zz)
     return zz < 0 ? 0 : p.nz - 1;
 }
 
+template <bool Walls>
 struct StageCopy {
     const DirPtrs& D;
     const Column& C;
@@ -140,10 +159,11 @@ struct StageCopy {
     template <int a>
     __device__ __forceinline__ void step() const
     {
-        cp_async4(gbuf + a * NT, pulled<a>(D.gin, C, P));
+        cp_async4(gbuf + a * NT, pulled<Walls, a>(D.gin, C, P));
     }
 };
 
+template <bool Walls>
 struct PullLoad {
     const float* const* base;
     const Column& C;
@@ -152,10 +172,11 @@ struct PullLoad {
     template <int a>
     __device__ __forceinline__ void step() const
     {
-        v[a] = __ldg(pulled<a>(base, C, P));
+        v[a] = __ldg(pulled<Walls, a>(base, C, P));
     }
 };
 
+template <bool Walls>
 struct RingCopy {
     const DirPtrs& D;
     const Column& C;
@@ -164,49 +185,52 @@ struct RingCopy {
     template <int a>
     __device__ __forceinline__ void step() const
     {
-        cp_async4(rbuf + a * NRING, pulled<a>(D.gin, C, P));
+        cp_async4(rbuf + a * NRING, pulled<Walls, a>(D.gin, C, P));
     }
 };
 
 // Staging of plane zz, in two halves so that other loads can be issued while
 // the copies are in flight.  issue: the tile's own g(zz) into gbuf (kept for
 // the collision of plane zz) and the ring cells' g(zz) into rbuf, both by
-// cp.async.  finish: wait, then phi (hi at [0, PLANE), lo at [3 PLANE,
-// 4 PLANE)) of every tile and ring cell into phi_plane.  Each thread sums
-// only the values it copied itself, so no barrier is needed in between.
+// cp.async.  finish: wait, then phi = (hi, lo) of every tile and ring cell
+// into phi_plane.  Each thread sums only the values it copied itself, so no
+// barrier is needed in between.
 __device__ __forceinline__ void stage_issue(const DevParams& p, const DirPtrs& D, const Column& own,
                                             const Column& ring, int tid, int zz, float* __restrict__ gbuf,
                                             float* __restrict__ rbuf)
 {
     Plane P;
     set_plane(P, p, plane_src(p, zz));
-    Unroll<Q3>::run(StageCopy{D, own, P, gbuf + tid});
-    if (tid < NRING) Unroll<Q3>::run(RingCopy{D, ring, P, rbuf + tid});
+    if (P.lo || P.hi) {  // uniform across the CTA
+        Unroll<Q3>::run(StageCopy<true>{D, own, P, gbuf + tid});
+        if (tid < NRING) Unroll<Q3>::run(RingCopy<true>{D, ring, P, rbuf + tid});
+    } else {
+        Unroll<Q3>::run(StageCopy<false>{D, own, P, gbuf + tid});
+        if (tid < NRING) Unroll<Q3>::run(RingCopy<false>{D, ring, P, rbuf + tid});
+    }
     cp_async_commit();
 }
 
 __device__ __forceinline__ void stage_finish(int tid, int oslot, int rslot, const float* __restrict__ gbuf,
-                                             const float* __restrict__ rbuf, float* __restrict__ phi_plane)
+                                             const float* __restrict__ rbuf, float2* __restrict__ phi_plane)
 {
     cp_async_wait_all();
     if (tid < NRING) {
         float hi, lo;
         phi_sum<3>([&](int a) { return rbuf[a * NRING + tid]; }, hi, lo);
-        phi_plane[rslot] = hi;
-        phi_plane[3 * PLANE + rslot] = lo;
+        phi_plane[rslot] = make_float2(hi, lo);
     }
     float hi, lo;
     phi_sum<3>([&](int a) { return gbuf[a * NT + tid]; }, hi, lo);
-    phi_plane[oslot] = hi;
-    phi_plane[3 * PLANE + oslot] = lo;
+    phi_plane[oslot] = make_float2(hi, lo);
 }
 
-__global__ void __launch_bounds__(NT, 2) step_fused3_kernel(DevParams p, FusedArgs A, DirPtrs Dp)
+__global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_fused3_kernel(DevParams p, FusedArgs A, DirPtrs Dp)
 {
     extern __shared__ float smem[];
     float* gS = smem;                     // [2][27][NT]
     float* rS = smem + 2 * Q3 * NT;       // [27][NRING] ring cells' g of the plane being staged
-    float* phiS = rS + Q3 * NRING;        // hi [3][RY][RX], then lo [3][RY][RX]
+    float2* phiS = (float2*)(rS + Q3 * NRING);  // (hi, lo) [3][RY][RX]
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
@@ -252,7 +276,10 @@ __global__ void __launch_bounds__(NT, 2) step_fused3_kernel(DevParams p, FusedAr
             Plane P;
             set_plane(P, p, z);
             float fr[Q3];
-            Unroll<Q3>::run(PullLoad{Dp.fin, own, P, fr});
+            if (P.lo || P.hi)
+                Unroll<Q3>::run(PullLoad<true>{Dp.fin, own, P, fr});
+            else
+                Unroll<Q3>::run(PullLoad<false>{Dp.fin, own, P, fr});
             stage_finish(tid, oslot, rslot, gS + (cur ^ 1) * Q3 * NT, rS, phiS + sN * PLANE);
             FlowMoments m;
             flow_moments<3>(m, fr);
@@ -262,10 +289,10 @@ __global__ void __launch_bounds__(NT, 2) step_fused3_kernel(DevParams p, FusedAr
 #pragma unroll
                 for (int a = 0; a < Q3; ++a) {
                     const int cz = Lat<3>::cz(a);
-                    const float* pl = phiS + (cz < 0 ? sP : (cz == 0 ? sC : sN)) * PLANE;
-                    const int o = oslot + Lat<3>::cy(a) * RX + Lat<3>::cx(a);
-                    nh[a] = pl[o];
-                    nl[a] = pl[3 * PLANE + o];
+                    const float2* pl = phiS + (cz < 0 ? sP : (cz == 0 ? sC : sN)) * PLANE;
+                    const float2 v = pl[oslot + Lat<3>::cy(a) * RX + Lat<3>::cx(a)];
+                    nh[a] = v.x;
+                    nl[a] = v.y;
                 }
                 float grad[3], lap;
                 stencil_from_nb<3>(nh, nl, grad, lap);
