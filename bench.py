@@ -112,6 +112,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(local_ms, cells_per_rank, steps, dist=None):
+    """Whole-job timing across ranks: the slowest rank's time counts (max over
+    ranks) and the value is the cell updates of all ranks per second, in
+    MLUPS.  Returns (max_ms, mlups)."""
+    total_ms = float(local_ms)
+    ws = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        ws = dist.get_world_size()
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, ws * cells_per_rank * steps / (total_ms * 1e-3) / 1e6
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -254,14 +270,9 @@ def main():
     stream.synchronize()
     barrier()
     clocks = sampler.stop()
-    total_ms = t_start.elapsed_time(t_end)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    if pg is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, mlups = aggregate(t_start.elapsed_time(t_end), cells, args.steps, pg)
     ms_per_step = total_ms / args.steps
-    mlups = ws * cells * args.steps / (total_ms * 1e-3) / 1e6
     launches_per_step = 2 if (args.kernel == 1) else 1
 
     # roofline of the step kernel: algorithmic bytes per launch / event time
@@ -288,14 +299,9 @@ def main():
         dom.step(1)
         dom.observables()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if pg is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_ms, e2e_mlups = aggregate((time.perf_counter() - t0) * 1e3, cells, e2e_steps, pg)
     obs_bytes = 96 + 8 * 2 * (wl["dims"][D - 1])
-    e2e = {"value": ws * cells * e2e_steps / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": nbytes,
-           "d2h_bytes_per_step": obs_bytes}
+    e2e = {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": obs_bytes}
 
     ob = dom.observables()
     line = {"metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,

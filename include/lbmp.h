@@ -176,6 +176,40 @@ LBMP_API int lbmp_download(lbmp_handle *h, void *host, size_t bytes);
 enum { LBMP_OPT_KERNEL = 0 };
 LBMP_API int lbmp_set_option(lbmp_handle *h, int option, long value);
 
+/* ---- batches: many domains advanced together ------------------------------
+ * A batch advances every member domain with one persistent kernel launch per
+ * lattice type and step: the kernel walks a device-side table of the members
+ * (sizes, parameters, population sets, parity, steps left) and splits their
+ * combined work evenly over the GPU, so small and uneven domains share the
+ * machine instead of each under-filling it.  The per-step bookkeeping
+ * (parity, remaining steps) is done on the device, so a run of steps is
+ * captured once in a CUDA graph and replayed until the membership changes.
+ * D3Q27 and D2Q9 members may be mixed (one kernel per lattice type).
+ * Results are bitwise those of stepping each member alone.
+ * Members are handles from lbmp_create on the batch's device; the batch does
+ * not own them.  A member must not be stepped, set or destroyed through its
+ * own handle while it belongs to a batch (remove it first); get_state and
+ * observables of a member are valid after lbmp_batch_step returns. */
+typedef struct lbmp_batch lbmp_batch;
+
+/* hbm_budget: upper bound (bytes) on the summed device state of the members,
+ * 0 = none; cuda_stream: stream of all batch work (NULL: the batch creates a
+ * private stream, since the legacy default stream cannot be captured). */
+LBMP_API int lbmp_batch_create(size_t hbm_budget, void *cuda_stream, lbmp_batch **out);
+LBMP_API int lbmp_batch_destroy(lbmp_batch *b);
+/* Admit h for `steps` more steps (> 0).  LBMP_ERR_NOMEM when it would exceed
+ * the budget, LBMP_ERR_INVALID_ARG when h is already a member or the batch is
+ * full (1024 members). */
+LBMP_API int lbmp_batch_add(lbmp_batch *b, lbmp_handle *h, long steps);
+LBMP_API int lbmp_batch_remove(lbmp_batch *b, lbmp_handle *h);
+/* Advance every member with steps left by up to n steps (graph launches on
+ * the batch's stream), then synchronise.  *n_finished (may be NULL) receives
+ * the number of members whose steps ran out during this call. */
+LBMP_API int lbmp_batch_step(lbmp_batch *b, long n, int *n_finished);
+/* Members and their remaining steps: fills up to max entries, returns the
+ * member count (or a negative status). */
+LBMP_API int lbmp_batch_members(const lbmp_batch *b, lbmp_handle **members, long *steps_left, int max);
+
 /* Mass without allocation (the paper has no counterpart: this is a service
  * of the library).  For callers that cannot allocate device memory, e.g. a
  * host framework that owns every byte of device memory and hands out only

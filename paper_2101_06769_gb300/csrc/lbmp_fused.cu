@@ -225,90 +225,170 @@ __device__ __forceinline__ void stage_finish(int tid, int oslot, int rslot, cons
     phi_plane[oslot] = make_float2(hi, lo);
 }
 
+// per-thread geometry inside a tile: own cell and (for tid < NRING) ring cell
+struct ThreadGeo {
+    int tid, tx, ty, oslot, lx, ly, rslot;
+};
+
+__device__ __forceinline__ ThreadGeo thread_geo()
+{
+    ThreadGeo T;
+    T.tid = threadIdx.x;
+    T.tx = T.tid % TX;
+    T.ty = T.tid / TX;
+    T.oslot = (T.ty + 1) * RX + (T.tx + 1);
+    T.lx = T.ly = T.rslot = 0;
+    if (T.tid < NRING) {
+        const int r = T.tid;
+        if (r < RX) {
+            T.lx = r - 1;
+            T.ly = -1;
+        } else if (r < 2 * RX) {
+            T.lx = r - RX - 1;
+            T.ly = TY;
+        } else if (r < 2 * RX + TY) {
+            T.lx = -1;
+            T.ly = r - 2 * RX;
+        } else {
+            T.lx = TX;
+            T.ly = r - 2 * RX - TY;
+        }
+        T.rslot = (T.ly + 1) * RX + (T.lx + 1);
+    }
+    return T;
+}
+
+// One segment of work: planes [z0, z1) of the tile at (x0, y0) of the domain
+// described by (p, Dp).  smem holds the g staging buffers, the ring buffer and
+// the three phi planes.  Ends with a barrier, so the caller may reuse shared
+// memory afterwards.
+__device__ __forceinline__ void fused_segment(const DevParams& p, const DirPtrs& Dp, const ThreadGeo& T, float* smem,
+                                              int x0, int y0, int z0, int z1)
+{
+    float* gS = smem;                           // [2][27][NT]
+    float* rS = smem + 2 * Q3 * NT;             // [27][NRING] ring cells' g of the plane being staged
+    float2* phiS = (float2*)(rS + Q3 * NRING);  // (hi, lo) [3][RY][RX]
+    const int tid = T.tid, oslot = T.oslot, rslot = T.rslot;
+    Column own, ring;
+    set_column(own, p, pmod(x0 + T.tx, p.nx), pmod(y0 + T.ty, p.ny));
+    set_column(ring, p, pmod(x0 + T.lx, p.nx), pmod(y0 + T.ly, p.ny));
+    const bool valid = (x0 + T.tx < p.nx) && (y0 + T.ty < p.ny);
+    int sP = 0, sC = 1, sN = 2;
+    stage_issue(p, Dp, own, ring, tid, z0 - 1, gS + Q3 * NT, rS);
+    stage_finish(tid, oslot, rslot, gS + Q3 * NT, rS, phiS + sP * PLANE);
+    stage_issue(p, Dp, own, ring, tid, z0, gS, rS);
+    stage_finish(tid, oslot, rslot, gS, rS, phiS + sC * PLANE);
+    for (int z = z0; z < z1; ++z) {
+        const int cur = (z - z0) & 1;
+        // g(z+1) and the ring copies in flight while f'(z) is loaded
+        stage_issue(p, Dp, own, ring, tid, z + 1, gS + (cur ^ 1) * Q3 * NT, rS);
+        Plane P;
+        set_plane(P, p, z);
+        float fr[Q3];
+        if (P.lo || P.hi)
+            Unroll<Q3>::run(PullLoad<true>{Dp.fin, own, P, fr});
+        else
+            Unroll<Q3>::run(PullLoad<false>{Dp.fin, own, P, fr});
+        stage_finish(tid, oslot, rslot, gS + (cur ^ 1) * Q3 * NT, rS, phiS + sN * PLANE);
+        FlowMoments m;
+        flow_moments<3>(m, fr);
+        __syncthreads();
+        if (valid) {
+            float nh[Q3], nl[Q3];
+#pragma unroll
+            for (int a = 0; a < Q3; ++a) {
+                const int cz = Lat<3>::cz(a);
+                const float2* pl = phiS + (cz < 0 ? sP : (cz == 0 ? sC : sN)) * PLANE;
+                const float2 v = pl[oslot + Lat<3>::cy(a) * RX + Lat<3>::cx(a)];
+                nh[a] = v.x;
+                nl[a] = v.y;
+            }
+            float grad[3], lap;
+            stencil_from_nb<3>(nh, nl, grad, lap);
+            CellState s;
+            float dh[27];
+            flow_collide<3>(p, nh[13], grad, lap, m, s, dh);
+            const int self = P.zs[1] + own.ys[1] + own.xs[1];
+            collide_outputs<3>(p, s, dh, m, GFromStrided{gS + cur * Q3 * NT + tid, NT}, nh[13], nl[13],
+                               PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self});
+        }
+        __syncthreads();
+        const int t = sP;
+        sP = sC;
+        sC = sN;
+        sN = t;
+    }
+}
+
 __global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_fused3_kernel(DevParams p, FusedArgs A, DirPtrs Dp)
 {
     extern __shared__ float smem[];
-    float* gS = smem;                     // [2][27][NT]
-    float* rS = smem + 2 * Q3 * NT;       // [27][NRING] ring cells' g of the plane being staged
-    float2* phiS = (float2*)(rS + Q3 * NRING);  // (hi, lo) [3][RY][RX]
-
-    const int tid = threadIdx.x;
-    const int tx = tid % TX, ty = tid / TX;
-    const int oslot = (ty + 1) * RX + (tx + 1);
-    int lx = 0, ly = 0, rslot = 0;
-    if (tid < NRING) {
-        const int r = tid;
-        if (r < RX) {
-            lx = r - 1;
-            ly = -1;
-        } else if (r < 2 * RX) {
-            lx = r - RX - 1;
-            ly = TY;
-        } else if (r < 2 * RX + TY) {
-            lx = -1;
-            ly = r - 2 * RX;
-        } else {
-            lx = TX;
-            ly = r - 2 * RX - TY;
-        }
-        rslot = (ly + 1) * RX + (lx + 1);
-    }
-
+    const ThreadGeo T = thread_geo();
     for (int item = blockIdx.x; item < A.nitems; item += gridDim.x) {
         const int tile = item % (A.tiles_x * A.tiles_y);
         const int chunk = item / (A.tiles_x * A.tiles_y);
-        const int x0 = (tile % A.tiles_x) * TX, y0 = (tile / A.tiles_x) * TY;
         const int z0 = chunk * A.chunk;
-        const int z1 = min(z0 + A.chunk, p.nz);
-        Column own, ring;
-        set_column(own, p, pmod(x0 + tx, p.nx), pmod(y0 + ty, p.ny));
-        set_column(ring, p, pmod(x0 + lx, p.nx), pmod(y0 + ly, p.ny));
-        const bool valid = (x0 + tx < p.nx) && (y0 + ty < p.ny);
-        int sP = 0, sC = 1, sN = 2;
-        stage_issue(p, Dp, own, ring, tid, z0 - 1, gS + Q3 * NT, rS);
-        stage_finish(tid, oslot, rslot, gS + Q3 * NT, rS, phiS + sP * PLANE);
-        stage_issue(p, Dp, own, ring, tid, z0, gS, rS);
-        stage_finish(tid, oslot, rslot, gS, rS, phiS + sC * PLANE);
-        for (int z = z0; z < z1; ++z) {
-            const int cur = (z - z0) & 1;
-            // g(z+1) and the ring copies in flight while f'(z) is loaded
-            stage_issue(p, Dp, own, ring, tid, z + 1, gS + (cur ^ 1) * Q3 * NT, rS);
-            Plane P;
-            set_plane(P, p, z);
-            float fr[Q3];
-            if (P.lo || P.hi)
-                Unroll<Q3>::run(PullLoad<true>{Dp.fin, own, P, fr});
-            else
-                Unroll<Q3>::run(PullLoad<false>{Dp.fin, own, P, fr});
-            stage_finish(tid, oslot, rslot, gS + (cur ^ 1) * Q3 * NT, rS, phiS + sN * PLANE);
-            FlowMoments m;
-            flow_moments<3>(m, fr);
-            __syncthreads();
-            if (valid) {
-                float nh[Q3], nl[Q3];
-#pragma unroll
-                for (int a = 0; a < Q3; ++a) {
-                    const int cz = Lat<3>::cz(a);
-                    const float2* pl = phiS + (cz < 0 ? sP : (cz == 0 ? sC : sN)) * PLANE;
-                    const float2 v = pl[oslot + Lat<3>::cy(a) * RX + Lat<3>::cx(a)];
-                    nh[a] = v.x;
-                    nl[a] = v.y;
-                }
-                float grad[3], lap;
-                stencil_from_nb<3>(nh, nl, grad, lap);
-                CellState s;
-                float dh[27];
-                flow_collide<3>(p, nh[13], grad, lap, m, s, dh);
-                const int self = P.zs[1] + own.ys[1] + own.xs[1];
-                collide_outputs<3>(p, s, dh, m, GFromStrided{gS + cur * Q3 * NT + tid, NT}, nh[13], nl[13],
-                                   PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self});
+        fused_segment(p, Dp, T, smem, (tile % A.tiles_x) * TX, (tile / A.tiles_x) * TY, z0,
+                      min(z0 + A.chunk, p.nz));
+    }
+}
+
+// Batch form: the work items of every member (same order as above within a
+// member, members concatenated) are split over one persistent grid.  A CTA
+// stages the parameters and the 108 direction bases of its current member in
+// shared memory; members whose steps have run out are skipped.
+__global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_batch3_kernel(const BatchDomain* __restrict__ table,
+                                                                          int ndom, int nitems)
+{
+    extern __shared__ float smem[];
+    __shared__ DevParams sp;
+    __shared__ DirPtrs sd;
+    __shared__ int s_dom, s_tx, s_ty, s_chunk, s_begin, s_active;
+    const ThreadGeo T = thread_geo();
+    int cur = -1;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        __syncthreads();  // every thread has read the previous item's shared values
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = ndom - 1;  // last member with item_begin <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (table[mid].item_begin <= item)
+                    lo = mid;
+                else
+                    hi = mid - 1;
             }
-            __syncthreads();
-            const int t = sP;
-            sP = sC;
-            sC = sN;
-            sN = t;
+            s_dom = lo;
         }
+        __syncthreads();
+        const int d = s_dom;
+        if (d != cur) {
+            const BatchDomain& B = table[d];
+            if (threadIdx.x == 0) {
+                sp = B.p;
+                s_tx = B.tiles_x;
+                s_ty = B.tiles_y;
+                s_chunk = B.chunk;
+                s_begin = B.item_begin;
+                s_active = B.steps_left > 0;
+            }
+            const int par = B.parity;
+            for (int k = threadIdx.x; k < 4 * Q3; k += blockDim.x) {
+                const int set = k / Q3, a = k % Q3;
+                const size_t off = (size_t)a * (size_t)B.p.N;
+                if (set == 0) sd.fin[a] = B.f[par] + off;
+                if (set == 1) sd.gin[a] = B.g[par] + off;
+                if (set == 2) sd.fout[a] = B.f[par ^ 1] + off;
+                if (set == 3) sd.gout[a] = B.g[par ^ 1] + off;
+            }
+            cur = d;
+            __syncthreads();
+        }
+        if (!s_active) continue;  // uniform
+        const int local = item - s_begin;
+        const int tiles = s_tx * s_ty;
+        const int tile = local % tiles;
+        const int z0 = (local / tiles) * s_chunk;
+        fused_segment(sp, sd, T, smem, (tile % s_tx) * TX, (tile / s_tx) * TY, z0, min(z0 + s_chunk, sp.nz));
     }
 }
 
@@ -320,10 +400,61 @@ LaunchCfg g_cfg;
 
 }  // namespace
 
-bool fused_supported(const lbmp_handle* h) { return h->D == 3; }
+bool fused_supported(const lbmp_handle* h) { return h->D == 3 || h->D == 2; }
+
+__global__ void batch_epilogue_kernel(BatchDomain* table, int ndom)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d < ndom && table[d].steps_left > 0) {
+        table[d].parity ^= 1;
+        table[d].steps_left -= 1;
+    }
+}
+
+int batch3_tile_x() { return TX; }
+int batch3_tile_y() { return TY; }
+
+static int g_batch_dev = -1, g_batch_cap = 0;
+
+// attributes and occupancy of the batch kernel (not capturable: call before capture)
+cudaError_t prepare_batch3(int device)
+{
+    int& dev_cached = g_batch_dev;
+    int& cap = g_batch_cap;
+    if (dev_cached != device) {
+        cudaError_t e = cudaFuncSetAttribute(step_batch3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_batch3_kernel, NT, kSmemBytes);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+        if (e != cudaSuccess) return e;
+        cap = (per_sm > 0 ? per_sm : 1) * sms;
+        dev_cached = device;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_batch3(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream)
+{
+    if (g_batch_dev != device) return cudaErrorNotReady;  // prepare_batch3 first
+    if (nitems <= 0) return cudaSuccess;
+    const int grid = nitems < g_batch_cap ? nitems : g_batch_cap;
+    step_batch3_kernel<<<grid, NT, kSmemBytes, stream>>>(table, ndom, nitems);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_epilogue(BatchDomain* table, int ndom, cudaStream_t stream)
+{
+    if (ndom <= 0) return cudaSuccess;
+    batch_epilogue_kernel<<<(ndom + 127) / 128, 128, 0, stream>>>(table, ndom);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_step_fused(lbmp_handle* h)
 {
+    if (h->D == 2) return launch_step_fused2(h);
     if (g_cfg.device != h->device) {
         cudaError_t e = cudaFuncSetAttribute(step_fused3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kSmemBytes);

@@ -1,0 +1,285 @@
+// lbmp_fused2.cu -- fused single-pass D2Q9 step (and its batch form).
+//
+// The 2-D counterpart of lbmp_fused.cu: a CTA owns a segment of TX2 cells of
+// one row and marches through a chunk of rows.  For row y it needs phi on rows
+// y-1, y, y+1 over the segment and one cell on each side; phi = sum_a g_a of
+// the pulled g, formed while g(y+1) is staged into shared memory by cp.async
+// (the two side cells by threads 0 and 1).  The step reads one population
+// set and writes the other, so the side reads never race with the
+// neighbouring segment's writes.  The per-cell arithmetic is the shared one
+// of lbmp_common.cuh, as in the reference pair.
+#include "lbmp_internal.h"
+
+namespace lbmp {
+
+namespace {
+
+constexpr int TX2 = 128;
+constexpr int Q2 = 9;
+constexpr int RW = TX2 + 2;  // row of phi incl. one side cell each way
+constexpr size_t kSmem2 = sizeof(float) * (2 * Q2 * TX2 + Q2 * 2) + sizeof(float2) * 3 * RW;
+
+struct DirPtrs2 {
+    const float* fin[Q2];
+    const float* gin[Q2];
+    float* fout[Q2];
+    float* gout[Q2];
+};
+
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ int pmod(int v, int n)
+{
+    const int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+// upstream x coordinates xs[c+1] = x - c (periodic)
+struct Col2 {
+    int xs[3];
+};
+__device__ __forceinline__ void set_col2(Col2& C, int x, int nx)
+{
+    C.xs[0] = x + 1 == nx ? 0 : x + 1;
+    C.xs[1] = x;
+    C.xs[2] = x == 0 ? nx - 1 : x - 1;
+}
+
+// upstream rows ys[c+1] = (y - c) nx; lo/hi: bottom/top row of a walled domain
+struct Row2 {
+    int ys[3];
+    bool lo, hi;
+};
+__device__ __forceinline__ void set_row2(Row2& R, const DevParams& p, int y)
+{
+    R.lo = !p.vert_periodic && y == 0;
+    R.hi = !p.vert_periodic && y == p.ny - 1;
+    R.ys[0] = (y + 1 == p.ny ? 0 : y + 1) * p.nx;
+    R.ys[1] = y * p.nx;
+    R.ys[2] = (y == 0 ? p.ny - 1 : y - 1) * p.nx;
+}
+
+// post-streaming population a of the cell (C, R): pulled from upstream, or
+// bounced back at a wall
+__device__ __forceinline__ const float* pulled2(const float* const* base, int a, const Col2& C, const Row2& R)
+{
+    const int cx = Lat<2>::cx(a), cy = Lat<2>::cy(a);
+    if ((cy == 1 && R.lo) || (cy == -1 && R.hi)) return base[Lat<2>::opp(a)] + (R.ys[1] + C.xs[1]);
+    return base[a] + (R.ys[cy + 1] + C.xs[cx + 1]);
+}
+
+__device__ __forceinline__ int row_src(const DevParams& p, int yy)
+{
+    if (yy >= 0 && yy < p.ny) return yy;
+    if (p.vert_periodic) return pmod(yy, p.ny);
+    return yy < 0 ? 0 : p.ny - 1;  // mirrored ghost (reading A17)
+}
+
+// stage row yy: own g into gbuf, side cells' g into sbuf, then phi into prow
+__device__ __forceinline__ void stage_row(const DevParams& p, const DirPtrs2& D, const Col2& own, const Col2& side,
+                                          int tid, int yy, float* __restrict__ gbuf, float* __restrict__ sbuf,
+                                          float2* __restrict__ prow)
+{
+    Row2 R;
+    set_row2(R, p, row_src(p, yy));
+#pragma unroll
+    for (int a = 0; a < Q2; ++a) cp_async4(gbuf + a * TX2 + tid, pulled2(D.gin, a, own, R));
+    if (tid < 2) {
+#pragma unroll
+        for (int a = 0; a < Q2; ++a) cp_async4(sbuf + a * 2 + tid, pulled2(D.gin, a, side, R));
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    float hi, lo;
+    if (tid < 2) {
+        phi_sum<2>([&](int a) { return sbuf[a * 2 + tid]; }, hi, lo);
+        prow[tid == 0 ? 0 : RW - 1] = make_float2(hi, lo);
+    }
+    phi_sum<2>([&](int a) { return gbuf[a * TX2 + tid]; }, hi, lo);
+    prow[tid + 1] = make_float2(hi, lo);
+}
+
+// rows [y0, y1) of the segment starting at x0
+__device__ __forceinline__ void fused2_segment(const DevParams& p, const DirPtrs2& D, float* smem, int x0, int y0,
+                                               int y1)
+{
+    float* gS = smem;                               // [2][9][TX2]
+    float* sS = smem + 2 * Q2 * TX2;                // [9][2]
+    float2* phiS = (float2*)(sS + Q2 * 2);          // [3][RW]
+    const int tid = threadIdx.x;
+    Col2 own, side;
+    set_col2(own, pmod(x0 + tid, p.nx), p.nx);
+    set_col2(side, pmod(tid == 0 ? x0 - 1 : x0 + TX2, p.nx), p.nx);
+    const bool valid = x0 + tid < p.nx;
+    int sP = 0, sC = 1, sN = 2;
+    stage_row(p, D, own, side, tid, y0 - 1, gS + Q2 * TX2, sS, phiS + sP * RW);
+    stage_row(p, D, own, side, tid, y0, gS, sS, phiS + sC * RW);
+    for (int y = y0; y < y1; ++y) {
+        const int cur = (y - y0) & 1;
+        Row2 R;
+        set_row2(R, p, y);
+        float fr[Q2];
+#pragma unroll
+        for (int a = 0; a < Q2; ++a) fr[a] = __ldg(pulled2(D.fin, a, own, R));
+        stage_row(p, D, own, side, tid, y + 1, gS + (cur ^ 1) * Q2 * TX2, sS, phiS + sN * RW);
+        FlowMoments m;
+        flow_moments<2>(m, fr);
+        __syncthreads();
+        if (valid) {
+            float nh[Q2], nl[Q2];
+#pragma unroll
+            for (int a = 0; a < Q2; ++a) {
+                const int cy = Lat<2>::cy(a);
+                const float2 v = phiS[(cy < 0 ? sP : (cy == 0 ? sC : sN)) * RW + tid + 1 + Lat<2>::cx(a)];
+                nh[a] = v.x;
+                nl[a] = v.y;
+            }
+            float grad[3], lap;
+            stencil_from_nb<2>(nh, nl, grad, lap);
+            CellState s;
+            float dh[27];
+            flow_collide<2>(p, nh[4], grad, lap, m, s, dh);
+            const int self = R.ys[1] + own.xs[1];
+            collide_outputs<2>(p, s, dh, m, GFromStrided{gS + cur * Q2 * TX2 + tid, TX2}, nh[4], nl[4],
+                               PtrOut{D.fout, self}, PtrOut{D.gout, self});
+        }
+        __syncthreads();
+        const int t = sP;
+        sP = sC;
+        sC = sN;
+        sN = t;
+    }
+}
+
+struct Fused2Args {
+    int tiles_x, chunk, nitems;
+};
+
+__global__ void __launch_bounds__(TX2) step_fused2_kernel(DevParams p, Fused2Args A, DirPtrs2 D)
+{
+    extern __shared__ float smem[];
+    for (int item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+        const int tile = item % A.tiles_x;
+        const int y0 = (item / A.tiles_x) * A.chunk;
+        fused2_segment(p, D, smem, tile * TX2, y0, min(y0 + A.chunk, p.ny));
+    }
+}
+
+__global__ void __launch_bounds__(TX2) step_batch2_kernel(const BatchDomain* __restrict__ table, int ndom,
+                                                          int nitems)
+{
+    extern __shared__ float smem[];
+    __shared__ DevParams sp;
+    __shared__ DirPtrs2 sd;
+    __shared__ int s_dom, s_tx, s_chunk, s_begin, s_active;
+    int cur = -1;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = ndom - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (table[mid].item_begin <= item)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            s_dom = lo;
+        }
+        __syncthreads();
+        const int d = s_dom;
+        if (d != cur) {
+            const BatchDomain& B = table[d];
+            if (threadIdx.x == 0) {
+                sp = B.p;
+                s_tx = B.tiles_x;
+                s_chunk = B.chunk;
+                s_begin = B.item_begin;
+                s_active = B.steps_left > 0;
+            }
+            const int par = B.parity;
+            for (int k = threadIdx.x; k < 4 * Q2; k += blockDim.x) {
+                const int set = k / Q2, a = k % Q2;
+                const size_t off = (size_t)a * (size_t)B.p.N;
+                if (set == 0) sd.fin[a] = B.f[par] + off;
+                if (set == 1) sd.gin[a] = B.g[par] + off;
+                if (set == 2) sd.fout[a] = B.f[par ^ 1] + off;
+                if (set == 3) sd.gout[a] = B.g[par ^ 1] + off;
+            }
+            cur = d;
+            __syncthreads();
+        }
+        if (!s_active) continue;
+        const int local = item - s_begin;
+        const int tile = local % s_tx;
+        const int y0 = (local / s_tx) * s_chunk;
+        fused2_segment(sp, sd, smem, tile * TX2, y0, min(y0 + s_chunk, sp.ny));
+    }
+}
+
+int g_f2_dev = -1, g_f2_cap = 0, g_b2_dev = -1, g_b2_cap = 0;
+
+cudaError_t setup_kernel(const void* fn, int device, int& dev_cached, int& cap)
+{
+    if (dev_cached == device) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem2);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TX2, kSmem2);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return e;
+    cap = (per_sm > 0 ? per_sm : 1) * sms;
+    dev_cached = device;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+int batch2_tile_x() { return TX2; }
+
+cudaError_t launch_step_fused2(lbmp_handle* h)
+{
+    cudaError_t e = setup_kernel((const void*)step_fused2_kernel, h->device, g_f2_dev, g_f2_cap);
+    if (e != cudaSuccess) return e;
+    DirPtrs2 D;
+    const int s = h->parity, d = 1 - h->parity;
+    for (int a = 0; a < Q2; ++a) {
+        const size_t off = (size_t)a * (size_t)h->N;
+        D.fin[a] = h->f[s] + off;
+        D.gin[a] = h->g[s] + off;
+        D.fout[a] = h->f[d] + off;
+        D.gout[a] = h->g[d] + off;
+    }
+    Fused2Args A;
+    A.tiles_x = (h->grid.nx + TX2 - 1) / TX2;
+    int chunk = h->grid.ny;
+    while (chunk > 8 && (long long)A.tiles_x * ((h->grid.ny + chunk - 1) / chunk) < 4LL * g_f2_cap) chunk /= 2;
+    A.chunk = chunk;
+    A.nitems = A.tiles_x * ((h->grid.ny + chunk - 1) / chunk);
+    const int grid = A.nitems < g_f2_cap ? A.nitems : g_f2_cap;
+    step_fused2_kernel<<<grid, TX2, kSmem2, h->stream>>>(h->dp, A, D);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_batch2(int device)
+{
+    return setup_kernel((const void*)step_batch2_kernel, device, g_b2_dev, g_b2_cap);
+}
+
+cudaError_t launch_batch2(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream)
+{
+    if (g_b2_dev != device) return cudaErrorNotReady;  // prepare_batch2 first
+    if (nitems <= 0) return cudaSuccess;
+    const int grid = nitems < g_b2_cap ? nitems : g_b2_cap;
+    step_batch2_kernel<<<grid, TX2, kSmem2, stream>>>(table, ndom, nitems);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmp

@@ -33,6 +33,15 @@ struct lbmp_handle {
 
 namespace lbmp {
 
+// one member of a batch, as the batch kernels see it (device memory)
+struct BatchDomain {
+    DevParams p;
+    float* f[2];
+    float* g[2];
+    int parity, steps_left;
+    int tiles_x, tiles_y, chunk, item_begin, items;
+};
+
 // kernel launchers (return cudaError_t of the launch)
 cudaError_t launch_phi_pass(lbmp_handle* h);
 cudaError_t launch_step_simple(lbmp_handle* h);
@@ -45,6 +54,15 @@ cudaError_t launch_get_state(lbmp_handle* h, double* dev_f, double* dev_g);
 cudaError_t launch_observables(lbmp_handle* h, double* dev_out);
 cudaError_t launch_mass(lbmp_handle* h, double* dev_out4);  // writes 4 doubles, [0] = mass
 bool fused_supported(const lbmp_handle* h);
+int batch3_tile_x();
+int batch3_tile_y();
+cudaError_t launch_step_fused2(lbmp_handle* h);
+int batch2_tile_x();
+cudaError_t prepare_batch2(int device);
+cudaError_t launch_batch2(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream);
+cudaError_t prepare_batch3(int device);
+cudaError_t launch_batch3(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream);
+cudaError_t launch_batch_epilogue(BatchDomain* table, int ndom, cudaStream_t stream);
 // record a message for lbmp_last_error() and return code
 int set_error(int code, const char* msg);
 

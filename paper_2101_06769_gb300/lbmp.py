@@ -25,7 +25,9 @@ ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5
 # every entry point declared in include/lbmp.h
 EXPORTS = ("lbmp_create", "lbmp_destroy", "lbmp_last_error", "lbmp_get_derived", "lbmp_init",
            "lbmp_step", "lbmp_sync", "lbmp_observables", "lbmp_get_state", "lbmp_set_state",
-           "lbmp_state_bytes", "lbmp_upload", "lbmp_download", "lbmp_set_option", "lbmp_mass_noalloc")
+           "lbmp_state_bytes", "lbmp_upload", "lbmp_download", "lbmp_set_option", "lbmp_mass_noalloc",
+           "lbmp_batch_create", "lbmp_batch_destroy", "lbmp_batch_add", "lbmp_batch_remove",
+           "lbmp_batch_step", "lbmp_batch_members")
 
 
 class Grid(C.Structure):
@@ -89,6 +91,12 @@ def load(path=None):
     L.lbmp_download.argtypes = [vp, vp, C.c_size_t]
     L.lbmp_set_option.argtypes = [vp, C.c_int, C.c_long]
     L.lbmp_mass_noalloc.argtypes = [vp, C.c_longlong, C.POINTER(C.c_double), vp]
+    L.lbmp_batch_create.argtypes = [C.c_size_t, vp, C.POINTER(vp)]
+    L.lbmp_batch_destroy.argtypes = [vp]
+    L.lbmp_batch_add.argtypes = [vp, vp, C.c_long]
+    L.lbmp_batch_remove.argtypes = [vp, vp]
+    L.lbmp_batch_step.argtypes = [vp, C.c_long, C.POINTER(C.c_int)]
+    L.lbmp_batch_members.argtypes = [vp, C.POINTER(vp), C.POINTER(C.c_long), C.c_int]
     _lib = L
     return L
 
@@ -194,3 +202,57 @@ class Domain:
 
     def download(self, host_ptr, nbytes):
         _check(load().lbmp_download(self._h, C.c_void_p(host_ptr), nbytes))
+
+
+class Batch:
+    """Domains advanced together by one persistent kernel per step (see
+    lbmp_batch_* in include/lbmp.h).  Members stay owned by the caller."""
+
+    def __init__(self, hbm_budget=0, stream=None):
+        h = C.c_void_p()
+        _check(load().lbmp_batch_create(int(hbm_budget), C.c_void_p(stream) if stream else None, C.byref(h)))
+        self._h = h
+        self._members = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lbmp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, dom, steps):
+        rc = load().lbmp_batch_add(self._h, dom.handle, int(steps))
+        _check(rc)
+        self._members[dom.handle.value] = dom
+
+    def try_add(self, dom, steps):
+        """False (instead of raising) when the domain does not fit the budget"""
+        rc = load().lbmp_batch_add(self._h, dom.handle, int(steps))
+        if rc == -2:
+            return False
+        _check(rc)
+        self._members[dom.handle.value] = dom
+        return True
+
+    def remove(self, dom):
+        _check(load().lbmp_batch_remove(self._h, dom.handle))
+        self._members.pop(dom.handle.value, None)
+
+    def step(self, n):
+        fin = C.c_int(0)
+        _check(load().lbmp_batch_step(self._h, int(n), C.byref(fin)))
+        return fin.value
+
+    def members(self):
+        n = load().lbmp_batch_members(self._h, None, None, 0)
+        if n < 0:
+            _check(n)
+        hs = (C.c_void_p * max(1, n))()
+        left = (C.c_long * max(1, n))()
+        load().lbmp_batch_members(self._h, hs, left, n)
+        return [(self._members.get(hs[k]), int(left[k])) for k in range(n)]
