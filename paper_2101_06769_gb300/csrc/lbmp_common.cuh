@@ -161,24 +161,43 @@ __device__ __forceinline__ void phi_sum(const Get& get, float& hi, float& lo)
     hi = s;
 }
 
+// Paired FP32 arithmetic (sm_100+ FFMA2/FADD2/FMUL2): one instruction
+// updates both lanes, each lane rounded exactly as its scalar counterpart.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+// TwoSum (Knuth) on both lanes: hi + lo accumulates v exactly
+__device__ __forceinline__ void two_sum2(float2& hi, float2& lo, float2 v)
+{
+    const float2 t = add2(hi, v);
+    const float2 bb = add2(t, neg2(hi));
+    lo = add2(lo, add2(add2(hi, neg2(add2(t, neg2(bb)))), add2(v, neg2(bb))));
+    hi = t;
+}
+
 // Isotropic differences (Sec. 2.2) from the Q neighbour values
 // phi(x + c_a) = nh[a] + nl[a]: grad_i = 3 sum w c_i phi(x+c),
-// lap = 6 sum w (phi(x+c) - phi(x)).  The gradient is summed over opposite
-// pairs so that it is exactly zero on a uniform field.
+// lap = 6 sum w (phi(x+c) - phi(x)).  Opposite neighbours are taken as a
+// pair: the gradient from the difference of their deviations from the
+// centre (exactly zero on a uniform field), the Laplacian from their sum.
 template <int D>
 __device__ __forceinline__ void stencil_from_nb(const float* nh, const float* nl, float grad[3], float& lap)
 {
     constexpr int Q = Lat<D>::Q;
     constexpr int C = Q / 2;
-    float gx = 0.f, gy = 0.f, gz = 0.f, ls = 0.f;
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        if (a == C) continue;
-        ls += Lat<D>::w(a) * ((nh[a] - nh[C]) + (nl[a] - nl[C]));
-    }
+    const float2 hc = f2(-nh[C], -nh[C]), lc = f2(-nl[C], -nl[C]);
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    float2 ls = f2(0.f, 0.f);
 #pragma unroll
     for (int a = 0; a < C; ++a) {
-        const float d = Lat<D>::w(a) * ((nh[a] - nh[Q - 1 - a]) + (nl[a] - nl[Q - 1 - a]));
+        const int b = Q - 1 - a;
+        const float w = Lat<D>::w(a);
+        // phi(x + c) - phi(x) and phi(x - c) - phi(x), hi and lo parts differenced first
+        const float2 dd = add2(add2(f2(nh[a], nh[b]), hc), add2(f2(nl[a], nl[b]), lc));
+        ls = fma2(f2(w, w), dd, ls);
+        const float d = w * (dd.x - dd.y);
         if (Lat<D>::cx(a)) gx += Lat<D>::cx(a) * d;
         if (Lat<D>::cy(a)) gy += Lat<D>::cy(a) * d;
         if (Lat<D>::cz(a)) gz += Lat<D>::cz(a) * d;
@@ -186,7 +205,7 @@ __device__ __forceinline__ void stencil_from_nb(const float* nh, const float* nl
     grad[0] = 3.f * gx;
     grad[1] = 3.f * gy;
     grad[2] = (D == 3) ? 3.f * gz : 0.f;
-    lap = 6.f * ls;
+    lap = 6.f * (ls.x + ls.y);
 }
 
 // ------------------------------------------------------ flow collision
@@ -211,8 +230,8 @@ __device__ __forceinline__ void flow_moments(FlowMoments& m, const float* f)
 #pragma unroll
     for (int a = 0; a < C; ++a) {
         const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
-        const float d = f[a] - f[Q - 1 - a];
-        const float s = f[a] + f[Q - 1 - a];
+        const float2 sd = fma2(f2(1.f, -1.f), f2(f[Q - 1 - a], f[Q - 1 - a]), f2(f[a], f[a]));
+        const float s = sd.x, d = sd.y;  // f_a + f_opp, f_a - f_opp
         m.P += s;
         if (cx) m.J[0] += cx * d;
         if (cy) m.J[1] += cy * d;
@@ -225,7 +244,6 @@ __device__ __forceinline__ void flow_moments(FlowMoments& m, const float* f)
         if (cy * cz) m.Pyz += (cy * cz) * s;
     }
 }
-
 
 // Per-cell results of the collision set-up that the output loops need.
 struct CellState {
@@ -454,33 +472,87 @@ struct SoAOut {
     __device__ __forceinline__ void operator()(int a, float v) const { base[a * stride] = v; }
 };
 
-template <int D, class GSrc, class Out>
-__device__ __forceinline__ void collide_outputs(const DevParams& p, const CellState& s, const float dh[27],
+// The outputs are formed for each direction a together with its opposite
+// (c -> -c, same weight): (a, opp(a)) are the two lanes of the paired FP32
+// arithmetic, and the shared factors (c.u, (c.u)^2, c.G, c.F, c.n) are
+// computed once per pair.
+// dh source: the register array of flow_collide, or a copy parked in shared
+// memory (strided per thread) to lower register pressure in the output loop
+struct DhArray {
+    const float* v;
+    __device__ __forceinline__ float operator[](int a) const { return v[a]; }
+};
+struct DhStrided {
+    const float* base;
+    int stride;
+    __device__ __forceinline__ float operator[](int a) const { return base[a * stride]; }
+};
+
+template <int D, class GSrc, class Out, class DH>
+__device__ __forceinline__ void collide_outputs(const DevParams& p, const CellState& s, const DH& dh,
                                                 const FlowMoments& m, const GSrc& gin, float gsum_hi,
                                                 float gsum_lo, const Out& fout, const Out& gout)
 {
     constexpr int Q = Lat<D>::Q;
     constexpr int C = Q / 2;
-    float fs = 0.f, gs = 0.f, gl = 0.f;
+    const float2 rcs2 = f2(s.rcs2, s.rcs2);
+    const float2 itau = f2(p.inv_tau_phi, p.inv_tau_phi);
+    const float2 phi2 = f2(s.phi, s.phi);
+    const float2 pm1 = f2(1.f, -1.f);
+    const float m15uu = -1.5f * s.uu;
+    float2 fs = f2(0.f, 0.f), gs = f2(0.f, 0.f), gl = f2(0.f, 0.f);
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        if (a == C) continue;
-        const float gd = gamma_dev<D>(s, a);
-        const float fv = flow_post<D>(s, dh, a, gd);
-        const float gv = phase_post<D>(p, s, a, gin(a), gd);
-        fout(a, fv);
-        gout(a, gv);
-        fs += fv;
-        // TwoSum (Knuth): the mass sum keeps its rounding error exactly, so a
-        // uniform field, whose every cell would round the same way, cannot drift
-        const float t = gs + gv;
-        const float bb = t - gs;
-        gl += (gs - (t - bb)) + (gv - bb);
-        gs = t;
+    for (int a = 0; a < C; ++a) {
+        const int b = Q - 1 - a;
+        const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
+        const float w = Lat<D>::w(a);
+        const float2 w2 = f2(w, w);
+        // equilibrium deviation Gamma - w = w [3 c.u + 4.5 (c.u)^2 - 1.5 u^2], lanes (c, -c)
+        const float cu = cx * s.u[0] + cy * s.u[1] + cz * s.u[2];
+        const float X = fmaf(4.5f * cu, cu, m15uu);
+        const float2 gd = mul2(w2, fma2(f2(3.f, -3.f), f2(cu, cu), f2(X, X)));
+        const float2 wgd = add2(w2, gd);
+        // Xi = (Gamma - w)(c - u).G + Gamma (c - u).F
+        const float cG0 = cx * s.G[0] + cy * s.G[1] + cz * s.G[2];
+        const float cF0 = cx * s.F[0] + cy * s.F[1] + cz * s.F[2];
+        const float2 cG = fma2(pm1, f2(cG0, cG0), f2(-s.uG, -s.uG));
+        const float2 cF = fma2(pm1, f2(cF0, cF0), f2(-s.uF, -s.uF));
+        const float2 xi = fma2(gd, cG, mul2(wgd, cF));
+        // E(u) - w telescoped over the axes, lanes (c, -c)
+        const float2 exs = f2(s.ew[0][cx + 1], s.ew[0][1 - cx]);
+        const float2 eys = f2(s.ew[1][cy + 1], s.ew[1][1 - cy]);
+        const float wx = (float)w1d(cx), wy = (float)w1d(cy), wz = (float)w1d(cz);
+        const float2 ex = add2(f2(wx, wx), exs);
+        float2 ew;
+        if (D == 3) {
+            const float2 ezs = f2(s.ew[2][cz + 1], s.ew[2][1 - cz]);
+            const float2 ey = add2(f2(wy, wy), eys);
+            ew = fma2(mul2(ex, ey), ezs, fma2(mul2(ex, eys), f2(wz, wz), mul2(exs, f2(wy * wz, wy * wz))));
+        } else {
+            ew = fma2(ex, eys, mul2(exs, f2(wy, wy)));
+        }
+        // f'* = rho cs2 (E - w + dh) + w p_h + Xi/2
+        const float wph = w * s.ph;
+        const float2 fo = fma2(rcs2, add2(ew, f2(dh[a], dh[b])), fma2(f2(0.5f, 0.5f), xi, f2(wph, wph)));
+        // g* = g + (phi Gamma - g)/tau + w (c.n) lambda 4 phi (1-phi)/W
+        const float cn0 = cx * s.n[0] + cy * s.n[1] + cz * s.n[2];
+        const float ws = w * s.sharp;
+        const float2 gi = f2(gin(a), gin(b));
+        const float2 go = fma2(f2(ws, ws), mul2(pm1, f2(cn0, cn0)), fma2(itau, fma2(phi2, wgd, neg2(gi)), gi));
+        fout(a, fo.x);
+        fout(b, fo.y);
+        gout(a, go.x);
+        gout(b, go.y);
+        fs = add2(fs, fo);
+        two_sum2(gs, gl, go);
     }
-    // target totals: P + u.G (flow) and the incoming sum (phase field)
-    fout(C, (m.P + s.uG) - fs);
-    gout(C, ((gsum_hi - gs) + (gsum_lo - gl)));
+    // target totals: P + u.G (flow) and the incoming sum (phase field); the
+    // rest populations take the difference (conservation identities above)
+    fout(C, (m.P + s.uG) - (fs.x + fs.y));
+    float t = gs.x + gs.y;  // combine the lanes exactly
+    const float bb = t - gs.x;
+    const float e = (gs.x - (t - bb)) + (gs.y - bb);
+    gout(C, (gsum_hi - t) + (gsum_lo - (gl.x + gl.y + e)));
 }
 
 }  // namespace lbmp

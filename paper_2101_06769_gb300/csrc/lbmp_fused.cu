@@ -37,14 +37,25 @@ namespace {
 #define LBMP_FUSED_TY 4
 #endif
 #ifndef LBMP_FUSED_MINB
-#define LBMP_FUSED_MINB 4
+#define LBMP_FUSED_MINB 3
+#endif
+// 1: f' of the plane is staged by cp.async into shared memory with the g
+// copies (frees the registers of 27 loads in flight); 0: loaded to registers
+#ifndef LBMP_FUSED_FSMEM
+#define LBMP_FUSED_FSMEM 0
+#endif
+// 1: the 27 post-collision moment differences are parked in shared memory
+// between the collision set-up and the output loop
+#ifndef LBMP_FUSED_DHSMEM
+#define LBMP_FUSED_DHSMEM 0
 #endif
 constexpr int TX = LBMP_FUSED_TX, TY = LBMP_FUSED_TY, NT = TX * TY;
 constexpr int RX = TX + 2, RY = TY + 2;
 constexpr int PLANE = RY * RX;
 constexpr int NRING = 2 * RX + 2 * TY;
 constexpr int Q3 = 27;
-constexpr size_t kSmemBytes = sizeof(float) * (2 * Q3 * NT + Q3 * NRING) + sizeof(float2) * 3 * PLANE;
+constexpr size_t kSmemBytes =
+    sizeof(float) * ((2 + LBMP_FUSED_FSMEM + LBMP_FUSED_DHSMEM) * Q3 * NT + Q3 * NRING) + sizeof(float2) * 3 * PLANE;
 static_assert(NRING <= NT, "one thread per ring cell");
 
 struct DirPtrs {
@@ -177,6 +188,19 @@ struct PullLoad {
 };
 
 template <bool Walls>
+struct FCopy {
+    const DirPtrs& D;
+    const Column& C;
+    const Plane& P;
+    float* fbuf;
+    template <int a>
+    __device__ __forceinline__ void step() const
+    {
+        cp_async4(fbuf + a * NT, pulled<Walls, a>(D.fin, C, P));
+    }
+};
+
+template <bool Walls>
 struct RingCopy {
     const DirPtrs& D;
     const Column& C;
@@ -268,6 +292,8 @@ __device__ __forceinline__ void fused_segment(const DevParams& p, const DirPtrs&
     float* gS = smem;                           // [2][27][NT]
     float* rS = smem + 2 * Q3 * NT;             // [27][NRING] ring cells' g of the plane being staged
     float2* phiS = (float2*)(rS + Q3 * NRING);  // (hi, lo) [3][RY][RX]
+    float* fS = (float*)(phiS + 3 * PLANE);     // [27][NT] f' of the plane (LBMP_FUSED_FSMEM)
+    float* dS = fS + LBMP_FUSED_FSMEM * Q3 * NT;  // [27][NT] dh (LBMP_FUSED_DHSMEM)
     const int tid = T.tid, oslot = T.oslot, rslot = T.rslot;
     Column own, ring;
     set_column(own, p, pmod(x0 + T.tx, p.nx), pmod(y0 + T.ty, p.ny));
@@ -284,14 +310,29 @@ __device__ __forceinline__ void fused_segment(const DevParams& p, const DirPtrs&
         stage_issue(p, Dp, own, ring, tid, z + 1, gS + (cur ^ 1) * Q3 * NT, rS);
         Plane P;
         set_plane(P, p, z);
+        FlowMoments m;
+#if LBMP_FUSED_FSMEM
+        if (P.lo || P.hi)
+            Unroll<Q3>::run(FCopy<true>{Dp, own, P, fS + tid});
+        else
+            Unroll<Q3>::run(FCopy<false>{Dp, own, P, fS + tid});
+        cp_async_commit();
+        stage_finish(tid, oslot, rslot, gS + (cur ^ 1) * Q3 * NT, rS, phiS + sN * PLANE);
+        {
+            float fr[Q3];
+#pragma unroll
+            for (int a = 0; a < Q3; ++a) fr[a] = fS[a * NT + tid];
+            flow_moments<3>(m, fr);
+        }
+#else
         float fr[Q3];
         if (P.lo || P.hi)
             Unroll<Q3>::run(PullLoad<true>{Dp.fin, own, P, fr});
         else
             Unroll<Q3>::run(PullLoad<false>{Dp.fin, own, P, fr});
         stage_finish(tid, oslot, rslot, gS + (cur ^ 1) * Q3 * NT, rS, phiS + sN * PLANE);
-        FlowMoments m;
         flow_moments<3>(m, fr);
+#endif
         __syncthreads();
         if (valid) {
             float nh[Q3], nl[Q3];
@@ -309,8 +350,15 @@ __device__ __forceinline__ void fused_segment(const DevParams& p, const DirPtrs&
             float dh[27];
             flow_collide<3>(p, nh[13], grad, lap, m, s, dh);
             const int self = P.zs[1] + own.ys[1] + own.xs[1];
-            collide_outputs<3>(p, s, dh, m, GFromStrided{gS + cur * Q3 * NT + tid, NT}, nh[13], nl[13],
+#if LBMP_FUSED_DHSMEM
+#pragma unroll
+            for (int a = 0; a < Q3; ++a) dS[a * NT + tid] = dh[a];
+            collide_outputs<3>(p, s, DhStrided{dS + tid, NT}, m, GFromStrided{gS + cur * Q3 * NT + tid, NT}, nh[13],
+                               nl[13], PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self});
+#else
+            collide_outputs<3>(p, s, DhArray{dh}, m, GFromStrided{gS + cur * Q3 * NT + tid, NT}, nh[13], nl[13],
                                PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self});
+#endif
         }
         __syncthreads();
         const int t = sP;

@@ -146,7 +146,7 @@ __device__ __forceinline__ void fused2_segment(const DevParams& p, const DirPtrs
             float dh[27];
             flow_collide<2>(p, nh[4], grad, lap, m, s, dh);
             const int self = R.ys[1] + own.xs[1];
-            collide_outputs<2>(p, s, dh, m, GFromStrided{gS + cur * Q2 * TX2 + tid, TX2}, nh[4], nl[4],
+            collide_outputs<2>(p, s, DhArray{dh}, m, GFromStrided{gS + cur * Q2 * TX2 + tid, TX2}, nh[4], nl[4],
                                PtrOut{D.fout, self}, PtrOut{D.gout, self});
         }
         __syncthreads();

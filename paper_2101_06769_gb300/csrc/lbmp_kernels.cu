@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(128) step_simple_kernel(DevParams p, const flo
     float gr[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) gr[a] = gin[pull_index<D>(p, a, x, y, z, i)];
-    collide_outputs<D>(p, s, dh, m, GFromArray{gr}, nh[Q / 2], nl[Q / 2], SoAOut{fout + i, p.N},
+    collide_outputs<D>(p, s, DhArray{dh}, m, GFromArray{gr}, nh[Q / 2], nl[Q / 2], SoAOut{fout + i, p.N},
                        SoAOut{gout + i, p.N});
 }
 
