@@ -151,7 +151,11 @@ int lbmp_create(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* 
         if (!grid->periodic[k]) return fail(LBMP_ERR_INVALID_ARG, "horizontal axes must be periodic");
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
     if (N > (1LL << 31) - 1) return fail(LBMP_ERR_INVALID_ARG, "more than 2^31-1 cells");
-    if (params->storage != LBMP_FP32) return fail(LBMP_ERR_UNSUPPORTED, "storage form not available in this build");
+    if (params->storage != LBMP_FP32 && params->storage != LBMP_FP16_SHIFTED && params->storage != LBMP_BF16_SHIFTED)
+        return fail(LBMP_ERR_INVALID_ARG, "unknown storage form");
+    // shifted codes are staged as 32-bit words holding two neighbouring cells
+    if (params->storage != LBMP_FP32 && (grid->nx & 1))
+        return fail(LBMP_ERR_INVALID_ARG, "16-bit storage needs an even nx");
     if (params->flags & ~7u) return fail(LBMP_ERR_INVALID_ARG, "unknown flag bits");
 
     lbmp_handle* h = new (std::nothrow) lbmp_handle();
@@ -179,7 +183,7 @@ int lbmp_create(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* 
         delete h;
         return cuda_fail(e, "cudaGetDevice");
     }
-    const size_t pop = sizeof(float) * (size_t)h->Q * (size_t)N;
+    const size_t pop = lbmp::set_bytes(h);
     for (int k = 0; k < 2; ++k) {
         e = cudaMalloc(&h->f[k], pop);
         if (e == cudaSuccess) e = cudaMalloc(&h->g[k], pop);
@@ -377,7 +381,7 @@ int lbmp_set_state(lbmp_handle* h, const double* f, const double* g)
 size_t lbmp_state_bytes(const lbmp_handle* h)
 {
     if (!h) return 0;
-    return 2 * sizeof(float) * (size_t)h->Q * (size_t)h->N;
+    return 2 * lbmp::set_bytes(h);
 }
 
 int lbmp_upload(lbmp_handle* h, const void* host, size_t bytes)

@@ -42,7 +42,7 @@ struct lbmp_batch {
 
 namespace {
 
-size_t state_bytes(const lbmp_handle* h) { return 4 * sizeof(float) * (size_t)h->Q * (size_t)h->N; }
+size_t state_bytes(const lbmp_handle* h) { return 2 * lbmp::set_bytes(h) * 2; }  // f' and g, two sets each
 
 void drop_graphs(lbmp_batch* b)
 {
@@ -182,6 +182,8 @@ LBMP_API int lbmp_batch_add(lbmp_batch* b, lbmp_handle* h, long steps)
     if (steps <= 0) return batch_fail(LBMP_ERR_INVALID_ARG, "steps must be > 0");
     if (h->device != b->device) return batch_fail(LBMP_ERR_INVALID_ARG, "domain lives on another device");
     if ((int)b->members.size() >= kMaxMembers) return batch_fail(LBMP_ERR_INVALID_ARG, "batch is full");
+    if (h->params.storage != LBMP_FP32)
+        return batch_fail(LBMP_ERR_UNSUPPORTED, "batch members must use FP32 storage");
     size_t used = 0;
     for (const Member& m : b->members) {
         if (m.h == h) return batch_fail(LBMP_ERR_INVALID_ARG, "domain is already a member");

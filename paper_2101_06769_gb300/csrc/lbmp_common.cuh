@@ -16,6 +16,8 @@
 //     differences, and E(u) - w is a telescoped product of per-axis terms.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -74,30 +76,273 @@ struct DevParams {
 // Post-streaming population a at cell (x,y,z) lives in the buffer written by
 // the previous step at the upstream cell x - c_a (pull); across a half-way
 // bounce-back wall it is the opposite population of the cell itself.
+// Returns the cell holding it and sets dir to the direction slot.
 template <int D>
-__device__ __forceinline__ long long pull_index(const DevParams& p, int a, int x, int y, int z, long long self)
+__device__ __forceinline__ long long pull_src(const DevParams& p, int a, int x, int y, int z, long long self,
+                                              int& dir)
 {
     const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
     int xs = x - cx;
     xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
+    dir = a;
     if (D == 3) {
         int ys = y - cy;
         ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
         int zs = z - cz;
         if (zs < 0 || zs >= p.nz) {
-            if (!p.vert_periodic) return (long long)Lat<D>::opp(a) * p.N + self;
+            if (!p.vert_periodic) {
+                dir = Lat<D>::opp(a);
+                return self;
+            }
             zs = zs < 0 ? zs + p.nz : zs - p.nz;
         }
-        return (long long)a * p.N + ((long long)zs * p.ny + ys) * p.nx + xs;
+        return ((long long)zs * p.ny + ys) * p.nx + xs;
     } else {
         int ys = y - cy;
         if (ys < 0 || ys >= p.ny) {
-            if (!p.vert_periodic) return (long long)Lat<D>::opp(a) * p.N + self;
+            if (!p.vert_periodic) {
+                dir = Lat<D>::opp(a);
+                return self;
+            }
             ys = ys < 0 ? ys + p.ny : ys - p.ny;
         }
-        return (long long)a * p.N + (long long)ys * p.nx + xs;
+        return (long long)ys * p.nx + xs;
     }
 }
+
+template <int D>
+__device__ __forceinline__ long long pull_index(const DevParams& p, int a, int x, int y, int z, long long self)
+{
+    int dir;
+    const long long c = pull_src<D>(p, a, x, y, z, self, dir);
+    return (long long)dir * p.N + c;
+}
+
+// Inverse of pull_src: the slot (cell, a) written by the cell (x,y,z) is read
+// as population dir of the returned cell (downstream x + c_a, or the cell
+// itself in the opposite direction when x + c_a lies across a wall).
+template <int D>
+__device__ __forceinline__ long long push_dst(const DevParams& p, int a, int x, int y, int z, long long self,
+                                              int& dir)
+{
+    const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
+    int xd = x + cx;
+    xd = xd < 0 ? xd + p.nx : (xd >= p.nx ? xd - p.nx : xd);
+    dir = a;
+    if (D == 3) {
+        int yd = y + cy;
+        yd = yd < 0 ? yd + p.ny : (yd >= p.ny ? yd - p.ny : yd);
+        int zd = z + cz;
+        if (zd < 0 || zd >= p.nz) {
+            if (!p.vert_periodic) {
+                dir = Lat<D>::opp(a);
+                return self;
+            }
+            zd = zd < 0 ? zd + p.nz : zd - p.nz;
+        }
+        return ((long long)zd * p.ny + yd) * p.nx + xd;
+    } else {
+        int yd = y + cy;
+        if (yd < 0 || yd >= p.ny) {
+            if (!p.vert_periodic) {
+                dir = Lat<D>::opp(a);
+                return self;
+            }
+            yd = yd < 0 ? yd + p.ny : yd - p.ny;
+        }
+        return (long long)yd * p.nx + xd;
+    }
+}
+
+// ------------------------------------------------------------- storage
+// Population storage forms (lbmp_storage).
+//
+// FP32: population a of cell i at base[a N + i].
+//
+// Shifted 16-bit (FP16 or BF16).  Every lattice weight is w_a = W_a / den
+// with W_a a power of two (D3Q27: 64, 16, 4, 1 over 216; D2Q9: 16, 4, 1 over
+// 36).  A cell stores one FP32 reference R at base[i] and, for each moving
+// direction a, a 16-bit code q_a at ((u16*)(base + N))[slot(a) N + i] with
+// slot(a) = a - (a > C).  The values are
+//     moving a:  v_a = W_a (R + s q_a),        rest:  v_C = W_C R,
+// so q holds only the deviation of v_a/W_a from the rest ratio v_C/W_C (the
+// O(c.u) equilibrium part and the non-equilibrium part), while the O(p_h)
+// pressure level of f' and the O(phi) level of g stay in the FP32 reference.
+// W_a R and W_a s q_a are exact, so a decoded value is rounded once.  The
+// writer encodes q_a = S (v_a/W_a - v_C/W_C) (s = 1/S a power of two that
+// keeps FP16 codes of a light phase out of the subnormal range) and then sets
+// R = (T - s sum_a W_a q_a)/den from the cell's total T, so the decoded
+// populations of a cell add up to T to within one rounding: the 16-bit codes
+// cannot bias mass or pressure.
+template <int D>
+__host__ __device__ constexpr float wint(int a)  // W_a = den w_a
+{
+    return (Lat<D>::cx(a) == 0 ? 4.f : 1.f) * (Lat<D>::cy(a) == 0 ? 4.f : 1.f) *
+           ((D == 3 && Lat<D>::cz(a) == 0) ? 4.f : 1.f);
+}
+template <int D>
+__host__ __device__ constexpr float wden()
+{
+    return D == 3 ? 216.f : 36.f;
+}
+
+struct StoreF32 {
+    static constexpr bool shifted = false;
+};
+struct StoreF16 {
+    static constexpr bool shifted = true;
+    static constexpr float S = 1048576.f, s = 1.f / 1048576.f;  // 2^20
+    // byte-permute selectors moving the low / high half of a word to bits 0..15
+    static constexpr unsigned kSelLo = 0x4410u, kSelHi = 0x4432u;
+    __device__ __forceinline__ static unsigned short enc(float q) { return __half_as_ushort(__float2half_rn(q)); }
+    __device__ __forceinline__ static float dec(unsigned short c) { return __half2float(__ushort_as_half(c)); }
+    __device__ __forceinline__ static float dec_word(unsigned w, unsigned sel)
+    {
+        return dec((unsigned short)__byte_perm(w, 0u, sel));
+    }
+};
+struct StoreBF16 {
+    static constexpr bool shifted = true;
+    static constexpr float S = 1.f, s = 1.f;  // BF16 has the FP32 exponent range
+    // selectors moving the low / high half of a word to bits 16..31 (zeros below)
+    static constexpr unsigned kSelLo = 0x1044u, kSelHi = 0x3244u;
+    __device__ __forceinline__ static unsigned short enc(float q)
+    {
+        return __bfloat16_as_ushort(__float2bfloat16_rn(q));
+    }
+    __device__ __forceinline__ static float dec(unsigned short c) { return __uint_as_float((unsigned)c << 16); }
+    __device__ __forceinline__ static float dec_word(unsigned w, unsigned sel)
+    {
+        return __uint_as_float(__byte_perm(w, 0u, sel));
+    }
+};
+
+// decoded value of moving population a from its code and the writer's reference
+template <int D, class St>
+__device__ __forceinline__ float dec_value(int a, float code_value, float R)
+{
+    const float W = wint<D>(a);
+    return fmaf(code_value, W * St::s, W * R);
+}
+
+// One population set in device memory (layout above).
+template <int D, class St>
+struct Pop {
+    float* base;
+    long long N;
+    __device__ __forceinline__ float load(int a, long long i) const
+    {
+        if constexpr (!St::shifted) {
+            return base[a * N + i];
+        } else {
+            constexpr int C = Lat<D>::Q / 2;
+            const float R = base[i];
+            if (a == C) return wint<D>(C) * R;
+            const unsigned short* q = (const unsigned short*)(base + N);
+            return dec_value<D, St>(a, St::dec(q[(a - (a > C)) * N + i]), R);
+        }
+    }
+    // the two exact parts W_a R and W_a s q_a of a shifted value (wq = 0 for the rest)
+    __device__ __forceinline__ void load_parts(int a, long long i, float& wr, float& wq) const
+    {
+        constexpr int C = Lat<D>::Q / 2;
+        const float W = wint<D>(a);
+        wr = W * base[i];
+        wq = 0.f;
+        if (a != C) {
+            const unsigned short* q = (const unsigned short*)(base + N);
+            wq = St::dec(q[(a - (a > C)) * N + i]) * (W * St::s);
+        }
+    }
+};
+
+// phi = sum_a v_a for shifted storage, from the exact parts of each value
+// (v_a = W_a R + W_a s q_a): the reference parts, of comparable size, in the
+// Fast2Sum chain of phi_sum (rest first); the code parts, small deviations,
+// in a plain sum added by one TwoSum.  The result is the sum of what the
+// writers stored to within the final rounding of the (hi, lo) pair, so the
+// one rounding of each decoded value (which the collision uses) never
+// enters mass.  get(a, wr, wq) returns the parts.
+template <int D, class Get>
+__device__ __forceinline__ void phi_sum_shifted(const Get& get, float& hi, float& lo)
+{
+    constexpr int Q = Lat<D>::Q;
+    constexpr int C = Q / 2;
+    float wr, wq;
+    get(C, wr, wq);
+    hi = wr;
+    lo = 0.f;
+    float qs = 0.f;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        if (a == C) continue;
+        get(a, wr, wq);
+        const float s = hi + wr;
+        lo += wr - (s - hi);
+        hi = s;
+        qs += wq;
+    }
+    const float t = hi + qs;
+    const float bb = t - hi;
+    lo += (hi - (t - bb)) + (qs - bb);
+    hi = t;
+    const float s = hi + lo;
+    lo = lo - (s - hi);
+    hi = s;
+}
+
+// R = (th + tl - sq) / den with the subtraction error-free (TwoSum), so that
+// the decoded values of a cell add up to its total to within the roundings
+// of one addition and one division
+template <int D>
+__device__ __forceinline__ float ref_from_total(float th, float tl, float sq)
+{
+    const float d = th - sq;
+    const float bb = d - th;
+    const float e = (th - (d - bb)) + (-sq - bb);
+    return (d + (e + tl)) / wden<D>();
+}
+
+// Encoder of one cell's post-collision values: the moving directions in the
+// order the collision emits them, then finish(th, tl) with the cell's
+// conserved total th + tl in place of the rest value.  off = S v_C/W_C is
+// the cell's rest ratio (the rest value from its formula); sq accumulates
+// s sum_a W_a q_a (exact products, small terms).
+template <int D, class St>
+struct EncSoA {  // cell i of a Pop: R at base + i, codes at stride N
+    static constexpr bool kTotal = true;
+    float* R;
+    unsigned short* q;
+    long long N;
+    float off;
+    mutable float sq;
+    __device__ __forceinline__ void operator()(int a, float v) const
+    {
+        constexpr int C = Lat<D>::Q / 2;
+        const float W = wint<D>(a);
+        const unsigned short c = St::enc(fmaf(v, St::S / W, -off));
+        q[(a - (a > C)) * N] = c;
+        sq += St::dec(c) * (W * St::s);
+    }
+    __device__ __forceinline__ void finish(float th, float tl) const { *R = ref_from_total<D>(th, tl, sq); }
+};
+template <int D, class St>
+struct EncPtr {  // per-direction code arrays (entry C unused), one cell index
+    static constexpr bool kTotal = true;
+    unsigned short* const* qb;
+    float* R;
+    int self;
+    float off;
+    mutable float sq;
+    __device__ __forceinline__ void operator()(int a, float v) const
+    {
+        const float W = wint<D>(a);
+        const unsigned short c = St::enc(fmaf(v, St::S / W, -off));
+        qb[a][self] = c;
+        sq += St::dec(c) * (W * St::s);
+    }
+    __device__ __forceinline__ void finish(float th, float tl) const { R[self] = ref_from_total<D>(th, tl, sq); }
+};
 
 // Neighbour of the phi stencil: periodic wrap, or the mirrored ghost at a
 // wall (the ghost equals the wall cell, reading A17).
@@ -442,6 +687,20 @@ __device__ __forceinline__ float phase_post(const DevParams& p, const CellState&
     return g + p.inv_tau_phi * (s.phi * (w + gdev) - g) + w * cn * s.sharp;
 }
 
+// Offsets S v_C/W_C of the shifted encoders: the rest populations of f' and
+// g from their formulas (the rest value emitted last equals them to within
+// rounding).
+template <int D, class St, class GSrc>
+__device__ __forceinline__ void rest_offsets(const DevParams& p, const CellState& s, const float dh[27],
+                                             const GSrc& gin, float& off_f, float& off_g)
+{
+    constexpr int C = Lat<D>::Q / 2;
+    const float gd = gamma_dev<D>(s, C);
+    const float k = St::S / wint<D>(C);
+    off_f = k * flow_post<D>(s, dh, C, gd);
+    off_g = k * phase_post<D>(p, s, C, gin(C), gd);
+}
+
 // All post-collision populations of one cell.  The moving populations follow
 // the formulas above; the rest population (a = Q/2) is formed last from the
 // exact conservation identities of the collision,
@@ -462,11 +721,13 @@ struct GFromStrided {
     __device__ __forceinline__ float operator()(int a) const { return base[a * stride]; }
 };
 struct PtrOut {  // per-direction array bases, one cell index
+    static constexpr bool kTotal = false;
     float* const* base;
     int self;
     __device__ __forceinline__ void operator()(int a, float v) const { base[a][self] = v; }
 };
 struct SoAOut {
+    static constexpr bool kTotal = false;
     float* base;
     long long stride;
     __device__ __forceinline__ void operator()(int a, float v) const { base[a * stride] = v; }
@@ -547,12 +808,18 @@ __device__ __forceinline__ void collide_outputs(const DevParams& p, const CellSt
         two_sum2(gs, gl, go);
     }
     // target totals: P + u.G (flow) and the incoming sum (phase field); the
-    // rest populations take the difference (conservation identities above)
-    fout(C, (m.P + s.uG) - (fs.x + fs.y));
-    float t = gs.x + gs.y;  // combine the lanes exactly
-    const float bb = t - gs.x;
-    const float e = (gs.x - (t - bb)) + (gs.y - bb);
-    gout(C, (gsum_hi - t) + (gsum_lo - (gl.x + gl.y + e)));
+    // rest populations take the difference (conservation identities above),
+    // or a shifted encoder takes the totals themselves
+    if constexpr (Out::kTotal) {
+        fout.finish(m.P, s.uG);
+        gout.finish(gsum_hi, gsum_lo);
+    } else {
+        fout(C, (m.P + s.uG) - (fs.x + fs.y));
+        float t = gs.x + gs.y;  // combine the lanes exactly
+        const float bb = t - gs.x;
+        const float e = (gs.x - (t - bb)) + (gs.y - bb);
+        gout(C, (gsum_hi - t) + (gsum_lo - (gl.x + gl.y + e)));
+    }
 }
 
 }  // namespace lbmp

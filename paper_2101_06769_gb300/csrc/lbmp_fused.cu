@@ -24,39 +24,14 @@
 // The per-cell arithmetic (lbmp_common.cuh) and its summation orders are the
 // ones of the reference pair in lbmp_kernels.cu, so the two paths agree.
 #include "lbmp_internal.h"
+#include "lbmp_tile.cuh"
 
 namespace lbmp {
 
 namespace {
 
-// tile shape and CTAs per SM (compile-time; the defaults are the measured best)
-#ifndef LBMP_FUSED_TX
-#define LBMP_FUSED_TX 32
-#endif
-#ifndef LBMP_FUSED_TY
-#define LBMP_FUSED_TY 4
-#endif
-#ifndef LBMP_FUSED_MINB
-#define LBMP_FUSED_MINB 3
-#endif
-// 1: f' of the plane is staged by cp.async into shared memory with the g
-// copies (frees the registers of 27 loads in flight); 0: loaded to registers
-#ifndef LBMP_FUSED_FSMEM
-#define LBMP_FUSED_FSMEM 0
-#endif
-// 1: the 27 post-collision moment differences are parked in shared memory
-// between the collision set-up and the output loop
-#ifndef LBMP_FUSED_DHSMEM
-#define LBMP_FUSED_DHSMEM 0
-#endif
-constexpr int TX = LBMP_FUSED_TX, TY = LBMP_FUSED_TY, NT = TX * TY;
-constexpr int RX = TX + 2, RY = TY + 2;
-constexpr int PLANE = RY * RX;
-constexpr int NRING = 2 * RX + 2 * TY;
-constexpr int Q3 = 27;
-constexpr size_t kSmemBytes =
-    sizeof(float) * ((2 + LBMP_FUSED_FSMEM + LBMP_FUSED_DHSMEM) * Q3 * NT + Q3 * NRING) + sizeof(float2) * 3 * PLANE;
-static_assert(NRING <= NT, "one thread per ring cell");
+using namespace tile;
+
 
 struct DirPtrs {
     const float* fin[Q3];
@@ -73,93 +48,6 @@ struct DirPtrs {
 struct FusedArgs {
     int tiles_x, tiles_y, chunk, nitems;
 };
-
-__device__ __forceinline__ void cp_async4(float* smem, const float* gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-__device__ __forceinline__ int pmod(int v, int n)
-{
-    const int r = v % n;
-    return r < 0 ? r + n : r;
-}
-
-// A column (x, y) and its upstream neighbours: xs[c+1] = x - c and
-// ys[c+1] = (y - c) nx, wrapped periodically.
-struct Column {
-    int xs[3], ys[3];
-};
-
-__device__ __forceinline__ void set_column(Column& C, const DevParams& p, int x, int y)
-{
-    C.xs[0] = x + 1 == p.nx ? 0 : x + 1;
-    C.xs[1] = x;
-    C.xs[2] = x == 0 ? p.nx - 1 : x - 1;
-    C.ys[0] = (y + 1 == p.ny ? 0 : y + 1) * p.nx;
-    C.ys[1] = y * p.nx;
-    C.ys[2] = (y == 0 ? p.ny - 1 : y - 1) * p.nx;
-}
-
-// A plane z and its upstream planes zs[c+1] = (z - c) nx ny; lo/hi flag the
-// bottom/top plane of a walled domain, where the population arriving across
-// the wall is the opposite population of the cell itself (half-way
-// bounce-back).
-struct Plane {
-    int zs[3];
-    bool lo, hi;
-};
-
-__device__ __forceinline__ void set_plane(Plane& P, const DevParams& p, int z)
-{
-    const int nxy = p.nx * p.ny;
-    P.lo = !p.vert_periodic && z == 0;
-    P.hi = !p.vert_periodic && z == p.nz - 1;
-    P.zs[0] = (z + 1 == p.nz ? 0 : z + 1) * nxy;
-    P.zs[1] = z * nxy;
-    P.zs[2] = (z == 0 ? p.nz - 1 : z - 1) * nxy;
-}
-
-// pointer to the post-streaming population a of the cell (column C, plane P);
-// Walls = false is the path of every plane that does not touch a wall
-template <bool Walls, int a>
-__device__ __forceinline__ const float* pulled(const float* const* base, const Column& C, const Plane& P)
-{
-    constexpr int cx = Lat<3>::cx(a), cy = Lat<3>::cy(a), cz = Lat<3>::cz(a);
-    if (Walls && ((cz == 1 && P.lo) || (cz == -1 && P.hi)))
-        return base[Lat<3>::opp(a)] + (P.zs[1] + C.ys[1] + C.xs[1]);
-    return base[a] + (P.zs[cz + 1] + C.ys[cy + 1] + C.xs[cx + 1]);
-}
-
-// compile-time loop over the directions (keeps base[a] a constant-bank operand)
-template <int N>
-struct Unroll {
-    template <class F>
-    __device__ __forceinline__ static void run(const F& f)
-    {
-        Unroll<N - 1>::run(f);
-        f.template step<N - 1>();
-    }
-};
-template <>
-struct Unroll<0> {
-    template <class F>
-    __device__ __forceinline__ static void run(const F&)
-    {
-    }
-};
-
-// plane whose phi stands for plane zz: periodic wrap, or the mirrored ghost
-// at a wall (reading A17)
-__device__ __forceinline__ int plane_src(const DevParams& p, int zz)
-{
-    if (zz >= 0 && zz < p.nz) return zz;
-    if (p.vert_periodic) return pmod(zz, p.nz);
-    return zz < 0 ? 0 : p.nz - 1;
-}
 
 template <bool Walls>
 struct StageCopy {
@@ -247,39 +135,6 @@ __device__ __forceinline__ void stage_finish(int tid, int oslot, int rslot, cons
     float hi, lo;
     phi_sum<3>([&](int a) { return gbuf[a * NT + tid]; }, hi, lo);
     phi_plane[oslot] = make_float2(hi, lo);
-}
-
-// per-thread geometry inside a tile: own cell and (for tid < NRING) ring cell
-struct ThreadGeo {
-    int tid, tx, ty, oslot, lx, ly, rslot;
-};
-
-__device__ __forceinline__ ThreadGeo thread_geo()
-{
-    ThreadGeo T;
-    T.tid = threadIdx.x;
-    T.tx = T.tid % TX;
-    T.ty = T.tid / TX;
-    T.oslot = (T.ty + 1) * RX + (T.tx + 1);
-    T.lx = T.ly = T.rslot = 0;
-    if (T.tid < NRING) {
-        const int r = T.tid;
-        if (r < RX) {
-            T.lx = r - 1;
-            T.ly = -1;
-        } else if (r < 2 * RX) {
-            T.lx = r - RX - 1;
-            T.ly = TY;
-        } else if (r < 2 * RX + TY) {
-            T.lx = -1;
-            T.ly = r - 2 * RX;
-        } else {
-            T.lx = TX;
-            T.ly = r - 2 * RX - TY;
-        }
-        T.rslot = (T.ly + 1) * RX + (T.lx + 1);
-    }
-    return T;
 }
 
 // One segment of work: planes [z0, z1) of the tile at (x0, y0) of the domain
@@ -448,7 +303,8 @@ LaunchCfg g_cfg;
 
 }  // namespace
 
-bool fused_supported(const lbmp_handle* h) { return h->D == 3 || h->D == 2; }
+// every FP32 domain; shifted 16-bit storage in 3-D (2-D runs the reference pair)
+bool fused_supported(const lbmp_handle* h) { return h->params.storage == LBMP_FP32 || h->D == 3; }
 
 __global__ void batch_epilogue_kernel(BatchDomain* table, int ndom)
 {
@@ -502,6 +358,7 @@ cudaError_t launch_batch_epilogue(BatchDomain* table, int ndom, cudaStream_t str
 
 cudaError_t launch_step_fused(lbmp_handle* h)
 {
+    if (h->params.storage != LBMP_FP32) return launch_step_fused16(h);
     if (h->D == 2) return launch_step_fused2(h);
     if (g_cfg.device != h->device) {
         cudaError_t e = cudaFuncSetAttribute(step_fused3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

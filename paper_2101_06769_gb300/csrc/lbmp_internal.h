@@ -42,6 +42,14 @@ struct BatchDomain {
     int tiles_x, tiles_y, chunk, item_begin, items;
 };
 
+// bytes of one population set (f' or g) in the handle's storage form
+inline size_t set_bytes(const lbmp_handle* h)
+{
+    const size_t N = (size_t)h->N, Q = (size_t)h->Q;
+    if (h->params.storage == LBMP_FP32) return sizeof(float) * Q * N;
+    return sizeof(float) * N + sizeof(unsigned short) * (Q - 1) * N;  // reference + 16-bit codes
+}
+
 // kernel launchers (return cudaError_t of the launch)
 cudaError_t launch_phi_pass(lbmp_handle* h);
 cudaError_t launch_step_simple(lbmp_handle* h);
@@ -57,6 +65,7 @@ bool fused_supported(const lbmp_handle* h);
 int batch3_tile_x();
 int batch3_tile_y();
 cudaError_t launch_step_fused2(lbmp_handle* h);
+cudaError_t launch_step_fused16(lbmp_handle* h);  // shifted 16-bit storage, D3Q27
 int batch2_tile_x();
 cudaError_t prepare_batch2(int device);
 cudaError_t launch_batch2(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream);

@@ -12,24 +12,44 @@
 namespace lbmp {
 
 // ------------------------------------------------------------- phi pass
-template <int D>
-__global__ void phi_pass_kernel(DevParams p, const float* __restrict__ g, float* __restrict__ phi)
+// value of the post-streaming population a of cell (x,y,z)
+template <int D, class St>
+__device__ __forceinline__ float pulled_value(const DevParams& p, const Pop<D, St>& set, int a, int x, int y, int z,
+                                              long long i)
+{
+    int dir;
+    const long long c = pull_src<D>(p, a, x, y, z, i, dir);
+    return set.load(dir, c);
+}
+
+template <int D, class St>
+__global__ void phi_pass_kernel(DevParams p, Pop<D, St> g, float* __restrict__ phi)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= p.N) return;
     int x, y, z;
     cell_xyz(p, i, x, y, z);
     float hi, lo;
-    phi_sum<D>([&](int a) { return g[pull_index<D>(p, a, x, y, z, i)]; }, hi, lo);
+    if constexpr (St::shifted) {
+        phi_sum_shifted<D>(
+            [&](int a, float& wr, float& wq) {
+                int dir;
+                const long long c = pull_src<D>(p, a, x, y, z, i, dir);
+                g.load_parts(dir, c, wr, wq);
+            },
+            hi, lo);
+    } else {
+        phi_sum<D>([&](int a) { return pulled_value<D, St>(p, g, a, x, y, z, i); }, hi, lo);
+    }
     phi[i] = hi;  // phi = sum_a g_a (Sec. 2.2), as hi + lo
     phi[p.N + i] = lo;
 }
 
 // ----------------------------------------------------- reference step
-template <int D>
-__global__ void __launch_bounds__(128) step_simple_kernel(DevParams p, const float* __restrict__ fin,
-                                                          const float* __restrict__ gin, float* __restrict__ fout,
-                                                          float* __restrict__ gout, const float* __restrict__ phi)
+template <int D, class St>
+__global__ void __launch_bounds__(128) step_simple_kernel(DevParams p, Pop<D, St> fin, Pop<D, St> gin,
+                                                          Pop<D, St> fout, Pop<D, St> gout,
+                                                          const float* __restrict__ phi)
 {
     constexpr int Q = Lat<D>::Q;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -47,7 +67,7 @@ __global__ void __launch_bounds__(128) step_simple_kernel(DevParams p, const flo
     stencil_from_nb<D>(nh, nl, grad, lap);
     float fr[Q];
 #pragma unroll
-    for (int a = 0; a < Q; ++a) fr[a] = fin[pull_index<D>(p, a, x, y, z, i)];
+    for (int a = 0; a < Q; ++a) fr[a] = pulled_value<D, St>(p, fin, a, x, y, z, i);
     FlowMoments m;
     flow_moments<D>(m, fr);
     CellState s;
@@ -55,36 +75,75 @@ __global__ void __launch_bounds__(128) step_simple_kernel(DevParams p, const flo
     flow_collide<D>(p, nh[Q / 2], grad, lap, m, s, dh);
     float gr[Q];
 #pragma unroll
-    for (int a = 0; a < Q; ++a) gr[a] = gin[pull_index<D>(p, a, x, y, z, i)];
-    collide_outputs<D>(p, s, DhArray{dh}, m, GFromArray{gr}, nh[Q / 2], nl[Q / 2], SoAOut{fout + i, p.N},
-                       SoAOut{gout + i, p.N});
+    for (int a = 0; a < Q; ++a) gr[a] = pulled_value<D, St>(p, gin, a, x, y, z, i);
+    if constexpr (St::shifted) {
+        float off_f, off_g;
+        rest_offsets<D, St>(p, s, dh, GFromArray{gr}, off_f, off_g);
+        collide_outputs<D>(p, s, DhArray{dh}, m, GFromArray{gr}, nh[Q / 2], nl[Q / 2],
+                           EncSoA<D, St>{fout.base + i, (unsigned short*)(fout.base + p.N) + i, p.N, off_f, 0.f},
+                           EncSoA<D, St>{gout.base + i, (unsigned short*)(gout.base + p.N) + i, p.N, off_g, 0.f});
+    } else {
+        collide_outputs<D>(p, s, DhArray{dh}, m, GFromArray{gr}, nh[Q / 2], nl[Q / 2], SoAOut{fout.base + i, p.N},
+                           SoAOut{gout.base + i, p.N});
+    }
 }
 
 static unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
 
-cudaError_t launch_phi_pass(lbmp_handle* h)
+// Calls F::template run<D, St>() for the handle's lattice and storage form.
+template <class F>
+static cudaError_t dispatch(const lbmp_handle* h, const F& f)
 {
-    const int B = 256;
-    if (h->D == 3)
-        phi_pass_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->g[h->parity], h->phi);
-    else
-        phi_pass_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->g[h->parity], h->phi);
-    return cudaGetLastError();
+    const int st = h->params.storage;
+    if (h->D == 3) {
+        if (st == LBMP_FP16_SHIFTED) return f.template run<3, StoreF16>();
+        if (st == LBMP_BF16_SHIFTED) return f.template run<3, StoreBF16>();
+        return f.template run<3, StoreF32>();
+    }
+    if (st == LBMP_FP16_SHIFTED) return f.template run<2, StoreF16>();
+    if (st == LBMP_BF16_SHIFTED) return f.template run<2, StoreBF16>();
+    return f.template run<2, StoreF32>();
 }
+
+template <int D, class St>
+static Pop<D, St> pop_of(const lbmp_handle* h, float* base)
+{
+    return Pop<D, St>{base, h->N};
+}
+
+struct PhiPassL {
+    lbmp_handle* h;
+    template <int D, class St>
+    cudaError_t run() const
+    {
+        const int B = 256;
+        phi_pass_kernel<D, St><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, pop_of<D, St>(h, h->g[h->parity]),
+                                                                       h->phi);
+        return cudaGetLastError();
+    }
+};
+
+cudaError_t launch_phi_pass(lbmp_handle* h) { return dispatch(h, PhiPassL{h}); }
+
+struct StepSimpleL {
+    lbmp_handle* h;
+    template <int D, class St>
+    cudaError_t run() const
+    {
+        const int B = 128;
+        const int s = h->parity, d = 1 - h->parity;
+        step_simple_kernel<D, St><<<grid_for(h->N, B), B, 0, h->stream>>>(
+            h->dp, pop_of<D, St>(h, h->f[s]), pop_of<D, St>(h, h->g[s]), pop_of<D, St>(h, h->f[d]),
+            pop_of<D, St>(h, h->g[d]), h->phi);
+        return cudaGetLastError();
+    }
+};
 
 cudaError_t launch_step_simple(lbmp_handle* h)
 {
     cudaError_t e = launch_phi_pass(h);
     if (e != cudaSuccess) return e;
-    const int B = 128;
-    const int s = h->parity, d = 1 - h->parity;
-    if (h->D == 3)
-        step_simple_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->f[s], h->g[s], h->f[d], h->g[d],
-                                                                      h->phi);
-    else
-        step_simple_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->f[s], h->g[s], h->f[d], h->g[d],
-                                                                      h->phi);
-    return cudaGetLastError();
+    return dispatch(h, StepSimpleL{h});
 }
 
 // ---------------------------------------------------- initial conditions
@@ -108,9 +167,11 @@ struct InitArgs {
 __device__ __forceinline__ double tanh_prof(double d, double W) { return 0.5 * (1.0 + tanh(2.0 * d / W)); }
 
 // Initial conditions (reading A18): tanh phi profiles, f' = f'_eq(p, rho, u),
-// g = g_eq(phi, u), written to the slots the next step pulls from.
+// g = g_eq(phi, u), written to the FP32 slots the next step pulls from, or
+// (cf != null) as canonical FP64 arrays [a][cell] for the shifted encoder.
 template <int D>
-__global__ void init_kernel(DevParams p, InitArgs A, float* __restrict__ f, float* __restrict__ g)
+__global__ void init_kernel(DevParams p, InitArgs A, float* __restrict__ f, float* __restrict__ g,
+                            double* __restrict__ cf, double* __restrict__ cg)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= p.N) return;
@@ -199,9 +260,16 @@ __global__ void init_kernel(DevParams p, InitArgs A, float* __restrict__ f, floa
         const double cu = Lat<D>::cx(a) * u[0] + Lat<D>::cy(a) * u[1] + Lat<D>::cz(a) * u[2];
         // Gamma - w = w [c.u/cs2 + ((c.u)^2 - cs2 u^2)/(2 cs4)]
         const double gdev = w * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-        const long long slot = pull_index<D>(p, a, x, y, z, i);
-        f[slot] = (float)(w * pr + rho * (1.0 / 3.0) * gdev);  // f'_eq (Sec. 2.3)
-        g[slot] = (float)(phi * (w + gdev));                   // g_eq (Sec. 2.2)
+        const double fe = w * pr + rho * (1.0 / 3.0) * gdev;  // f'_eq (Sec. 2.3)
+        const double ge = phi * (w + gdev);                    // g_eq (Sec. 2.2)
+        if (cf) {
+            cf[(long long)a * p.N + i] = fe;
+            cg[(long long)a * p.N + i] = ge;
+        } else {
+            const long long slot = pull_index<D>(p, a, x, y, z, i);
+            f[slot] = (float)fe;
+            g[slot] = (float)ge;
+        }
     }
 }
 
@@ -218,16 +286,50 @@ cudaError_t launch_init(lbmp_handle* h, int case_id, const double* args, unsigne
     A.seed = seed;
     A.case_id = case_id;
     const int B = 128;
+    if (h->params.storage == LBMP_FP32) {
+        if (h->D == 3)
+            init_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, A, h->f[h->parity], h->g[h->parity],
+                                                                   nullptr, nullptr);
+        else
+            init_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, A, h->f[h->parity], h->g[h->parity],
+                                                                   nullptr, nullptr);
+        return cudaGetLastError();
+    }
+    // shifted storage: canonical FP64 state first, then the per-cell encoder
+    const size_t n = (size_t)h->Q * (size_t)h->N;
+    double* c = nullptr;
+    cudaError_t e = cudaMallocAsync(&c, 2 * n * sizeof(double), h->stream);
+    if (e != cudaSuccess) return e;
     if (h->D == 3)
-        init_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, A, h->f[h->parity], h->g[h->parity]);
+        init_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, A, nullptr, nullptr, c, c + n);
     else
-        init_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, A, h->f[h->parity], h->g[h->parity]);
-    return cudaGetLastError();
+        init_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, A, nullptr, nullptr, c, c + n);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_set_state(h, c, c + n);
+    cudaFreeAsync(c, h->stream);
+    return e;
 }
 
 // ------------------------------------------------------ state exchange
+// canonical (post-streaming, [a][cell]) FP64 <- stored state
+template <int D, class St>
+__global__ void get_state_kernel(DevParams p, Pop<D, St> f, Pop<D, St> g, double* cf, double* cg)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= p.N) return;
+    int x, y, z;
+    cell_xyz(p, i, x, y, z);
+#pragma unroll
+    for (int a = 0; a < Lat<D>::Q; ++a) {
+        const long long c = (long long)a * p.N + i;
+        if (cf) cf[c] = (double)pulled_value<D, St>(p, f, a, x, y, z, i);
+        if (cg) cg[c] = (double)pulled_value<D, St>(p, g, a, x, y, z, i);
+    }
+}
+
+// stored FP32 state <- canonical FP64 (one thread per reading cell)
 template <int D>
-__global__ void state_io_kernel(DevParams p, float* f, float* g, double* cf, double* cg, int to_canonical)
+__global__ void set_state_f32_kernel(DevParams p, float* f, float* g, const double* cf, const double* cg)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= p.N) return;
@@ -237,45 +339,99 @@ __global__ void state_io_kernel(DevParams p, float* f, float* g, double* cf, dou
     for (int a = 0; a < Lat<D>::Q; ++a) {
         const long long slot = pull_index<D>(p, a, x, y, z, i);
         const long long c = (long long)a * p.N + i;
-        if (to_canonical) {
-            if (cf) cf[c] = (double)f[slot];
-            if (cg) cg[c] = (double)g[slot];
-        } else {
-            f[slot] = (float)cf[c];
-            g[slot] = (float)cg[c];
-        }
+        f[slot] = (float)cf[c];
+        g[slot] = (float)cg[c];
     }
 }
 
+// Shifted encoding of one writer cell from the canonical values v[a] of the
+// slots it owns (FP64 arithmetic; R from the exact total, see Pop).
+template <int D, class St>
+__device__ void encode_cell(const Pop<D, St>& set, long long j, const double* v)
+{
+    constexpr int Q = Lat<D>::Q, C = Q / 2;
+    double T = 0.0;
+    for (int a = 0; a < Q; ++a) T += v[a];
+    const double rC = v[C] / (double)wint<D>(C);
+    unsigned short* q = (unsigned short*)(set.base + set.N);
+    double sum = 0.0;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        if (a == C) continue;
+        const double W = (double)wint<D>(a);
+        const unsigned short c = St::enc((float)((v[a] / W - rC) * (double)St::S));
+        q[(a - (a > C)) * set.N + j] = c;
+        sum += W * (double)St::s * (double)St::dec(c);
+    }
+    set.base[j] = (float)((T - sum) / (double)wden<D>());
+}
+
+template <int D, class St>
+__global__ void set_state_shifted_kernel(DevParams p, Pop<D, St> f, Pop<D, St> g, const double* cf,
+                                         const double* cg)
+{
+    constexpr int Q = Lat<D>::Q;
+    const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (j >= p.N) return;
+    int x, y, z;
+    cell_xyz(p, j, x, y, z);
+    double vf[Q], vg[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        int dir;
+        const long long r = push_dst<D>(p, a, x, y, z, j, dir);
+        vf[a] = cf[(long long)dir * p.N + r];
+        vg[a] = cg[(long long)dir * p.N + r];
+    }
+    encode_cell<D, St>(f, j, vf);
+    encode_cell<D, St>(g, j, vg);
+}
+
+struct SetStateL {
+    lbmp_handle* h;
+    const double *cf, *cg;
+    template <int D, class St>
+    cudaError_t run() const
+    {
+        const int B = 128;
+        float *f = h->f[h->parity], *g = h->g[h->parity];
+        if constexpr (St::shifted)
+            set_state_shifted_kernel<D, St><<<grid_for(h->N, B), B, 0, h->stream>>>(
+                h->dp, pop_of<D, St>(h, f), pop_of<D, St>(h, g), cf, cg);
+        else
+            set_state_f32_kernel<D><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, f, g, cf, cg);
+        return cudaGetLastError();
+    }
+};
+
+struct GetStateL {
+    lbmp_handle* h;
+    double *cf, *cg;
+    template <int D, class St>
+    cudaError_t run() const
+    {
+        const int B = 128;
+        get_state_kernel<D, St><<<grid_for(h->N, B), B, 0, h->stream>>>(
+            h->dp, pop_of<D, St>(h, h->f[h->parity]), pop_of<D, St>(h, h->g[h->parity]), cf, cg);
+        return cudaGetLastError();
+    }
+};
+
 cudaError_t launch_set_state(lbmp_handle* h, const double* dev_f, const double* dev_g)
 {
-    const int B = 256;
-    if (h->D == 3)
-        state_io_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->f[h->parity], h->g[h->parity],
-                                                                   (double*)dev_f, (double*)dev_g, 0);
-    else
-        state_io_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->f[h->parity], h->g[h->parity],
-                                                                   (double*)dev_f, (double*)dev_g, 0);
-    return cudaGetLastError();
+    return dispatch(h, SetStateL{h, dev_f, dev_g});
 }
 
 cudaError_t launch_get_state(lbmp_handle* h, double* dev_f, double* dev_g)
 {
-    const int B = 256;
-    if (h->D == 3)
-        state_io_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->f[h->parity], h->g[h->parity], dev_f,
-                                                                   dev_g, 1);
-    else
-        state_io_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, h->f[h->parity], h->g[h->parity], dev_f,
-                                                                   dev_g, 1);
-    return cudaGetLastError();
+    return dispatch(h, GetStateL{h, dev_f, dev_g});
 }
 
 // ---------------------------------------------------------- observables
 // rho, u and p_h = P + cs2 u.grad(rho)/2 of one cell, as in the step.
-template <int D>
-__device__ void cell_macro(const DevParams& p, const float* __restrict__ f, const float* __restrict__ phi, int x,
-                           int y, int z, long long i, float& rho, float u[3], float& ph)
+template <int D, class St>
+__device__ void cell_macro(const DevParams& p, const Pop<D, St>& f, const float* __restrict__ phi, int x, int y,
+                           int z, long long i, float& rho, float u[3], float& ph)
 {
     constexpr int Q = Lat<D>::Q;
     float nh[Q], nl[Q];
@@ -289,7 +445,7 @@ __device__ void cell_macro(const DevParams& p, const float* __restrict__ f, cons
     stencil_from_nb<D>(nh, nl, grad, lap);
     float fr[Q];
 #pragma unroll
-    for (int a = 0; a < Q; ++a) fr[a] = f[pull_index<D>(p, a, x, y, z, i)];
+    for (int a = 0; a < Q; ++a) fr[a] = pulled_value<D, St>(p, f, a, x, y, z, i);
     FlowMoments m;
     flow_moments<D>(m, fr);
     CellState s;
@@ -301,9 +457,9 @@ __device__ void cell_macro(const DevParams& p, const float* __restrict__ f, cons
 }
 
 // per-block partial sums: mass, kinetic energy, max|u|, non-finite count
-template <int D>
-__global__ void __launch_bounds__(256) obs_partial_kernel(DevParams p, const float* __restrict__ f,
-                                                          const float* __restrict__ phi, double* __restrict__ part)
+template <int D, class St>
+__global__ void __launch_bounds__(256) obs_partial_kernel(DevParams p, Pop<D, St> f, const float* __restrict__ phi,
+                                                          double* __restrict__ part)
 {
     __shared__ double sm[4][256];
     double mass = 0.0, ke = 0.0, um = 0.0, bad = 0.0;
@@ -312,7 +468,7 @@ __global__ void __launch_bounds__(256) obs_partial_kernel(DevParams p, const flo
         int x, y, z;
         cell_xyz(p, i, x, y, z);
         float rho, u[3], ph;
-        cell_macro<D>(p, f, phi, x, y, z, i, rho, u, ph);
+        cell_macro<D, St>(p, f, phi, x, y, z, i, rho, u, ph);
         const double uu = (double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2];
         const double ph_i = (double)phi[i] + (double)phi[p.N + i];
         mass += ph_i;
@@ -372,9 +528,9 @@ __global__ void __launch_bounds__(256) obs_final_kernel(const double* __restrict
 }
 
 // mean p_h over the 3^D block at a probe cell (one block of threads per probe)
-template <int D>
-__global__ void probe_kernel(DevParams p, const float* __restrict__ f, const float* __restrict__ phi, int px, int py,
-                             int pz, int qx, int qy, int qz, double* __restrict__ out)
+template <int D, class St>
+__global__ void probe_kernel(DevParams p, Pop<D, St> f, const float* __restrict__ phi, int px, int py, int pz, int qx,
+                             int qy, int qz, double* __restrict__ out)
 {
     __shared__ double sm[32];
     const int t = threadIdx.x;
@@ -394,7 +550,7 @@ __global__ void probe_kernel(DevParams p, const float* __restrict__ f, const flo
         }
         const long long i = ((long long)z * p.ny + y) * p.nx + x;
         float rho, u[3], ph;
-        cell_macro<D>(p, f, phi, x, y, z, i, rho, u, ph);
+        cell_macro<D, St>(p, f, phi, x, y, z, i, rho, u, ph);
         v = ph;
     }
     sm[t] = v;
@@ -425,38 +581,39 @@ __global__ void column_kernel(DevParams p, const float* __restrict__ phi, double
     out[nv + k] = (double)phi[ib] + (double)phi[p.N + ib];
 }
 
+struct ObsL {
+    lbmp_handle* h;
+    double* out;
+    bool full;  // false: mass and the other reductions only
+    template <int D, class St>
+    cudaError_t run() const
+    {
+        const Pop<D, St> f = pop_of<D, St>(h, h->f[h->parity]);
+        obs_partial_kernel<D, St><<<h->red_blocks, 256, 0, h->stream>>>(h->dp, f, h->phi, h->red);
+        obs_final_kernel<<<1, 256, 0, h->stream>>>(h->red, h->red_blocks, out);
+        if (full) {
+            const int nv = (D == 3) ? h->grid.nz : h->grid.ny;
+            const int* pr = h->probe;
+            probe_kernel<D, St><<<2, 32, 0, h->stream>>>(h->dp, f, h->phi, pr[0], pr[1], D == 3 ? pr[2] : 0, 0, 0,
+                                                         0, out + 4);
+            column_kernel<D><<<grid_for(nv, 128), 128, 0, h->stream>>>(h->dp, h->phi, out + 16);
+        }
+        return cudaGetLastError();
+    }
+};
+
 cudaError_t launch_observables(lbmp_handle* h, double* dev_out)
 {
     cudaError_t e = launch_phi_pass(h);
     if (e != cudaSuccess) return e;
-    const float* f = h->f[h->parity];
-    const int nv = (h->D == 3) ? h->grid.nz : h->grid.ny;
-    const int* pr = h->probe;
-    if (h->D == 3) {
-        obs_partial_kernel<3><<<h->red_blocks, 256, 0, h->stream>>>(h->dp, f, h->phi, h->red);
-        obs_final_kernel<<<1, 256, 0, h->stream>>>(h->red, h->red_blocks, dev_out);
-        probe_kernel<3><<<2, 32, 0, h->stream>>>(h->dp, f, h->phi, pr[0], pr[1], pr[2], 0, 0, 0, dev_out + 4);
-        column_kernel<3><<<grid_for(nv, 128), 128, 0, h->stream>>>(h->dp, h->phi, dev_out + 16);
-    } else {
-        obs_partial_kernel<2><<<h->red_blocks, 256, 0, h->stream>>>(h->dp, f, h->phi, h->red);
-        obs_final_kernel<<<1, 256, 0, h->stream>>>(h->red, h->red_blocks, dev_out);
-        probe_kernel<2><<<2, 32, 0, h->stream>>>(h->dp, f, h->phi, pr[0], pr[1], 0, 0, 0, 0, dev_out + 4);
-        column_kernel<2><<<grid_for(nv, 128), 128, 0, h->stream>>>(h->dp, h->phi, dev_out + 16);
-    }
-    return cudaGetLastError();
+    return dispatch(h, ObsL{h, dev_out, true});
 }
 
 cudaError_t launch_mass(lbmp_handle* h, double* dev_out4)
 {
     cudaError_t e = launch_phi_pass(h);
     if (e != cudaSuccess) return e;
-    const float* f = h->f[h->parity];
-    if (h->D == 3)
-        obs_partial_kernel<3><<<h->red_blocks, 256, 0, h->stream>>>(h->dp, f, h->phi, h->red);
-    else
-        obs_partial_kernel<2><<<h->red_blocks, 256, 0, h->stream>>>(h->dp, f, h->phi, h->red);
-    obs_final_kernel<<<1, 256, 0, h->stream>>>(h->red, h->red_blocks, dev_out4);
-    return cudaGetLastError();
+    return dispatch(h, ObsL{h, dev_out4, false});
 }
 
 }  // namespace lbmp

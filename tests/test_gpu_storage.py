@@ -1,0 +1,182 @@
+"""Shifted 16-bit population storage (FP16 / BF16 codes, FP32 reference per
+cell) against the FP64 oracle and against the FP32 path.
+
+Tolerances.  A stored code carries a deviation q of v_a/W_a from the cell's
+rest ratio with the relative precision of its format (half-ulp 2^-12 for
+FP16, 2^-9 for BF16), so every stored population is perturbed by about
+2^-12 (FP16) or 2^-9 (BF16) of its deviation from the rest-shaped part; the
+reference, totals and arithmetic stay FP32.  Measured errors after 100 steps
+(norm-wise, as in the FP32 parity tests) are at most 7.3e-4 on f' and 8.8e-5
+on g and phi for FP16 -- f' is the pressure-scale family whose deviations
+are largest relative to its maximum -- and 8x that for BF16 (three fewer
+mantissa bits).  The bounds below keep a factor ~2.5 of margin and the same
+ratio 8 between the formats.  Observable-level bars follow the storage
+requirement: Laplace pressure jump within 1 % of the oracle, relative mass
+drift within 1e-6 over the run, and Rayleigh-Taylor tip positions within a
+fraction of a cell of the FP32 run.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2101_06769_gb300 import Domain, LbmpError
+from paper_2101_06769_gb300.lbmp import BF16_SHIFTED, FP16_SHIFTED, FP32
+
+from test_gpu_parity import CASES, rel_err
+
+pytestmark = pytest.mark.gpu
+
+STORAGES = {"fp16": FP16_SHIFTED, "bf16": BF16_SHIFTED}
+TOL_F = {"fp16": 2e-3, "bf16": 1.6e-2}     # f'
+TOL_G = {"fp16": 2e-4, "bf16": 1.6e-3}     # g and phi
+
+EVEN = dict(CASES)
+for k in [k for k, c in EVEN.items() if c["dims"][0] % 2]:
+    del EVEN[k]
+# ragged, even nx: a partial tile in x and y, walls and periodic z
+EVEN["ragged3d_walls"] = dict(D=3, dims=(38, 29, 23), periodic=(1, 1, 0),
+                              phys=dict(rho_ratio=10.0, nu_ratio=5.0, nu_h=0.02, sigma=5e-3, g_accel=1e-5,
+                                        mobility=0.03, width=4.0),
+                              case="rt", args=[11.0, 3.0, 1e-2, 1.0], seed=6)
+EVEN["ragged3d_even"] = dict(D=3, dims=(38, 29, 23), periodic=(1, 1, 1),
+                             phys=dict(rho_ratio=20.0, nu_ratio=2.0, nu_h=0.05, sigma=1e-2, mobility=0.02,
+                                       width=4.0),
+                             case="drop_static", args=[7.0, 1.0, 1e-2], seed=5)
+
+
+def domain(c, storage):
+    return Domain(c["D"], c["dims"], c["periodic"], storage=storage, **c["phys"])
+
+
+def test_odd_nx_rejected():
+    c = CASES["ragged3d"]
+    assert c["dims"][0] % 2 == 1
+    with pytest.raises(LbmpError):
+        domain(c, FP16_SHIFTED)
+
+
+def test_state_bytes_halved():
+    c = EVEN["rt3d"]
+    a, b = domain(c, FP32), domain(c, FP16_SHIFTED)
+    N = np.prod(c["dims"])
+    assert a.state_bytes() == 2 * 4 * 27 * N
+    assert b.state_bytes() == 2 * (4 * N + 2 * 26 * N)
+
+
+@pytest.mark.parametrize("st", sorted(STORAGES))
+@pytest.mark.parametrize("name", ["rt3d", "splash3d", "rt2d", "ragged3d_walls"])
+def test_encode_round_trip(name, st):
+    """set_state encodes the canonical FP64 state; get_state decodes it.  The
+    global totals (sum of every population) are kept to FP32 rounding, each
+    value to the code precision."""
+    c = EVEN[name]
+    o = O.Oracle(c["D"], c["dims"], c["periodic"], **c["phys"])
+    o.init(c["case"], c["args"], seed=c["seed"])
+    f0, g0, _ = o.get_state()
+    d = domain(c, STORAGES[st])
+    d.set_state(f0, g0)
+    f1, g1, p1 = d.get_state()
+    assert abs(g1.sum() - g0.sum()) <= 1e-7 * g0.sum()
+    assert rel_err(g1, g0) <= TOL_G[st]
+    assert rel_err(f1, f0) <= TOL_F[st]
+    assert np.allclose(p1, g1.sum(0), rtol=0, atol=1e-6)
+
+
+@pytest.mark.parametrize("st", sorted(STORAGES))
+@pytest.mark.parametrize("name", sorted(EVEN))
+def test_step_parity_100_shifted(name, st):
+    c = EVEN[name]
+    o = O.Oracle(c["D"], c["dims"], c["periodic"], **c["phys"])
+    o.init(c["case"], c["args"], seed=c["seed"])
+    f0, g0, _ = o.get_state()
+    d = domain(c, STORAGES[st])
+    d.set_state(f0, g0)
+    o.step(100)
+    d.step(100)
+    fo, go, po = o.get_state()
+    fg, gg, pg = d.get_state()
+    ef, eg, ep = rel_err(fg, fo), rel_err(gg, go), rel_err(pg, po)
+    assert ef <= TOL_F[st] and eg <= TOL_G[st] and ep <= TOL_G[st], (name, st, ef, eg, ep)
+
+
+@pytest.mark.parametrize("st", sorted(STORAGES))
+@pytest.mark.parametrize("name", ["splash3d", "ragged3d_walls", "thin3d", "ragged3d_even"])
+def test_fused_and_reference_agree_bitwise_shifted(name, st):
+    """The fused 16-bit kernel and the reference pair decode, collide and
+    encode with the same FP32 operations in the same order."""
+    c = EVEN[name]
+    a, b = domain(c, STORAGES[st]), domain(c, STORAGES[st])
+    for dm, k in ((a, 0), (b, 1)):
+        dm.init(c["case"], c["args"], seed=c["seed"])
+        dm.set_kernel(k)
+        dm.step(23)
+    sa, sb = a.get_state(), b.get_state()
+    assert all(np.array_equal(x, y) for x, y in zip(sa, sb))
+    raw = []
+    for dm in (a, b):
+        buf = np.empty(dm.state_bytes(), np.uint8)
+        dm.download(buf.ctypes.data, buf.size)
+        dm.sync()
+        raw.append(buf)
+    assert np.array_equal(raw[0], raw[1])
+
+
+@pytest.mark.parametrize("st", sorted(STORAGES))
+def test_mass_drift_steady_drop(st):
+    """A converged static drop repeats the same roundings every step, so any
+    per-step mass error would grow linearly: the drift must stay <= 1e-6."""
+    phys = dict(rho_ratio=10.0, nu_ratio=1.0, nu_h=0.1, sigma=2e-3, mobility=0.02, width=4.0)
+    d = Domain(3, (48, 48, 48), (1, 1, 1), storage=STORAGES[st], **phys)
+    d.init("drop_static", [12.0, 1.0, 0.0], seed=1)
+    d.step(4000)
+    ob = d.observables()
+    assert abs(ob.mass_drift_rel) <= 1e-6, ob.mass_drift_rel
+
+
+@pytest.mark.parametrize("st", sorted(STORAGES))
+def test_laplace_jump_vs_oracle(st):
+    """Static 3-D drop: the pressure jump of the 16-bit run is within 1 % of
+    the FP64 oracle's after the same steps."""
+    phys = dict(rho_ratio=10.0, nu_ratio=1.0, nu_h=0.1, sigma=2e-3, mobility=0.02, width=4.0)
+    dims, args, steps = (32, 32, 32), [8.0, 1.0, 0.0], 1500
+    o = O.Oracle(3, dims, (1, 1, 1), **phys)
+    o.init("drop_static", args, seed=1)
+    o.step(steps)
+    ref = o.observables().laplace_dp
+    d = Domain(3, dims, (1, 1, 1), storage=STORAGES[st], **phys)
+    d.init("drop_static", args, seed=1)
+    d.step(steps)
+    got = d.observables().laplace_dp
+    assert ref > 0 and abs(got - ref) <= 1e-2 * ref, (got, ref)
+
+
+def test_rt_tips_follow_fp32():
+    """Reduced 3-D Rayleigh-Taylor over five time units T = L/U*: spike and
+    bubble tips of the 16-bit runs stay within a fraction of a cell of the
+    FP32 run (measured: 0.003 cells FP16, 0.13 cells BF16), mass drift <= 1e-6."""
+    c = EVEN["rt3d"]
+    T = int(round(c["phys"]["L_ref"] / 0.04))
+    tips = {}
+    for st in (FP32, FP16_SHIFTED, BF16_SHIFTED):
+        d = domain(c, st)
+        d.init(c["case"], c["args"], seed=c["seed"])
+        rec = []
+        for _ in range(5):
+            d.step(T)
+            ob = d.observables()
+            assert abs(ob.mass_drift_rel) <= 1e-6
+            rec.append((ob.tip_spike, ob.tip_bubble))
+        tips[st] = np.array(rec)
+    assert np.abs(tips[FP16_SHIFTED] - tips[FP32]).max() <= 0.05
+    assert np.abs(tips[BF16_SHIFTED] - tips[FP32]).max() <= 0.5
+
+
+def test_batch_rejects_shifted_members():
+    from paper_2101_06769_gb300 import Batch
+    c = EVEN["rt3d"]
+    b = Batch()
+    d = domain(c, FP16_SHIFTED)
+    d.init(c["case"], c["args"], seed=1)
+    with pytest.raises(LbmpError):
+        b.add(d, 10)
+    b.close()
