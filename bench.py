@@ -46,7 +46,40 @@ WORKLOADS = {
         case="rt", args=[128.0, 6.4, 1e-4, 1.0], seed=1),
 }
 
-BYTES_PER_CELL = {3: 2 * (27 + 27) * 4, 2: 2 * (9 + 9) * 4}  # populations read once + written once, FP32
+# algorithmic bytes per cell update: every population read once and written
+# once (phi is formed on chip and never stored by the fused kernels)
+BYTES_PER_CELL = {3: 2 * (27 + 27) * 4, 2: 2 * (9 + 9) * 4}  # FP32
+# shifted 16-bit storage: per population set one FP32 reference + (Q-1) codes
+BYTES_PER_CELL_16 = {3: 2 * 2 * (4 + 26 * 2), 2: 2 * 2 * (4 + 8 * 2)}
+STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
+# of the step kernel, per cell, from the ncu capture summarised in profiles/;
+# keyed by the SHA-256 of the kernel sources it was taken on, so that it is
+# reported as null once those sources change.
+TRAFFIC = {
+    # 128x128x512 rt3d, one launch of step_fused3_kernel: 1.89 GB read + 1.77 GB written
+    ("rt3d", "fp32"): {"bytes_per_cell": 3.66e9 / 8388608, "sources": "846e1678ee0eb821"},
+    # same workload, step_fused3s_kernel<StoreF16>: 973.99 MB read + 901.00 MB written
+    ("rt3d", "fp16"): {"bytes_per_cell": 1874.99e6 / 8388608, "sources": "846e1678ee0eb821"},
+}
+TRAFFIC_SOURCES = ["lbmp_common.cuh", "lbmp_tile.cuh", "lbmp_fused.cu", "lbmp_fused16.cu"]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2101_06769_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(workload, storage, cells):
+    rec = TRAFFIC.get((workload, storage))
+    if not rec or rec["sources"] != kernel_source_hash():
+        return None
+    return rec["bytes_per_cell"] * cells
 
 
 def load_peaks():
@@ -205,6 +238,81 @@ def run_reference(args, wl):
     return 0
 
 
+def time_steps(step, stream, n):
+    """mean ms of one call of step() over n calls, CUDA events on the stream"""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(n):
+        step()
+    b.record(stream)
+    stream.synchronize()
+    return a.elapsed_time(b) / n
+
+
+# the batched form: one batch of uneven Rayleigh-Taylor members (3-D cubes
+# and slabs, 2-D squares), the same non-dimensional set-up scaled per member
+BATCH_MIX = [(3, (64, 64, 64))] * 2 + [(3, (96, 96, 96))] * 2 + [(3, (128, 128, 128))] * 2 + \
+            [(3, (128, 128, 256))] * 2 + [(2, (512, 512, 1))] * 4
+
+
+def measure_forms(args, wl, stream, peak, pg):
+    """The other forms of the step on the same device: the workload with
+    FP16 and BF16 shifted storage (fused kernel), and a batch of uneven
+    domains advanced by the persistent batch kernels and CUDA graphs."""
+    from paper_2101_06769_gb300 import Batch, Domain
+    D = wl["D"]
+    out, launches = {}, 0
+    n = max(3, args.form_steps)
+    for name in ("fp16", "bf16"):
+        if name == args.storage or (D == 2 and args.kernel == 0):
+            continue
+        d = Domain(D, wl["dims"], wl["periodic"], stream=stream.cuda_stream, storage=STORAGE[name], **wl["phys"])
+        d.init(wl["case"], wl["args"], seed=wl["seed"])
+        d.step(5)
+        ms = time_steps(lambda: d.step(1), stream, n)
+        launches += n
+        _, mlups = aggregate(ms * n, d.N, n, pg)
+        bpc = BYTES_PER_CELL_16[D]
+        gbs = bpc * d.N / (ms * 1e-3) / 1e9
+        ob = d.observables()
+        out[name] = {"mlups": mlups, "ms_per_step": ms, "bytes_per_cell": bpc, "achieved_gbs": gbs,
+                     "frac": gbs / peak, "mass_drift_rel": ob.mass_drift_rel, "steps": n,
+                     "traffic": traffic_per_launch(args.workload, name, d.N)}
+        d.close()
+    # batched form
+    doms, cells, byts = [], 0, 0
+    b = Batch(stream=stream.cuda_stream)
+    for k, (Dm, dims) in enumerate(BATCH_MIX):
+        L = float(dims[0])
+        per = (1, 1, 0) if Dm == 3 else (1, 0, 1)
+        d = Domain(Dm, dims, per, stream=stream.cuda_stream, atwood=0.5, nu_ratio=1.0, Re=1024.0,
+                   g_accel=0.04 ** 2 / L, L_ref=L, mobility=0.02, width=5.0)
+        d.init("rt", [dims[Dm - 1] / 2.0, 0.1 * L, 1e-4, 1.0], seed=100 + k)
+        b.add(d, 10 ** 6)
+        doms.append(d)
+        cells += d.N
+        byts += BYTES_PER_CELL[Dm] * d.N
+    b.step(16)  # rebuild, capture and warm the graphs
+    nb = 4 * max(1, n // 16)  # graph replays of 16 steps
+    ms16 = time_steps(lambda: b.step(16), stream, nb)
+    ms = ms16 / 16
+    launches += nb * 16 * 3  # per step: 3-D batch kernel, 2-D batch kernel, epilogue
+    _, mlups = aggregate(ms * nb * 16, cells, nb * 16, pg)
+    gbs = byts / (ms * 1e-3) / 1e9
+    out["batched"] = {"mlups": mlups, "ms_per_step": ms, "members": len(doms), "cells": cells,
+                      "bytes_per_step": byts, "achieved_gbs": gbs, "frac": gbs / peak,
+                      "mix": "2x64^3, 2x96^3, 2x128^3, 2x128x128x256 D3Q27 + 4x512^2 D2Q9 Rayleigh-Taylor, FP32",
+                      "steps": nb * 16}
+    for d in doms:
+        b.remove(d)
+        d.close()
+    b.close()
+    out["_launches"] = launches
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,6 +324,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--grid", default=None, help="override nx,ny,nz (profiling on a smaller case)")
+    ap.add_argument("--storage", default="fp32", choices=sorted(STORAGE))
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16/batched form measurements")
+    ap.add_argument("--form-steps", type=int, default=50)
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.grid:
@@ -241,7 +352,8 @@ def main():
 
     stream = torch.cuda.Stream()
     D = wl["D"]
-    dom = Domain(D, wl["dims"], wl["periodic"], stream=stream.cuda_stream, **wl["phys"])
+    dom = Domain(D, wl["dims"], wl["periodic"], stream=stream.cuda_stream, storage=STORAGE[args.storage],
+                 **wl["phys"])
     dom.set_kernel(args.kernel)
     dom.init(wl["case"], wl["args"], seed=wl["seed"] + rank)
     cells = dom.N
@@ -278,12 +390,14 @@ def main():
     # roofline of the step kernel: algorithmic bytes per launch / event time
     peak, peak_kind = load_peaks()
     kern_ms = statistics.mean(step_ms)
-    bytes_launch = BYTES_PER_CELL[D] * cells
+    bpc = BYTES_PER_CELL[D] if args.storage == "fp32" else BYTES_PER_CELL_16[D]
+    bytes_launch = bpc * cells
     achieved = bytes_launch / (kern_ms * 1e-3) / 1e9
+    traffic = traffic_per_launch(args.workload, args.storage, cells) if (args.kernel == 0 and not args.grid) else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_kind": peak_kind, "traffic": None,
+            "peak_kind": peak_kind, "traffic": traffic,
             "kernel": "step_fused" if args.kernel == 0 else "step_simple + phi_pass",
-            "bytes_per_cell": BYTES_PER_CELL[D]}
+            "bytes_per_cell": bpc}
 
     # end to end through the public API with host buffers: per step upload the
     # state from pinned host memory, advance one step, read the observables back
@@ -308,17 +422,20 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl["desc"], "grid": list(wl["dims"]), "cells": cells,
-                       "storage": "fp32", "l2": "inputs larger than L2 (no flush)",
+                       "storage": args.storage, "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas{ws}"},
             "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "health": ob.health, "mass_drift_rel": ob.mass_drift_rel}
+    dom.close()
+    if not args.no_forms and not args.grid:
+        line["forms"] = measure_forms(args, wl, stream, peak, pg)
+        line["gpu_launches_forms"] = line["forms"].pop("_launches")
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     if pg is not None:
         pg.barrier()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    dom.close()
     if pg is not None:
         pg.destroy_process_group()
     return 0
