@@ -270,6 +270,8 @@ def measure_forms(args, wl, stream, peak, pg):
             continue
         d = Domain(D, wl["dims"], wl["periodic"], stream=stream.cuda_stream, storage=STORAGE[name], **wl["phys"])
         d.init(wl["case"], wl["args"], seed=wl["seed"])
+        if not args.no_autotune:
+            d.autotune(reps=3, cache=False)
         d.step(5)
         ms = time_steps(lambda: d.step(1), stream, n)
         launches += n
@@ -327,6 +329,7 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=sorted(STORAGE))
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16/batched form measurements")
     ap.add_argument("--form-steps", type=int, default=50)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.grid:
@@ -357,6 +360,11 @@ def main():
     dom.set_kernel(args.kernel)
     dom.init(wl["case"], wl["args"], seed=wl["seed"] + rank)
     cells = dom.N
+    launch = {"chunk": 0, "ctas_per_sm": 0, "tuned": False}
+    if not args.no_autotune and args.kernel == 0:
+        # launch-shape autotuner of the library (trials do not advance the state)
+        chunk, ctas, trials = dom.autotune(reps=3, cache=False)
+        launch = {"chunk": chunk, "ctas_per_sm": ctas, "tuned": True, "trials": len(trials)}
     dom.step(args.warmup)
     dom.sync()
 
@@ -423,7 +431,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl["desc"], "grid": list(wl["dims"]), "cells": cells,
                        "storage": args.storage, "l2": "inputs larger than L2 (no flush)",
-                       "parallelism": f"replicas{ws}"},
+                       "parallelism": f"replicas{ws}", "launch": launch},
             "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "health": ob.health, "mass_drift_rel": ob.mass_drift_rel}
     dom.close()

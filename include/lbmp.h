@@ -171,10 +171,40 @@ LBMP_API size_t lbmp_state_bytes(const lbmp_handle *h);
 LBMP_API int lbmp_upload(lbmp_handle *h, const void *host, size_t bytes);
 LBMP_API int lbmp_download(lbmp_handle *h, void *host, size_t bytes);
 
-/* Kernel selection (for A/B tests and measurement): 0 = default fused
- * kernel, 1 = simple reference pair (phi pass + one thread per cell). */
-enum { LBMP_OPT_KERNEL = 0 };
+/* Options of a handle.
+ *   LBMP_OPT_KERNEL: 0 = default fused kernel, 1 = simple reference pair
+ *     (phi pass + one thread per cell), for A/B tests and measurement.
+ *   LBMP_OPT_CHUNK: planes (rows in 2-D) per work item of the fused
+ *     kernels, 0 = automatic (the default), else >= 1.
+ *   LBMP_OPT_CTAS_PER_SM: resident CTAs per SM of the fused kernels'
+ *     persistent grid, 0 = the occupancy maximum (the default), else >= 1
+ *     (values above the maximum act as the maximum).
+ * Launch-shape options change speed only, never results.  Returns
+ * LBMP_ERR_INVALID_ARG for an unknown option or an out-of-range value. */
+enum { LBMP_OPT_KERNEL = 0, LBMP_OPT_CHUNK = 1, LBMP_OPT_CTAS_PER_SM = 2 };
 LBMP_API int lbmp_set_option(lbmp_handle *h, int option, long value);
+
+/* Launch-shape autotuner of the fused step kernel (no counterpart in the
+ * paper; serving-side tuning).  Times each candidate (planes per work item
+ * in {automatic, 4, 8, 16, 32, 64, 128} up to the marching extent, CTAs per
+ * SM in {maximum, 1, 2}) over `reps` launches (>= 1) after one warm-up
+ * launch, with CUDA events on the handle's stream, and keeps the fastest as
+ * the handle's options.  Trial launches read the current population set and
+ * write the other one, which the next step overwrites: the state is not
+ * advanced and results are unchanged.  `table` (caller-owned, may be NULL)
+ * receives up to max_entries trials; *n_entries (may be NULL) the number of
+ * trials run.  With LBMP_OPT_KERNEL = 1 nothing is tuned (n_entries = 0).
+ * Synchronises the handle's stream. */
+typedef struct {
+    int chunk;        /* LBMP_OPT_CHUNK value of the trial (0 = automatic) */
+    int ctas_per_sm;  /* LBMP_OPT_CTAS_PER_SM value of the trial (0 = maximum) */
+    double ms;        /* mean time of one step launch */
+} lbmp_tune_entry;
+LBMP_API int lbmp_autotune(lbmp_handle *h, int reps, lbmp_tune_entry *table, int max_entries, int *n_entries);
+
+/* Name of the current CUDA device (for keying tuning caches); writes a
+ * NUL-terminated string of at most len bytes. */
+LBMP_API int lbmp_device_name(char *out, int len);
 
 /* ---- batches: many domains advanced together ------------------------------
  * A batch advances every member domain with one persistent kernel launch per

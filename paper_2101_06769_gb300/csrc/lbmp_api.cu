@@ -227,9 +227,22 @@ int lbmp_set_option(lbmp_handle* h, int option, long value)
 {
     int rc = check_handle(h);
     if (rc) return rc;
-    if (option != LBMP_OPT_KERNEL || value < 0 || value > 1) return fail(LBMP_ERR_INVALID_ARG, "bad option");
-    h->kernel = (int)value;
-    return LBMP_OK;
+    switch (option) {
+    case LBMP_OPT_KERNEL:
+        if (value < 0 || value > 1) return fail(LBMP_ERR_INVALID_ARG, "kernel must be 0 or 1");
+        h->kernel = (int)value;
+        return LBMP_OK;
+    case LBMP_OPT_CHUNK:
+        if (value < 0 || value > (1L << 30)) return fail(LBMP_ERR_INVALID_ARG, "chunk must be >= 0");
+        h->opt_chunk = (int)value;
+        return LBMP_OK;
+    case LBMP_OPT_CTAS_PER_SM:
+        if (value < 0 || value > 64) return fail(LBMP_ERR_INVALID_ARG, "CTAs per SM must lie in [0, 64]");
+        h->opt_ctas = (int)value;
+        return LBMP_OK;
+    default:
+        return fail(LBMP_ERR_INVALID_ARG, "unknown option");
+    }
 }
 
 int lbmp_init(lbmp_handle* h, int case_id, const double* case_args, int nargs, unsigned long long seed)

@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_batch3_kernel(const 
 
 struct LaunchCfg {
     int device = -1;
-    int grid_cap = 0;
+    int per_sm = 0, sms = 0;
 };
 LaunchCfg g_cfg;
 
@@ -369,7 +369,8 @@ cudaError_t launch_step_fused(lbmp_handle* h)
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
         if (e != cudaSuccess) return e;
-        g_cfg.grid_cap = (per_sm > 0 ? per_sm : 1) * sms;
+        g_cfg.per_sm = per_sm > 0 ? per_sm : 1;
+        g_cfg.sms = sms;
         g_cfg.device = h->device;
     }
     DirPtrs D;
@@ -384,14 +385,10 @@ cudaError_t launch_step_fused(lbmp_handle* h)
     FusedArgs A;
     A.tiles_x = (h->grid.nx + TX - 1) / TX;
     A.tiles_y = (h->grid.ny + TY - 1) / TY;
-    const int tiles = A.tiles_x * A.tiles_y;
-    // chunk length: enough items to balance the persistent grid, at least 8 planes
-    int chunk = h->grid.nz;
-    while (chunk > 8 && (long long)tiles * ((h->grid.nz + chunk - 1) / chunk) < 4LL * g_cfg.grid_cap) chunk /= 2;
-    A.chunk = chunk;
-    A.nitems = tiles * ((h->grid.nz + chunk - 1) / chunk);
-    const int grid = A.nitems < g_cfg.grid_cap ? A.nitems : g_cfg.grid_cap;
-    step_fused3_kernel<<<grid, NT, kSmemBytes, h->stream>>>(h->dp, A, D);
+    const LaunchShape L = launch_shape(h, A.tiles_x * A.tiles_y, h->grid.nz, g_cfg.per_sm, g_cfg.sms);
+    A.chunk = L.chunk;
+    A.nitems = L.nitems;
+    step_fused3_kernel<<<L.grid, NT, kSmemBytes, h->stream>>>(h->dp, A, D);
     return cudaGetLastError();
 }
 

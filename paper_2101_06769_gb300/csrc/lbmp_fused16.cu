@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_fused3s_kernel(DevPa
 
 struct Cfg16 {
     int device = -1;
-    int grid_cap = 0;
+    int per_sm = 0, sms = 0;
 };
 
 template <class St>
@@ -363,7 +363,8 @@ cudaError_t launch16(lbmp_handle* h, Cfg16& cfg)
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
         if (e != cudaSuccess) return e;
-        cfg.grid_cap = (per_sm > 0 ? per_sm : 1) * sms;
+        cfg.per_sm = per_sm > 0 ? per_sm : 1;
+        cfg.sms = sms;
         cfg.device = h->device;
     }
     DirPtrs16 D;
@@ -388,13 +389,10 @@ cudaError_t launch16(lbmp_handle* h, Cfg16& cfg)
     FusedArgs16 A;
     A.tiles_x = (h->grid.nx + TX - 1) / TX;
     A.tiles_y = (h->grid.ny + TY - 1) / TY;
-    const int tiles = A.tiles_x * A.tiles_y;
-    int chunk = h->grid.nz;
-    while (chunk > 8 && (long long)tiles * ((h->grid.nz + chunk - 1) / chunk) < 4LL * cfg.grid_cap) chunk /= 2;
-    A.chunk = chunk;
-    A.nitems = tiles * ((h->grid.nz + chunk - 1) / chunk);
-    const int grid = A.nitems < cfg.grid_cap ? A.nitems : cfg.grid_cap;
-    step_fused3s_kernel<St><<<grid, NT, kSmem16, h->stream>>>(h->dp, A, D);
+    const LaunchShape L = launch_shape(h, A.tiles_x * A.tiles_y, h->grid.nz, cfg.per_sm, cfg.sms);
+    A.chunk = L.chunk;
+    A.nitems = L.nitems;
+    step_fused3s_kernel<St><<<L.grid, NT, kSmem16, h->stream>>>(h->dp, A, D);
     return cudaGetLastError();
 }
 

@@ -223,9 +223,9 @@ __global__ void __launch_bounds__(TX2) step_batch2_kernel(const BatchDomain* __r
     }
 }
 
-int g_f2_dev = -1, g_f2_cap = 0, g_b2_dev = -1, g_b2_cap = 0;
+int g_f2_dev = -1, g_f2_per_sm = 0, g_f2_sms = 0, g_b2_dev = -1, g_b2_cap = 0;
 
-cudaError_t setup_kernel(const void* fn, int device, int& dev_cached, int& cap)
+cudaError_t setup_kernel(const void* fn, int device, int& dev_cached, int& per_sm_out, int& sms_out)
 {
     if (dev_cached == device) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem2);
@@ -235,7 +235,8 @@ cudaError_t setup_kernel(const void* fn, int device, int& dev_cached, int& cap)
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
-    cap = (per_sm > 0 ? per_sm : 1) * sms;
+    per_sm_out = per_sm > 0 ? per_sm : 1;
+    sms_out = sms;
     dev_cached = device;
     return cudaSuccess;
 }
@@ -246,7 +247,7 @@ int batch2_tile_x() { return TX2; }
 
 cudaError_t launch_step_fused2(lbmp_handle* h)
 {
-    cudaError_t e = setup_kernel((const void*)step_fused2_kernel, h->device, g_f2_dev, g_f2_cap);
+    cudaError_t e = setup_kernel((const void*)step_fused2_kernel, h->device, g_f2_dev, g_f2_per_sm, g_f2_sms);
     if (e != cudaSuccess) return e;
     DirPtrs2 D;
     const int s = h->parity, d = 1 - h->parity;
@@ -259,18 +260,22 @@ cudaError_t launch_step_fused2(lbmp_handle* h)
     }
     Fused2Args A;
     A.tiles_x = (h->grid.nx + TX2 - 1) / TX2;
-    int chunk = h->grid.ny;
-    while (chunk > 8 && (long long)A.tiles_x * ((h->grid.ny + chunk - 1) / chunk) < 4LL * g_f2_cap) chunk /= 2;
-    A.chunk = chunk;
-    A.nitems = A.tiles_x * ((h->grid.ny + chunk - 1) / chunk);
-    const int grid = A.nitems < g_f2_cap ? A.nitems : g_f2_cap;
-    step_fused2_kernel<<<grid, TX2, kSmem2, h->stream>>>(h->dp, A, D);
+    const LaunchShape L = launch_shape(h, A.tiles_x, h->grid.ny, g_f2_per_sm, g_f2_sms);
+    A.chunk = L.chunk;
+    A.nitems = L.nitems;
+    step_fused2_kernel<<<L.grid, TX2, kSmem2, h->stream>>>(h->dp, A, D);
     return cudaGetLastError();
 }
 
 cudaError_t prepare_batch2(int device)
 {
-    return setup_kernel((const void*)step_batch2_kernel, device, g_b2_dev, g_b2_cap);
+    int per_sm = 0, sms = 0, dev = g_b2_dev;
+    cudaError_t e = setup_kernel((const void*)step_batch2_kernel, device, dev, per_sm, sms);
+    if (e == cudaSuccess && g_b2_dev != device) {
+        g_b2_cap = per_sm * sms;
+        g_b2_dev = device;
+    }
+    return e;
 }
 
 cudaError_t launch_batch2(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream)

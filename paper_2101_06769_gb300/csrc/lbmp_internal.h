@@ -24,6 +24,8 @@ struct lbmp_handle {
     int parity;        // f[parity], g[parity] hold the current state
     long step;
     int kernel;        // LBMP_OPT_KERNEL
+    int opt_chunk;     // LBMP_OPT_CHUNK: planes (rows) per work item, 0 = automatic
+    int opt_ctas;      // LBMP_OPT_CTAS_PER_SM: resident CTAs per SM of the grid, 0 = occupancy maximum
     int probe[3];
     // observables scratch (partial sums per block) and result slot
     double* red;
@@ -41,6 +43,32 @@ struct BatchDomain {
     int parity, steps_left;
     int tiles_x, tiles_y, chunk, item_begin, items;
 };
+
+// Launch shape of a persistent fused kernel over `tiles` tiles marching
+// through `nmarch` planes (rows in 2-D): planes per work item and grid size,
+// from the handle's options or the defaults (enough items for four rounds of
+// the full-occupancy grid, at least 8 planes per item).
+struct LaunchShape {
+    int chunk, nitems, grid;
+};
+inline LaunchShape launch_shape(const lbmp_handle* h, int tiles, int nmarch, int per_sm, int sms)
+{
+    if (per_sm < 1) per_sm = 1;
+    const int ctas = (h->opt_ctas > 0 && h->opt_ctas < per_sm) ? h->opt_ctas : per_sm;
+    const long long cap = (long long)ctas * sms;
+    int chunk;
+    if (h->opt_chunk > 0) {
+        chunk = h->opt_chunk < nmarch ? h->opt_chunk : nmarch;
+    } else {
+        chunk = nmarch;
+        while (chunk > 8 && (long long)tiles * ((nmarch + chunk - 1) / chunk) < 4LL * per_sm * sms) chunk /= 2;
+    }
+    LaunchShape L;
+    L.chunk = chunk;
+    L.nitems = tiles * ((nmarch + chunk - 1) / chunk);
+    L.grid = (int)(L.nitems < cap ? L.nitems : cap);
+    return L;
+}
 
 // bytes of one population set (f' or g) in the handle's storage form
 inline size_t set_bytes(const lbmp_handle* h)

@@ -1,0 +1,88 @@
+// lbmp_tune.cu -- launch-shape autotuner of the fused step kernels
+// (include/lbmp.h, lbmp_autotune) and the device name query.
+//
+// A trial launch is the step kernel without the parity flip of lbmp_step: it
+// reads the current population set and writes the other one, so the state
+// the handle exposes is untouched and the next real step overwrites the
+// trial's output.
+#include <stdio.h>
+#include <string.h>
+
+#include "lbmp_internal.h"
+
+extern "C" {
+
+LBMP_API int lbmp_autotune(lbmp_handle* h, int reps, lbmp_tune_entry* table, int max_entries, int* n_entries)
+{
+    if (n_entries) *n_entries = 0;
+    if (!h) return lbmp::set_error(LBMP_ERR_INVALID_ARG, "null handle");
+    if (reps < 1) return lbmp::set_error(LBMP_ERR_INVALID_ARG, "reps must be >= 1");
+    if (max_entries < 0) return lbmp::set_error(LBMP_ERR_INVALID_ARG, "max_entries must be >= 0");
+    if (h->kernel != 0 || !lbmp::fused_supported(h)) return LBMP_OK;
+    const int nmarch = h->D == 3 ? h->grid.nz : h->grid.ny;
+    int chunks[8], nc = 0;
+    chunks[nc++] = 0;
+    for (int c = 4; c <= 128; c *= 2)
+        if (c <= nmarch) chunks[nc++] = c;
+    const int ctas[3] = {0, 1, 2};
+    const int saved_chunk = h->opt_chunk, saved_ctas = h->opt_ctas;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    double best = 1e300;
+    int best_chunk = saved_chunk, best_ctas = saved_ctas, n = 0;
+    for (int i = 0; i < nc && e == cudaSuccess; ++i)
+        for (int j = 0; j < 3 && e == cudaSuccess; ++j) {
+            h->opt_chunk = chunks[i];
+            h->opt_ctas = ctas[j];
+            e = lbmp::launch_step_fused(h);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = lbmp::launch_step_fused(h);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) break;
+            const double per = (double)ms / reps;
+            if (table && n < max_entries) table[n] = lbmp_tune_entry{chunks[i], ctas[j], per};
+            ++n;
+            if (per < best) {
+                best = per;
+                best_chunk = chunks[i];
+                best_ctas = ctas[j];
+            }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        h->opt_chunk = saved_chunk;
+        h->opt_ctas = saved_ctas;
+        char buf[256];
+        snprintf(buf, sizeof buf, "autotune: %s", cudaGetErrorString(e));
+        return lbmp::set_error(LBMP_ERR_CUDA, buf);
+    }
+    h->opt_chunk = best_chunk;
+    h->opt_ctas = best_ctas;
+    if (n_entries) *n_entries = n;
+    return LBMP_OK;
+}
+
+LBMP_API int lbmp_device_name(char* out, int len)
+{
+    if (!out || len < 1) return lbmp::set_error(LBMP_ERR_INVALID_ARG, "bad output buffer");
+    int dev = 0;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) {
+        out[0] = 0;
+        char buf[256];
+        snprintf(buf, sizeof buf, "device name: %s", cudaGetErrorString(e));
+        return lbmp::set_error(LBMP_ERR_CUDA, buf);
+    }
+    strncpy(out, prop.name, (size_t)len - 1);
+    out[len - 1] = 0;
+    return LBMP_OK;
+}
+
+}  // extern "C"

@@ -18,7 +18,7 @@ FP32, FP16_SHIFTED, BF16_SHIFTED = 0, 1, 2
 CASE = {"rt": 0, "drop_static": 1, "flat": 2, "poiseuille": 3, "drop_sheet": 4, "shear_wave": 5,
         "uniform": 6}
 FLAG_WE_LIGHT, FLAG_DYNAMIC_VISC, FLAG_UNIFORM_FORCE = 1, 2, 4
-OPT_KERNEL = 0
+OPT_KERNEL, OPT_CHUNK, OPT_CTAS_PER_SM = 0, 1, 2
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5: "UNSTABLE",
           -6: "UNSUPPORTED"}
 
@@ -27,7 +27,7 @@ EXPORTS = ("lbmp_create", "lbmp_destroy", "lbmp_last_error", "lbmp_get_derived",
            "lbmp_step", "lbmp_sync", "lbmp_observables", "lbmp_get_state", "lbmp_set_state",
            "lbmp_state_bytes", "lbmp_upload", "lbmp_download", "lbmp_set_option", "lbmp_mass_noalloc",
            "lbmp_batch_create", "lbmp_batch_destroy", "lbmp_batch_add", "lbmp_batch_remove",
-           "lbmp_batch_step", "lbmp_batch_members")
+           "lbmp_batch_step", "lbmp_batch_members", "lbmp_autotune", "lbmp_device_name")
 
 
 class Grid(C.Structure):
@@ -54,6 +54,10 @@ class Obs(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TuneEntry(C.Structure):
+    _fields_ = [("chunk", C.c_int), ("ctas_per_sm", C.c_int), ("ms", C.c_double)]
 
 
 class LbmpError(RuntimeError):
@@ -97,6 +101,8 @@ def load(path=None):
     L.lbmp_batch_remove.argtypes = [vp, vp]
     L.lbmp_batch_step.argtypes = [vp, C.c_long, C.POINTER(C.c_int)]
     L.lbmp_batch_members.argtypes = [vp, C.POINTER(vp), C.POINTER(C.c_long), C.c_int]
+    L.lbmp_autotune.argtypes = [vp, C.c_int, C.POINTER(TuneEntry), C.c_int, C.POINTER(C.c_int)]
+    L.lbmp_device_name.argtypes = [C.c_char_p, C.c_int]
     _lib = L
     return L
 
@@ -126,6 +132,8 @@ class Domain:
     def __init__(self, D, dims, periodic=(1, 1, 1), stream=None, **params):
         L = load()
         self.D = D
+        self.periodic = tuple(int(v) for v in periodic)
+        self.storage = int(params.get("storage", FP32))
         self.dims = tuple(int(v) for v in dims)
         self.Q = 27 if D == 3 else 9
         self.N = self.dims[0] * self.dims[1] * self.dims[2]
@@ -162,6 +170,18 @@ class Domain:
 
     def set_kernel(self, k):
         _check(load().lbmp_set_option(self._h, OPT_KERNEL, int(k)))
+
+    def set_option(self, option, value):
+        _check(load().lbmp_set_option(self._h, int(option), int(value)))
+
+    def autotune(self, reps=5, cache=True):
+        """Pick the fused kernel's launch shape (lbmp_autotune).  With
+        cache=True the choice is stored per (device, lattice, storage, grid,
+        boundaries) in a JSON file (LBMP_TUNE_CACHE, default
+        ~/.cache/lbmp/tune.json) and reused without trials.  Returns
+        (chunk, ctas_per_sm, trials) with trials a list of (chunk, ctas, ms)."""
+        from . import tune
+        return tune.autotune(self, reps=reps, cache=cache)
 
     def init(self, case, args, seed=0):
         cid = CASE[case] if isinstance(case, str) else int(case)
