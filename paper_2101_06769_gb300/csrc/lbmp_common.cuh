@@ -72,6 +72,31 @@ struct DevParams {
     unsigned flags;
 };
 
+// Paired FP32 arithmetic (sm_100+ FFMA2/FADD2/FMUL2): one instruction
+// updates both lanes, each lane rounded exactly as its scalar counterpart.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+// TwoSum (Knuth) on both lanes: hi + lo accumulates v exactly
+__device__ __forceinline__ void two_sum2(float2& hi, float2& lo, float2 v)
+{
+    const float2 t = add2(hi, v);
+    const float2 bb = add2(t, neg2(hi));
+    lo = add2(lo, add2(add2(hi, neg2(add2(t, neg2(bb)))), add2(v, neg2(bb))));
+    hi = t;
+}
+
+// directions a < Q/2 in order of decreasing weight (faces, edges, corners)
+template <int D>
+__host__ __device__ constexpr int by_weight(int k)  // k-th direction a < Q/2 by decreasing weight
+{
+    constexpr int o3[13] = {4, 10, 12, 1, 3, 5, 7, 9, 11, 0, 2, 6, 8};
+    constexpr int o2[4] = {1, 3, 0, 2};
+    return D == 3 ? o3[k] : o2[k];
+}
+
 // ----------------------------------------------------------- pull helpers
 // Post-streaming population a at cell (x,y,z) lives in the buffer written by
 // the previous step at the upstream cell x - c_a (pull); across a half-way
@@ -268,27 +293,31 @@ __device__ __forceinline__ void phi_sum_shifted(const Get& get, float& hi, float
 {
     constexpr int Q = Lat<D>::Q;
     constexpr int C = Q / 2;
-    float wr, wq;
+    float wr, wq, wr2, wq2;
     get(C, wr, wq);
-    hi = wr;
-    lo = 0.f;
-    float qs = 0.f;
+    float2 h = f2(wr, 0.f), l = f2(0.f, 0.f), q = f2(0.f, 0.f);
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        if (a == C) continue;
+    for (int k = 0; k < C; ++k) {
+        const int a = by_weight<D>(k);
         get(a, wr, wq);
-        const float s = hi + wr;
-        lo += wr - (s - hi);
-        hi = s;
-        qs += wq;
+        get(Q - 1 - a, wr2, wq2);
+        const float2 v = f2(wr, wr2);
+        const float2 s = add2(h, v);
+        l = add2(l, add2(v, neg2(add2(s, neg2(h)))));
+        h = s;
+        q = add2(q, f2(wq, wq2));
     }
-    const float t = hi + qs;
-    const float bb = t - hi;
-    lo += (hi - (t - bb)) + (qs - bb);
-    hi = t;
-    const float s = hi + lo;
-    lo = lo - (s - hi);
-    hi = s;
+    // join the reference lanes (TwoSum), add the code sum (TwoSum), renormalise
+    float t = h.x + h.y;
+    float bb = t - h.x;
+    float e = (h.x - (t - bb)) + (h.y - bb);
+    const float qs = q.x + q.y;
+    const float t2 = t + qs;
+    bb = t2 - t;
+    e += (t - (t2 - bb)) + (qs - bb);
+    const float lsum = (l.x + l.y) + e;
+    hi = t2 + lsum;
+    lo = lsum - (hi - t2);
 }
 
 // R = (th + tl - sq) / den with the subtraction error-free (TwoSum), so that
@@ -386,40 +415,34 @@ __device__ __forceinline__ long long nbr_index(const DevParams& p, int a, int x,
 // largest, w = 8/27 or 4/9 of phi) is added first and every later term is
 // smaller than the running sum, so Dekker's Fast2Sum recovers each rounding
 // error exactly with three additions.
+//
+// The chain runs as two lanes of paired arithmetic: lane x starts from the
+// rest population and takes the directions a < Q/2, lane y starts from zero
+// and takes their opposites, both in order of decreasing weight (faces,
+// edges, corners) so that each term is no larger than the running sum on
+// smooth fields; the lanes are then joined by one TwoSum.
+
 template <int D, class Get>
 __device__ __forceinline__ void phi_sum(const Get& get, float& hi, float& lo)
 {
     constexpr int Q = Lat<D>::Q;
     constexpr int C = Q / 2;
-    hi = get(C);
-    lo = 0.f;
+    float2 h = f2(get(C), 0.f), l = f2(0.f, 0.f);
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        if (a == C) continue;
-        const float v = get(a);
-        const float s = hi + v;
-        lo += v - (s - hi);
-        hi = s;
+    for (int k = 0; k < C; ++k) {
+        const int a = by_weight<D>(k);
+        const float2 v = f2(get(a), get(Q - 1 - a));
+        const float2 s = add2(h, v);
+        l = add2(l, add2(v, neg2(add2(s, neg2(h)))));
+        h = s;
     }
-    const float s = hi + lo;  // renormalise: |lo| <= ulp(hi)/2
-    lo = lo - (s - hi);
-    hi = s;
-}
-
-// Paired FP32 arithmetic (sm_100+ FFMA2/FADD2/FMUL2): one instruction
-// updates both lanes, each lane rounded exactly as its scalar counterpart.
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-// TwoSum (Knuth) on both lanes: hi + lo accumulates v exactly
-__device__ __forceinline__ void two_sum2(float2& hi, float2& lo, float2 v)
-{
-    const float2 t = add2(hi, v);
-    const float2 bb = add2(t, neg2(hi));
-    lo = add2(lo, add2(add2(hi, neg2(add2(t, neg2(bb)))), add2(v, neg2(bb))));
-    hi = t;
+    // join the lanes exactly, then renormalise (|lo| <= ulp(hi)/2)
+    const float t = h.x + h.y;
+    const float bb = t - h.x;
+    const float e = (h.x - (t - bb)) + (h.y - bb);
+    const float lsum = (l.x + l.y) + e;
+    hi = t + lsum;
+    lo = lsum - (hi - t);
 }
 
 // Isotropic differences (Sec. 2.2) from the Q neighbour values
@@ -427,20 +450,22 @@ __device__ __forceinline__ void two_sum2(float2& hi, float2& lo, float2 v)
 // lap = 6 sum w (phi(x+c) - phi(x)).  Opposite neighbours are taken as a
 // pair: the gradient from the difference of their deviations from the
 // centre (exactly zero on a uniform field), the Laplacian from their sum.
-template <int D>
-__device__ __forceinline__ void stencil_from_nb(const float* nh, const float* nl, float grad[3], float& lap)
+// nb(a) returns the pair (hi, lo) of phi(x + c_a); centre = nb(C).
+template <int D, class NB>
+__device__ __forceinline__ void stencil_from(const NB& nb, float2 centre, float grad[3], float& lap)
 {
     constexpr int Q = Lat<D>::Q;
     constexpr int C = Q / 2;
-    const float2 hc = f2(-nh[C], -nh[C]), lc = f2(-nl[C], -nl[C]);
+    const float2 hc = f2(-centre.x, -centre.x), lc = f2(-centre.y, -centre.y);
     float gx = 0.f, gy = 0.f, gz = 0.f;
     float2 ls = f2(0.f, 0.f);
 #pragma unroll
     for (int a = 0; a < C; ++a) {
         const int b = Q - 1 - a;
         const float w = Lat<D>::w(a);
+        const float2 va = nb(a), vb = nb(b);
         // phi(x + c) - phi(x) and phi(x - c) - phi(x), hi and lo parts differenced first
-        const float2 dd = add2(add2(f2(nh[a], nh[b]), hc), add2(f2(nl[a], nl[b]), lc));
+        const float2 dd = add2(add2(f2(va.x, vb.x), hc), add2(f2(va.y, vb.y), lc));
         ls = fma2(f2(w, w), dd, ls);
         const float d = w * (dd.x - dd.y);
         if (Lat<D>::cx(a)) gx += Lat<D>::cx(a) * d;
@@ -451,6 +476,13 @@ __device__ __forceinline__ void stencil_from_nb(const float* nh, const float* nl
     grad[1] = 3.f * gy;
     grad[2] = (D == 3) ? 3.f * gz : 0.f;
     lap = 6.f * (ls.x + ls.y);
+}
+
+template <int D>
+__device__ __forceinline__ void stencil_from_nb(const float* nh, const float* nl, float grad[3], float& lap)
+{
+    constexpr int C = Lat<D>::Q / 2;
+    stencil_from<D>([&](int a) { return f2(nh[a], nl[a]); }, f2(nh[C], nl[C]), grad, lap);
 }
 
 // ------------------------------------------------------ flow collision

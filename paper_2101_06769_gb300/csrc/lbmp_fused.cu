@@ -190,29 +190,29 @@ __device__ __forceinline__ void fused_segment(const DevParams& p, const DirPtrs&
 #endif
         __syncthreads();
         if (valid) {
-            float nh[Q3], nl[Q3];
-#pragma unroll
-            for (int a = 0; a < Q3; ++a) {
-                const int cz = Lat<3>::cz(a);
-                const float2* pl = phiS + (cz < 0 ? sP : (cz == 0 ? sC : sN)) * PLANE;
-                const float2 v = pl[oslot + Lat<3>::cy(a) * RX + Lat<3>::cx(a)];
-                nh[a] = v.x;
-                nl[a] = v.y;
-            }
+            const float2* pm = phiS + sP * PLANE + oslot;
+            const float2* pc = phiS + sC * PLANE + oslot;
+            const float2* pn = phiS + sN * PLANE + oslot;
+            const float2 centre = pc[0];
             float grad[3], lap;
-            stencil_from_nb<3>(nh, nl, grad, lap);
+            stencil_from<3>(
+                [&](int a) {
+                    const int cz = Lat<3>::cz(a);
+                    return (cz < 0 ? pm : (cz == 0 ? pc : pn))[Lat<3>::cy(a) * RX + Lat<3>::cx(a)];
+                },
+                centre, grad, lap);
             CellState s;
             float dh[27];
-            flow_collide<3>(p, nh[13], grad, lap, m, s, dh);
+            flow_collide<3>(p, centre.x, grad, lap, m, s, dh);
             const int self = P.zs[1] + own.ys[1] + own.xs[1];
 #if LBMP_FUSED_DHSMEM
 #pragma unroll
             for (int a = 0; a < Q3; ++a) dS[a * NT + tid] = dh[a];
-            collide_outputs<3>(p, s, DhStrided{dS + tid, NT}, m, GFromStrided{gS + cur * Q3 * NT + tid, NT}, nh[13],
-                               nl[13], PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self});
+            collide_outputs<3>(p, s, DhStrided{dS + tid, NT}, m, GFromStrided{gS + cur * Q3 * NT + tid, NT},
+                               centre.x, centre.y, PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self});
 #else
-            collide_outputs<3>(p, s, DhArray{dh}, m, GFromStrided{gS + cur * Q3 * NT + tid, NT}, nh[13], nl[13],
-                               PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self});
+            collide_outputs<3>(p, s, DhArray{dh}, m, GFromStrided{gS + cur * Q3 * NT + tid, NT}, centre.x,
+                               centre.y, PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self});
 #endif
         }
         __syncthreads();
