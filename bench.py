@@ -238,6 +238,16 @@ def run_reference(args, wl):
     return 0
 
 
+def kernel_name(args, D):
+    if args.kernel == 1:
+        return "phi_pass_kernel + step_simple_kernel"
+    if args.storage != "fp32":
+        return "step_fused3s_kernel<Store%s>" % args.storage.upper() if D == 3 else "step_simple_kernel"
+    if D == 2:
+        return "step_fused2_kernel"
+    return "step_fused3b_kernel" if args.kernel == 2 else "step_fused3_kernel"
+
+
 def time_steps(step, stream, n):
     """mean ms of one call of step() over n calls, CUDA events on the stream"""
     import torch
@@ -322,7 +332,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rt3d", choices=sorted(WORKLOADS))
-    ap.add_argument("--kernel", type=int, default=0, help="0 fused (default), 1 reference pair")
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="0 fused (default), 1 reference pair, 2 fused with bulk-copy staging")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--grid", default=None, help="override nx,ny,nz (profiling on a smaller case)")
@@ -361,7 +372,7 @@ def main():
     dom.init(wl["case"], wl["args"], seed=wl["seed"] + rank)
     cells = dom.N
     launch = {"chunk": 0, "ctas_per_sm": 0, "tuned": False}
-    if not args.no_autotune and args.kernel == 0:
+    if not args.no_autotune and args.kernel != 1:
         # launch-shape autotuner of the library (trials do not advance the state)
         chunk, ctas, trials = dom.autotune(reps=3, cache=False)
         launch = {"chunk": chunk, "ctas_per_sm": ctas, "tuned": True, "trials": len(trials)}
@@ -404,7 +415,7 @@ def main():
     traffic = traffic_per_launch(args.workload, args.storage, cells) if (args.kernel == 0 and not args.grid) else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_kind": peak_kind, "traffic": traffic,
-            "kernel": "step_fused" if args.kernel == 0 else "step_simple + phi_pass",
+            "kernel": kernel_name(args, D),
             "bytes_per_cell": bpc}
 
     # end to end through the public API with host buffers: per step upload the

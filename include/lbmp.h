@@ -152,10 +152,13 @@ LBMP_API int lbmp_init(lbmp_handle *h, int case_id, const double *case_args, int
 /* Advance n time steps (Sec. 2.2/2.3), asynchronously on the handle's stream. */
 LBMP_API int lbmp_step(lbmp_handle *h, long n);
 
-/* Wait for the handle's stream; reports a device-side error status. */
+/* Wait for the handle's stream; reports a device-side error status:
+ * LBMP_ERR_TIMEOUT when a bounded wait inside a step kernel ran out (the
+ * kernel then stopped early and the state is invalid; re-initialise). */
 LBMP_API int lbmp_sync(lbmp_handle *h);
 
-/* FP64 observables (synchronises). */
+/* FP64 observables (synchronises); LBMP_ERR_TIMEOUT as lbmp_sync,
+ * LBMP_ERR_UNSTABLE when the state holds non-finite values. */
 LBMP_API int lbmp_observables(lbmp_handle *h, lbmp_obs *out);
 
 /* Host copies of the state in the exchange format (synchronise).  f and g
@@ -172,8 +175,13 @@ LBMP_API int lbmp_upload(lbmp_handle *h, const void *host, size_t bytes);
 LBMP_API int lbmp_download(lbmp_handle *h, void *host, size_t bytes);
 
 /* Options of a handle.
- *   LBMP_OPT_KERNEL: 0 = default fused kernel, 1 = simple reference pair
- *     (phi pass + one thread per cell), for A/B tests and measurement.
+ *   LBMP_OPT_KERNEL: 0 = default fused kernel (g staged by 4-byte cp.async),
+ *     1 = simple reference pair (phi pass + one thread per cell), 2 = for
+ *     FP32 D3Q27 with nx % 4 == 0 the fused kernel with g staged by bulk
+ *     copies (TMA engine) and bounded mbarrier waits, else as 0; for A/B
+ *     tests and measurement.  0 and 1 give bitwise identical results; 2
+ *     performs the same operations but the compiler may fuse a multiply-add
+ *     differently, so it agrees to within a few ulps.
  *   LBMP_OPT_CHUNK: planes (rows in 2-D) per work item of the fused
  *     kernels, 0 = automatic (the default), else >= 1.
  *   LBMP_OPT_CTAS_PER_SM: resident CTAs per SM of the fused kernels'
@@ -181,7 +189,17 @@ LBMP_API int lbmp_download(lbmp_handle *h, void *host, size_t bytes);
  *     (values above the maximum act as the maximum).
  * Launch-shape options change speed only, never results.  Returns
  * LBMP_ERR_INVALID_ARG for an unknown option or an out-of-range value. */
-enum { LBMP_OPT_KERNEL = 0, LBMP_OPT_CHUNK = 1, LBMP_OPT_CTAS_PER_SM = 2 };
+enum {
+    LBMP_OPT_KERNEL = 0,
+    LBMP_OPT_CHUNK = 1,
+    LBMP_OPT_CTAS_PER_SM = 2,
+    LBMP_OPT_WAIT_LIMIT_NS = 3, /* bound of every wait inside a step kernel, in ns
+                                   (default 2e9; range [1e3, 6e10]) */
+    LBMP_OPT_TEST_STALL = 4     /* test only: 1 arms each staging barrier of the
+                                   bulk-copy kernel for 16 bytes more than its copies
+                                   deliver, so that its waits run out and the next
+                                   lbmp_sync reports LBMP_ERR_TIMEOUT; 0 (default) off */
+};
 LBMP_API int lbmp_set_option(lbmp_handle *h, int option, long value);
 
 /* Launch-shape autotuner of the fused step kernel (no counterpart in the

@@ -105,6 +105,8 @@ void fill_devparams(lbmp_handle* h)
     q.g_accel = (float)d.g_accel;
     q.force_x = (float)d.force_x;
     q.flags = h->params.flags;
+    q.wait_ns = 2000000000ull;  // 2 s
+    q.test_extra_tx = 0;
 }
 
 void free_handle(lbmp_handle* h)
@@ -119,6 +121,18 @@ void free_handle(lbmp_handle* h)
     delete h;
 }
 
+// slot of red_out (a double) that holds the device status word (an int);
+// slots 0-5 take the observables, 12-15 the reference mass, 16- the columns
+constexpr int kStatusSlot = 8;
+
+// LBMP_ERR_TIMEOUT if a step kernel recorded a bounded wait that ran out
+int status_of(int word)
+{
+    if (word & lbmp::kStatusWaitTimeout)
+        return fail(LBMP_ERR_TIMEOUT, "a bounded wait of a step kernel ran out; the state is invalid");
+    return LBMP_OK;
+}
+
 int check_handle(const lbmp_handle* h)
 {
     if (!h) return fail(LBMP_ERR_INVALID_ARG, "null handle");
@@ -129,6 +143,13 @@ int check_handle(const lbmp_handle* h)
 
 namespace lbmp {
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+cudaError_t launch_step(lbmp_handle* h)
+{
+    if (h->kernel == 1 || !fused_supported(h)) return launch_step_simple(h);
+    if (h->kernel == 2 && bulk_supported(h)) return launch_step_fused_bulk(h);
+    return launch_step_fused(h);
+}
 }  // namespace lbmp
 
 extern "C" {
@@ -194,6 +215,8 @@ int lbmp_create(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* 
     if (e == cudaSuccess) e = cudaMalloc(&h->red, sizeof(double) * 4 * h->red_blocks);
     const int nv = (D == 3) ? grid->nz : grid->ny;
     if (e == cudaSuccess) e = cudaMalloc(&h->red_out, sizeof(double) * (16 + 2 * (size_t)nv));
+    if (e == cudaSuccess) e = cudaMemset(h->red_out, 0, sizeof(double) * 16);
+    if (e == cudaSuccess) h->dp.status = (int*)(h->red_out + kStatusSlot);
     if (e != cudaSuccess) {
         free_handle(h);
         cudaGetLastError();
@@ -229,7 +252,7 @@ int lbmp_set_option(lbmp_handle* h, int option, long value)
     if (rc) return rc;
     switch (option) {
     case LBMP_OPT_KERNEL:
-        if (value < 0 || value > 1) return fail(LBMP_ERR_INVALID_ARG, "kernel must be 0 or 1");
+        if (value < 0 || value > 2) return fail(LBMP_ERR_INVALID_ARG, "kernel must be 0, 1 or 2");
         h->kernel = (int)value;
         return LBMP_OK;
     case LBMP_OPT_CHUNK:
@@ -239,6 +262,14 @@ int lbmp_set_option(lbmp_handle* h, int option, long value)
     case LBMP_OPT_CTAS_PER_SM:
         if (value < 0 || value > 64) return fail(LBMP_ERR_INVALID_ARG, "CTAs per SM must lie in [0, 64]");
         h->opt_ctas = (int)value;
+        return LBMP_OK;
+    case LBMP_OPT_WAIT_LIMIT_NS:
+        if (value < 1000 || value > 60000000000L) return fail(LBMP_ERR_INVALID_ARG, "wait limit must lie in [1 us, 60 s]");
+        h->dp.wait_ns = (unsigned long long)value;
+        return LBMP_OK;
+    case LBMP_OPT_TEST_STALL:
+        if (value < 0 || value > 1) return fail(LBMP_ERR_INVALID_ARG, "test stall must be 0 or 1");
+        h->dp.test_extra_tx = value ? 16u : 0u;
         return LBMP_OK;
     default:
         return fail(LBMP_ERR_INVALID_ARG, "unknown option");
@@ -267,6 +298,7 @@ int lbmp_init(lbmp_handle* h, int case_id, const double* case_args, int nargs, u
         const int nv = (&h->grid.nx)[h->D - 1];
         h->probe[h->D - 1] = pv < 0 ? 0 : (pv >= nv ? nv - 1 : pv);
     }
+    LBMP_CUDA(cudaMemsetAsync(h->red_out + kStatusSlot, 0, sizeof(double), h->stream), "status reset");
     LBMP_CUDA(lbmp::launch_init(h, case_id, a, seed), "init kernel");
     LBMP_CUDA(lbmp::launch_mass(h, h->red_out + 12), "reference mass");
     return LBMP_OK;
@@ -278,8 +310,7 @@ int lbmp_step(lbmp_handle* h, long n)
     if (rc) return rc;
     if (n < 0) return fail(LBMP_ERR_INVALID_ARG, "negative step count");
     for (long k = 0; k < n; ++k) {
-        cudaError_t e = (h->kernel == 1 || !lbmp::fused_supported(h)) ? lbmp::launch_step_simple(h)
-                                                                        : lbmp::launch_step_fused(h);
+        cudaError_t e = lbmp::launch_step(h);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel");
         h->parity ^= 1;
         h->step += 1;
@@ -292,7 +323,9 @@ int lbmp_sync(lbmp_handle* h)
     int rc = check_handle(h);
     if (rc) return rc;
     LBMP_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
-    return LBMP_OK;
+    int word = 0;
+    LBMP_CUDA(cudaMemcpy(&word, h->red_out + kStatusSlot, sizeof word, cudaMemcpyDeviceToHost), "status word");
+    return status_of(word);
 }
 
 int lbmp_observables(lbmp_handle* h, lbmp_obs* out)
@@ -337,7 +370,11 @@ int lbmp_observables(lbmp_handle* h, lbmp_obs* out)
             break;
         }
     out->step = h->step;
+    int word = 0;
+    memcpy(&word, host + kStatusSlot, sizeof word);
     delete[] host;
+    rc = status_of(word);
+    if (rc != LBMP_OK) return rc;
     return out->health ? fail(LBMP_ERR_UNSTABLE, "non-finite values in the state") : LBMP_OK;
 }
 
@@ -382,6 +419,7 @@ int lbmp_set_state(lbmp_handle* h, const double* f, const double* g)
     if (e == cudaSuccess) e = cudaMallocAsync(&dg, n * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(df, f, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dg, g, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->red_out + kStatusSlot, 0, sizeof(double), h->stream);
     if (e == cudaSuccess) e = lbmp::launch_set_state(h, df, dg);
     if (e == cudaSuccess) e = lbmp::launch_mass(h, h->red_out + 12);
     if (df) cudaFreeAsync(df, h->stream);

@@ -70,7 +70,13 @@ struct DevParams {
     float lam_sharp;        // lambda_phi * 4 / W
     float g_accel, force_x;
     unsigned flags;
+    int* status;            // device status word of the handle (kStatus* bits), or null
+    unsigned long long wait_ns;  // bound of every wait of a step kernel (nanoseconds)
+    unsigned test_extra_tx;      // test only: extra bytes expected per staged plane (its wait runs out)
 };
+
+// bits of the device status word
+constexpr int kStatusWaitTimeout = 1;  // a bounded wait of a step kernel ran out
 
 // Paired FP32 arithmetic (sm_100+ FFMA2/FADD2/FMUL2): one instruction
 // updates both lanes, each lane rounded exactly as its scalar counterpart.

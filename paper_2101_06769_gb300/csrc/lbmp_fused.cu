@@ -62,18 +62,6 @@ struct StageCopy {
     }
 };
 
-template <bool Walls>
-struct PullLoad {
-    const float* const* base;
-    const Column& C;
-    const Plane& P;
-    float* v;
-    template <int a>
-    __device__ __forceinline__ void step() const
-    {
-        v[a] = __ldg(pulled<Walls, a>(base, C, P));
-    }
-};
 
 template <bool Walls>
 struct FCopy {

@@ -23,7 +23,7 @@ struct lbmp_handle {
     float* phi;        // phi = sum g as hi [0, N) + lo [N, 2N), refreshed by the phi pass
     int parity;        // f[parity], g[parity] hold the current state
     long step;
-    int kernel;        // LBMP_OPT_KERNEL
+    int kernel;        // LBMP_OPT_KERNEL: 0 default, 1 reference pair, 2 bulk-copy staging
     int opt_chunk;     // LBMP_OPT_CHUNK: planes (rows) per work item, 0 = automatic
     int opt_ctas;      // LBMP_OPT_CTAS_PER_SM: resident CTAs per SM of the grid, 0 = occupancy maximum
     int probe[3];
@@ -94,6 +94,10 @@ int batch3_tile_x();
 int batch3_tile_y();
 cudaError_t launch_step_fused2(lbmp_handle* h);
 cudaError_t launch_step_fused16(lbmp_handle* h);  // shifted 16-bit storage, D3Q27
+bool bulk_supported(const lbmp_handle* h);         // FP32 D3Q27 with nx % 4 == 0
+cudaError_t launch_step_fused_bulk(lbmp_handle* h);
+// the step kernel(s) selected by LBMP_OPT_KERNEL for this handle (no parity flip)
+cudaError_t launch_step(lbmp_handle* h);
 int batch2_tile_x();
 cudaError_t prepare_batch2(int device);
 cudaError_t launch_batch2(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream);

@@ -114,6 +114,20 @@ struct Unroll<0> {
     }
 };
 
+// post-streaming values of the 27 directions of one cell into registers
+template <bool Walls>
+struct PullLoad {
+    const float* const* base;
+    const Column& C;
+    const Plane& P;
+    float* v;
+    template <int a>
+    __device__ __forceinline__ void step() const
+    {
+        v[a] = __ldg(pulled<Walls, a>(base, C, P));
+    }
+};
+
 // plane whose phi stands for plane zz: periodic wrap, or the mirrored ghost
 // at a wall (reading A17)
 __device__ __forceinline__ int plane_src(const DevParams& p, int zz)

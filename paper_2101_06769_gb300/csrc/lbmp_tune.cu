@@ -18,7 +18,7 @@ LBMP_API int lbmp_autotune(lbmp_handle* h, int reps, lbmp_tune_entry* table, int
     if (!h) return lbmp::set_error(LBMP_ERR_INVALID_ARG, "null handle");
     if (reps < 1) return lbmp::set_error(LBMP_ERR_INVALID_ARG, "reps must be >= 1");
     if (max_entries < 0) return lbmp::set_error(LBMP_ERR_INVALID_ARG, "max_entries must be >= 0");
-    if (h->kernel != 0 || !lbmp::fused_supported(h)) return LBMP_OK;
+    if (h->kernel == 1 || !lbmp::fused_supported(h)) return LBMP_OK;
     const int nmarch = h->D == 3 ? h->grid.nz : h->grid.ny;
     int chunks[8], nc = 0;
     chunks[nc++] = 0;
@@ -35,9 +35,9 @@ LBMP_API int lbmp_autotune(lbmp_handle* h, int reps, lbmp_tune_entry* table, int
         for (int j = 0; j < 3 && e == cudaSuccess; ++j) {
             h->opt_chunk = chunks[i];
             h->opt_ctas = ctas[j];
-            e = lbmp::launch_step_fused(h);  // warm-up
+            e = lbmp::launch_step(h);  // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = lbmp::launch_step_fused(h);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = lbmp::launch_step(h);
             if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;

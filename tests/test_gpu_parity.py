@@ -48,6 +48,12 @@ CASES = {
                      phys=dict(rho_ratio=10.0, nu_ratio=5.0, nu_h=0.02, sigma=5e-3, g_accel=1e-5,
                                mobility=0.03, width=4.0, flags=2),
                      case="rt", args=[23.0, 3.0, 1e-2, 1.0], seed=6),
+    # nx a multiple of 4 but not of the tile width: the bulk-copy staging with
+    # windows that wrap around x, ragged tiles in x and y, walls
+    "wide3d": dict(D=3, dims=(44, 29, 23), periodic=(1, 1, 0),
+                   phys=dict(rho_ratio=10.0, nu_ratio=5.0, nu_h=0.02, sigma=5e-3, g_accel=1e-5,
+                             mobility=0.03, width=4.0),
+                   case="rt", args=[11.0, 3.0, 1e-2, 1.0], seed=8),
     # thin 3-D with walls: every thread block touches a wall plane
     "thin3d": dict(D=3, dims=(8, 6, 5), periodic=(1, 1, 0),
                    phys=dict(rho_ratio=3.0, nu_ratio=1.0, nu_h=0.05, sigma=1e-2, g_accel=1e-4,
@@ -83,7 +89,7 @@ def test_init_matches_oracle(name):
         assert np.abs(fg).max() == 0.0
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_step_parity_100(name, kernel):
     c, o, d = make_pair(name)
@@ -112,19 +118,26 @@ def test_step_parity_odd_even(name, steps):
     assert rel_err(fg, fo) <= TOL and rel_err(gg, go) <= TOL and rel_err(pg, po) <= TOL
 
 
-def test_kernels_agree_bitwise():
-    """The fused kernel and the reference pair perform the same FP32 operations
-    in the same order, so their states agree exactly."""
-    c = CASES["splash3d"]
-    a = Domain(c["D"], c["dims"], c["periodic"], **c["phys"])
-    b = Domain(c["D"], c["dims"], c["periodic"], **c["phys"])
-    for dm, k in ((a, 0), (b, 1)):
+@pytest.mark.parametrize("name", ["splash3d", "wide3d", "thin3d", "rt3d", "ragged3d"])
+def test_kernels_agree(name):
+    """The default fused kernel and the reference pair perform the same FP32
+    operations in the same order, so their states agree exactly.  The
+    bulk-copy staging kernel (option 2, nx % 4 == 0) stages the same values;
+    compiled in another unit it may fuse a multiply-add differently, so it
+    agrees to within rounding (measured: 1 ulp in a handful of values after
+    one step, at most 1.2e-6 of the value range after 25, where the FP32
+    parity bar against the FP64 oracle is 1e-5)."""
+    c = CASES[name]
+    states = []
+    for k in (0, 1, 2):
+        dm = Domain(c["D"], c["dims"], c["periodic"], **c["phys"])
         dm.init(c["case"], c["args"], seed=c["seed"])
         dm.set_kernel(k)
         dm.step(25)
-    fa, ga, pa = a.get_state()
-    fb, gb, pb = b.get_state()
-    assert np.array_equal(fa, fb) and np.array_equal(ga, gb) and np.array_equal(pa, pb)
+        states.append(dm.get_state())
+    assert all(np.array_equal(x, y) for x, y in zip(states[0], states[1]))
+    for x, y in zip(states[0], states[2]):
+        assert rel_err(y, x) <= 5e-6
 
 
 def test_set_get_round_trip_is_exact():
