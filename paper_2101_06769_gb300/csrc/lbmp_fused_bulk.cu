@@ -5,10 +5,10 @@
 // difference is how the pulled g of a plane reaches shared memory.  Instead
 // of one 4-byte cp.async per population and cell (tile and ring), each CTA
 // copies, for every direction a and every output row y of the tile plus its
-// ring (TY + 2 rows), the 40-float window [x0-4, x0+36) of the source row
-// y - c_y of plane z - c_z: a 16-byte aligned run that contains the pulled
-// value of every tile and ring cell of that row (x - c_x lies in
-// [x0-2, x0+33]).  27 x (TY+2) bulk copies of 160 bytes per plane (a row
+// ring (TY + 2 rows), the (TX+8)-float window [x0-4, x0+TX+4) of the source
+// row y - c_y of plane z - c_z: a 16-byte aligned run that contains the
+// pulled value of every tile and ring cell of that row (x - c_x lies in
+// [x0-2, x0+TX+1]).  27 x (TY+2) bulk copies per plane (a row
 // that wraps around the periodic x boundary is split, nx being a multiple of
 // 4), completed on an mbarrier with a transaction count; the threads then
 // read the window at column x - x0 + 4 - c_x.  At a wall plane a bounced
@@ -29,7 +29,7 @@ namespace {
 
 using namespace tile;
 
-constexpr int WX = 40;            // window width (floats)
+constexpr int WX = TX + 8;        // window width (floats): [x0-4, x0+TX+4)
 constexpr int WR = TY + 2;        // window rows: tile rows and the two ring rows
 constexpr int WIN = Q3 * WR * WX;  // floats of one staged plane
 constexpr unsigned kPlaneBytes = sizeof(float) * WIN;
