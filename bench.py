@@ -261,10 +261,13 @@ def time_steps(step, stream, n):
     return a.elapsed_time(b) / n
 
 
-# the batched form: one batch of uneven Rayleigh-Taylor members (3-D cubes
-# and slabs, 2-D squares), the same non-dimensional set-up scaled per member
-BATCH_MIX = [(3, (64, 64, 64))] * 2 + [(3, (96, 96, 96))] * 2 + [(3, (128, 128, 128))] * 2 + \
-            [(3, (128, 128, 256))] * 2 + [(2, (512, 512, 1))] * 4
+# the batched form: one batch of uneven Rayleigh-Taylor members with sizes
+# from the serving stream's ranges (3-D 64^3-128^3 cubes, 2-D 128^2-512^2
+# squares), the same non-dimensional set-up scaled per member
+BATCH_MIX = [(3, (64, 64, 64))] * 6 + [(3, (96, 96, 96))] * 4 + [(3, (128, 128, 128))] * 2 + \
+            [(2, (128, 128, 1))] * 4 + [(2, (256, 256, 1))] * 4 + [(2, (512, 512, 1))] * 2
+BATCH_MIX_DESC = ("6x64^3, 4x96^3, 2x128^3 D3Q27 + 4x128^2, 4x256^2, 2x512^2 D2Q9 Rayleigh-Taylor, FP32 "
+                  "(sizes of the serving stream)")
 
 
 def measure_forms(args, wl, stream, peak, pg):
@@ -306,6 +309,8 @@ def measure_forms(args, wl, stream, peak, pg):
         doms.append(d)
         cells += d.N
         byts += BYTES_PER_CELL[Dm] * d.N
+    if not args.no_autotune:
+        b.autotune(reps=2)  # tile shape and planes per item of the batch kernels
     b.step(16)  # rebuild, capture and warm the graphs
     nb = 4 * max(1, n // 16)  # graph replays of 16 steps
     ms16 = time_steps(lambda: b.step(16), stream, nb)
@@ -315,12 +320,30 @@ def measure_forms(args, wl, stream, peak, pg):
     gbs = byts / (ms * 1e-3) / 1e9
     out["batched"] = {"mlups": mlups, "ms_per_step": ms, "members": len(doms), "cells": cells,
                       "bytes_per_step": byts, "achieved_gbs": gbs, "frac": gbs / peak,
-                      "mix": "2x64^3, 2x96^3, 2x128^3, 2x128x128x256 D3Q27 + 4x512^2 D2Q9 Rayleigh-Taylor, FP32",
+                      "mix": BATCH_MIX_DESC,
                       "steps": nb * 16}
     for d in doms:
         b.remove(d)
-        d.close()
     b.close()
+    # the same members stepped one domain at a time (one launch per member and
+    # step, each with its own tuned launch shape): the plain one-domain form
+    for d in doms:
+        if not args.no_autotune:
+            d.autotune(reps=2, cache=False)
+    na = max(4, n // 4)
+
+    def alone_round():
+        for d in doms:
+            d.step(1)
+
+    ms_alone = time_steps(alone_round, stream, na)
+    launches += na * len(doms)
+    _, mlups_alone = aggregate(ms_alone * na, cells, na, pg)
+    out["batched"]["alone_mlups"] = mlups_alone
+    out["batched"]["alone_ms_per_step"] = ms_alone
+    out["batched"]["speedup_vs_alone"] = mlups / mlups_alone
+    for d in doms:
+        d.close()
     out["_launches"] = launches
     return out
 

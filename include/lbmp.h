@@ -193,6 +193,8 @@ enum {
     LBMP_OPT_KERNEL = 0,
     LBMP_OPT_CHUNK = 1,
     LBMP_OPT_CTAS_PER_SM = 2,
+    LBMP_OPT_TILE = 5,          /* tile shape of the FP32 D3Q27 fused kernel:
+                                   0 = 32 x 4 (default), 1 = 16 x 8, 2 = 8 x 16 */
     LBMP_OPT_WAIT_LIMIT_NS = 3, /* bound of every wait inside a step kernel, in ns
                                    (default 2e9; range [1e3, 6e10]) */
     LBMP_OPT_TEST_STALL = 4     /* test only: 1 arms each staging barrier of the
@@ -203,11 +205,12 @@ enum {
 LBMP_API int lbmp_set_option(lbmp_handle *h, int option, long value);
 
 /* Launch-shape autotuner of the fused step kernel (no counterpart in the
- * paper; serving-side tuning).  Times each candidate (planes per work item
- * in {automatic, 4, 8, 16, 32, 64, 128} up to the marching extent, CTAs per
- * SM in {maximum, 1, 2}) over `reps` launches (>= 1) after one warm-up
- * launch, with CUDA events on the handle's stream, and keeps the fastest as
- * the handle's options.  Trial launches read the current population set and
+ * paper; serving-side tuning).  Times each candidate (tile shape in {32 x 4,
+ * 16 x 8, 8 x 16} for the FP32 D3Q27 kernel, planes per work item -- cells
+ * per thread per work item -- in {automatic, 4, 8, 16, 32, 64, 128} up to
+ * the marching extent, CTAs per SM in {maximum, 1, 2}) over `reps` launches
+ * (>= 1) after one warm-up launch, with CUDA events on the handle's stream,
+ * and keeps the fastest as the handle's options.  Trial launches read the current population set and
  * write the other one, which the next step overwrites: the state is not
  * advanced and results are unchanged.  `table` (caller-owned, may be NULL)
  * receives up to max_entries trials; *n_entries (may be NULL) the number of
@@ -217,6 +220,7 @@ typedef struct {
     int chunk;        /* LBMP_OPT_CHUNK value of the trial (0 = automatic) */
     int ctas_per_sm;  /* LBMP_OPT_CTAS_PER_SM value of the trial (0 = maximum) */
     double ms;        /* mean time of one step launch */
+    int tile;         /* LBMP_OPT_TILE value of the trial */
 } lbmp_tune_entry;
 LBMP_API int lbmp_autotune(lbmp_handle *h, int reps, lbmp_tune_entry *table, int max_entries, int *n_entries);
 
@@ -257,6 +261,18 @@ LBMP_API int lbmp_batch_step(lbmp_batch *b, long n, int *n_finished);
 /* Members and their remaining steps: fills up to max entries, returns the
  * member count (or a negative status). */
 LBMP_API int lbmp_batch_members(const lbmp_batch *b, lbmp_handle **members, long *steps_left, int max);
+
+/* Autotuner of the batch kernels (no counterpart in the paper): times one
+ * step of the current members' kernels (the D3Q27 and D2Q9 batch kernels,
+ * no epilogue) for each D3Q27 tile shape {32 x 4, 16 x 8, 8 x 16} and
+ * planes (rows) per work item {8, 16, 32, 64}, over `reps` launches after a
+ * warm-up, and keeps the fastest for the batch; the graphs are re-captured at
+ * the next lbmp_batch_step.  Trial launches read each member's current
+ * population set and write the other one: no member advances and results
+ * are unchanged.  table / n_entries as in lbmp_autotune (entry.tile and
+ * entry.chunk set, ctas_per_sm = 0).  Synchronises the batch's stream. */
+LBMP_API int lbmp_batch_autotune(lbmp_batch *b, int reps, lbmp_tune_entry *table, int max_entries,
+                                 int *n_entries);
 
 /* Mass without allocation (the paper has no counterpart: this is a service
  * of the library).  For callers that cannot allocate device memory, e.g. a

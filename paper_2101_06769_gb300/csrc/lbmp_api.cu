@@ -147,8 +147,12 @@ int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 cudaError_t launch_step(lbmp_handle* h)
 {
     if (h->kernel == 1 || !fused_supported(h)) return launch_step_simple(h);
+    if (h->params.storage != LBMP_FP32) return launch_step_fused16(h);
+    if (h->D == 2) return launch_step_fused2(h);
     if (h->kernel == 2 && bulk_supported(h)) return launch_step_fused_bulk(h);
-    return launch_step_fused(h);
+    if (h->opt_tile == 1) return launch_step_fused3_t16x8(h);
+    if (h->opt_tile == 2) return launch_step_fused3_t8x16(h);
+    return launch_step_fused3(h);
 }
 }  // namespace lbmp
 
@@ -262,6 +266,10 @@ int lbmp_set_option(lbmp_handle* h, int option, long value)
     case LBMP_OPT_CTAS_PER_SM:
         if (value < 0 || value > 64) return fail(LBMP_ERR_INVALID_ARG, "CTAs per SM must lie in [0, 64]");
         h->opt_ctas = (int)value;
+        return LBMP_OK;
+    case LBMP_OPT_TILE:
+        if (value < 0 || value > 2) return fail(LBMP_ERR_INVALID_ARG, "tile must be 0, 1 or 2");
+        h->opt_tile = (int)value;
         return LBMP_OK;
     case LBMP_OPT_WAIT_LIMIT_NS:
         if (value < 1000 || value > 60000000000L) return fail(LBMP_ERR_INVALID_ARG, "wait limit must lie in [1 us, 60 s]");

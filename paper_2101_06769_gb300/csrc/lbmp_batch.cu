@@ -6,7 +6,11 @@
 // epilogue flips the parities and counts the steps down.  Nothing a step
 // needs comes from the host, so the kernels of a run of steps are captured
 // once in a CUDA graph and the graph is replayed until the membership (or the
-// set of members with steps left) changes.
+// set of members with steps left) changes.  Within a step the D3Q27 and the
+// D2Q9 batch kernels run on two forked streams (independent members), joined
+// before the epilogue.  The tile shape of the D3Q27 kernel and the planes
+// (rows) per work item are options of the batch, picked by
+// lbmp_batch_autotune.
 #include <stdio.h>
 #include <string.h>
 
@@ -31,6 +35,9 @@ struct lbmp_batch {
     size_t budget;
     cudaStream_t stream;
     bool own_stream;  // created here: the legacy default stream cannot be captured
+    cudaStream_t side;               // second branch of a step (D2Q9 members)
+    cudaEvent_t fork, join;
+    int tile, chunk;                 // D3Q27 tile shape (LBMP_OPT_TILE values), planes per item (0 = 16)
     int device;
     std::vector<Member> members;
     lbmp::BatchDomain* d_table;       // device, kMaxMembers entries: 3-D members, then 2-D members
@@ -51,15 +58,34 @@ void drop_graphs(lbmp_batch* b)
     b->g_long = b->g_one = nullptr;
 }
 
+// the step kernels of one step (no epilogue): D3Q27 members on the batch
+// stream, D2Q9 members on the side stream when both kinds are present
+cudaError_t step_kernels(lbmp_batch* b)
+{
+    cudaError_t e = cudaSuccess;
+    const bool fork = b->ndom3 && b->ndom2;
+    if (fork) {
+        e = cudaEventRecord(b->fork, b->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
+    }
+    if (e == cudaSuccess && b->ndom3)
+        e = lbmp::batch3_ops(b->tile).launch(b->d_table, b->ndom3, b->nitems3, b->device, b->stream);
+    if (e == cudaSuccess && b->ndom2)
+        e = lbmp::launch_batch2(b->d_table + b->ndom3, b->ndom2, b->nitems2, b->device, fork ? b->side : b->stream);
+    if (e == cudaSuccess && fork) {
+        e = cudaEventRecord(b->join, b->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join, 0);
+    }
+    return e;
+}
+
 cudaError_t capture(lbmp_batch* b, int steps, cudaGraphExec_t* out)
 {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     for (int k = 0; k < steps && e == cudaSuccess; ++k) {
-        if (b->ndom3) e = lbmp::launch_batch3(b->d_table, b->ndom3, b->nitems3, b->device, b->stream);
-        if (e == cudaSuccess && b->ndom2)
-            e = lbmp::launch_batch2(b->d_table + b->ndom3, b->ndom2, b->nitems2, b->device, b->stream);
+        e = step_kernels(b);
         if (e == cudaSuccess) e = lbmp::launch_batch_epilogue(b->d_table, b->ndom3 + b->ndom2, b->stream);
     }
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
@@ -70,15 +96,17 @@ cudaError_t capture(lbmp_batch* b, int steps, cudaGraphExec_t* out)
 }
 
 // Rebuild the device table from the members with steps left (3-D members
-// first, then 2-D, each with its own work numbering), and the graphs.
-cudaError_t rebuild(lbmp_batch* b)
+// first, then 2-D, each with its own work numbering), and (graphs) the graphs.
+cudaError_t rebuild(lbmp_batch* b, bool graphs = true)
 {
     drop_graphs(b);
     b->h_table.clear();
     b->ndom3 = b->nitems3 = b->ndom2 = b->nitems2 = 0;
     for (int D = 3; D >= 2; --D) {
     int item = 0;
-    const int TX = D == 3 ? lbmp::batch3_tile_x() : lbmp::batch2_tile_x(), TY = D == 3 ? lbmp::batch3_tile_y() : 1;
+    const lbmp::Batch3Ops& ops3 = lbmp::batch3_ops(b->tile);
+    const int TX = D == 3 ? ops3.tile_x : lbmp::batch2_tile_x(), TY = D == 3 ? ops3.tile_y : 1;
+    const int chunk = b->chunk > 0 ? b->chunk : 16;
     for (const Member& m : b->members) {
         if (m.left <= 0 || m.h->D != D) continue;
         const lbmp_handle* h = m.h;
@@ -95,7 +123,7 @@ cudaError_t rebuild(lbmp_batch* b)
         const int nmarch = D == 3 ? h->grid.nz : h->grid.ny;
         d.tiles_x = (h->grid.nx + TX - 1) / TX;
         d.tiles_y = D == 3 ? (h->grid.ny + TY - 1) / TY : 1;
-        d.chunk = nmarch < 16 ? nmarch : 16;
+        d.chunk = nmarch < chunk ? nmarch : chunk;
         d.item_begin = item;
         d.items = d.tiles_x * d.tiles_y * ((nmarch + d.chunk - 1) / d.chunk);
         item += d.items;
@@ -112,15 +140,15 @@ cudaError_t rebuild(lbmp_batch* b)
     const int ndom = b->ndom3 + b->ndom2;
     cudaError_t e = cudaSuccess;
     if (ndom > 0) {
-        if (b->ndom3) e = lbmp::prepare_batch3(b->device);
+        if (b->ndom3) e = lbmp::batch3_ops(b->tile).prepare(b->device);
         if (e == cudaSuccess && b->ndom2) e = lbmp::prepare_batch2(b->device);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(b->d_table, b->h_table.data(), sizeof(lbmp::BatchDomain) * ndom,
                                 cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess) e = capture(b, kGraphSteps, &b->g_long);
-        if (e == cudaSuccess) e = capture(b, 1, &b->g_one);
+        if (e == cudaSuccess && graphs) e = capture(b, kGraphSteps, &b->g_long);
+        if (e == cudaSuccess && graphs) e = capture(b, 1, &b->g_one);
     }
-    if (e == cudaSuccess) b->dirty = false;
+    if (e == cudaSuccess) b->dirty = !graphs;
     return e;
 }
 
@@ -146,6 +174,10 @@ LBMP_API int lbmp_batch_create(size_t hbm_budget, void* cuda_stream, lbmp_batch*
     b->budget = hbm_budget;
     b->stream = (cudaStream_t)cuda_stream;
     b->own_stream = false;
+    b->side = nullptr;
+    b->fork = b->join = nullptr;
+    b->tile = 0;
+    b->chunk = 0;
     b->d_table = nullptr;
     b->ndom3 = b->nitems3 = b->ndom2 = b->nitems2 = 0;
     b->dirty = true;
@@ -155,8 +187,14 @@ LBMP_API int lbmp_batch_create(size_t hbm_budget, void* cuda_stream, lbmp_batch*
         e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
         b->own_stream = e == cudaSuccess;
     }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_table, sizeof(lbmp::BatchDomain) * kMaxMembers);
     if (e != cudaSuccess) {
+        if (b->fork) cudaEventDestroy(b->fork);
+        if (b->join) cudaEventDestroy(b->join);
+        if (b->side) cudaStreamDestroy(b->side);
         if (b->own_stream) cudaStreamDestroy(b->stream);
         delete b;
         return batch_cuda_fail(e, "batch table");
@@ -171,6 +209,9 @@ LBMP_API int lbmp_batch_destroy(lbmp_batch* b)
     cudaStreamSynchronize(b->stream);
     drop_graphs(b);
     if (b->d_table) cudaFree(b->d_table);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->side) cudaStreamDestroy(b->side);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return LBMP_OK;
@@ -253,6 +294,52 @@ LBMP_API int lbmp_batch_step(lbmp_batch* b, long n, int* n_finished)
         }
     }
     if (n_finished) *n_finished = finished;
+    return LBMP_OK;
+}
+
+LBMP_API int lbmp_batch_autotune(lbmp_batch* b, int reps, lbmp_tune_entry* table, int max_entries, int* n_entries)
+{
+    if (n_entries) *n_entries = 0;
+    if (!b) return batch_fail(LBMP_ERR_INVALID_ARG, "null batch");
+    if (reps < 1) return batch_fail(LBMP_ERR_INVALID_ARG, "reps must be >= 1");
+    if (max_entries < 0) return batch_fail(LBMP_ERR_INVALID_ARG, "max_entries must be >= 0");
+    const int saved_tile = b->tile, saved_chunk = b->chunk;
+    const int chunks[4] = {8, 16, 32, 64};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    double best = 1e300;
+    int best_tile = saved_tile, best_chunk = saved_chunk, n = 0;
+    for (int t = 0; t < 3 && e == cudaSuccess; ++t)
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+            b->tile = t;
+            b->chunk = chunks[i];
+            e = rebuild(b, false);  // table only; trial launches have no epilogue
+            if (e != cudaSuccess || b->ndom3 + b->ndom2 == 0) break;
+            e = step_kernels(b);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = step_kernels(b);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) break;
+            const double per = (double)ms / reps;
+            if (table && n < max_entries) table[n] = lbmp_tune_entry{chunks[i], 0, per, t};
+            ++n;
+            if (per < best) {
+                best = per;
+                best_tile = t;
+                best_chunk = chunks[i];
+            }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    b->tile = n ? best_tile : saved_tile;
+    b->chunk = n ? best_chunk : saved_chunk;
+    b->dirty = true;  // graphs are rebuilt with the chosen shape at the next step
+    if (e != cudaSuccess) return batch_cuda_fail(e, "batch autotune");
+    if (n_entries) *n_entries = n;
     return LBMP_OK;
 }
 

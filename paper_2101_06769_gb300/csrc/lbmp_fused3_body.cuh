@@ -1,0 +1,394 @@
+// lbmp_fused3_body.cuh -- the fused D3Q27 FP32 step kernel, its batch form
+// and its launcher, for the tile shape of the including unit.
+//
+// The fused single-pass step: phi, its isotropic differences, the cumulant
+// flow collision, the phase-field collision and the streaming of both
+// population sets in one kernel.
+//
+// Work decomposition: a CTA owns an xy tile of TX x TY cells (one thread per
+// cell column) and marches through a chunk of z planes.  For plane z it needs
+// phi on planes z-1, z, z+1 over the tile plus a one-cell ring.  phi = sum_a g_a
+// of the post-streaming g, i.e. of exactly the values the step pulls, so each
+// plane's phi is formed from the populations themselves while they are
+// staged: the tile's own g(z+1) is copied asynchronously (cp.async) into
+// shared memory, summed for phi and kept for the collision of plane z+1; the
+// ring cells' g are loaded and summed by the first threads.  Because the step
+// reads one population set and writes the other, the ring reads cannot race
+// with the neighbouring tile's writes.  No phi field is stored and no
+// separate phi pass runs; the only bytes beyond "every population read once
+// and written once" are ring reads, which the neighbouring tiles fetch at
+// about the same time (mostly L2 hits), and one extra plane per chunk.
+//
+// Addressing: the 27 per-direction array bases of the four population sets
+// are kernel parameters (constant bank); a pulled value is base[a] plus a
+// 32-bit cell index assembled from three per-axis neighbour offsets, so each
+// load costs an add and a wide multiply-add.
+//
+// The per-cell arithmetic (lbmp_common.cuh) and its summation orders are the
+// ones of the reference pair in lbmp_kernels.cu, so the two paths agree.
+//
+// The including unit defines LBMP_FUSED3_LAUNCH (the launcher's name),
+// LBMP_BATCH3_OPS (the name of its batch-kernel table) and, for a tile shape
+// other than the default, LBMP_FUSED_TX / _TY and LBMP_TILE_NS;
+// LBMP_FUSED3_WITH_COMMON adds the pieces shared by every tile shape.
+#pragma once
+
+#include "lbmp_internal.h"
+#include "lbmp_tile.cuh"
+
+namespace lbmp {
+
+namespace {
+
+using namespace LBMP_TILE_NS;
+
+
+struct DirPtrs {
+    const float* fin[Q3];
+    const float* gin[Q3];
+    float* fout[Q3];
+    float* gout[Q3];
+};
+
+// Work items: (tile, chunk of z planes), tile index fastest, so the CTAs
+// running at any moment hold neighbouring tiles of the same z range and the
+// ring reads of one tile are the own reads of another (L2 hits).  A
+// contiguous split of the plane-columns per CTA, which balances better on
+// paper, measured slower for that reason.
+struct FusedArgs {
+    int tiles_x, tiles_y, chunk, nitems;
+};
+
+template <bool Walls>
+struct StageCopy {
+    const DirPtrs& D;
+    const Column& C;
+    const Plane& P;
+    float* gbuf;
+    template <int a>
+    __device__ __forceinline__ void step() const
+    {
+        cp_async4(gbuf + a * NT, pulled<Walls, a>(D.gin, C, P));
+    }
+};
+
+
+template <bool Walls>
+struct FCopy {
+    const DirPtrs& D;
+    const Column& C;
+    const Plane& P;
+    float* fbuf;
+    template <int a>
+    __device__ __forceinline__ void step() const
+    {
+        cp_async4(fbuf + a * NT, pulled<Walls, a>(D.fin, C, P));
+    }
+};
+
+template <bool Walls>
+struct RingCopy {
+    const DirPtrs& D;
+    const Column& C;
+    const Plane& P;
+    float* rbuf;
+    template <int a>
+    __device__ __forceinline__ void step() const
+    {
+        cp_async4(rbuf + a * NRING, pulled<Walls, a>(D.gin, C, P));
+    }
+};
+
+// Staging of plane zz, in two halves so that other loads can be issued while
+// the copies are in flight.  issue: the tile's own g(zz) into gbuf (kept for
+// the collision of plane zz) and the ring cells' g(zz) into rbuf, both by
+// cp.async.  finish: wait, then phi = (hi, lo) of every tile and ring cell
+// into phi_plane.  Each thread sums only the values it copied itself, so no
+// barrier is needed in between.
+__device__ __forceinline__ void stage_issue(const DevParams& p, const DirPtrs& D, const Column& own,
+                                            const Column& ring, int tid, int zz, float* __restrict__ gbuf,
+                                            float* __restrict__ rbuf)
+{
+    Plane P;
+    set_plane(P, p, plane_src(p, zz));
+    if (P.lo || P.hi) {  // uniform across the CTA
+        Unroll<Q3>::run(StageCopy<true>{D, own, P, gbuf + tid});
+        if (tid < NRING) Unroll<Q3>::run(RingCopy<true>{D, ring, P, rbuf + tid});
+    } else {
+        Unroll<Q3>::run(StageCopy<false>{D, own, P, gbuf + tid});
+        if (tid < NRING) Unroll<Q3>::run(RingCopy<false>{D, ring, P, rbuf + tid});
+    }
+    cp_async_commit();
+}
+
+__device__ __forceinline__ void stage_finish(int tid, int oslot, int rslot, const float* __restrict__ gbuf,
+                                             const float* __restrict__ rbuf, float2* __restrict__ phi_plane)
+{
+    cp_async_wait_all();
+    if (tid < NRING) {
+        float hi, lo;
+        phi_sum<3>([&](int a) { return rbuf[a * NRING + tid]; }, hi, lo);
+        phi_plane[rslot] = make_float2(hi, lo);
+    }
+    float hi, lo;
+    phi_sum<3>([&](int a) { return gbuf[a * NT + tid]; }, hi, lo);
+    phi_plane[oslot] = make_float2(hi, lo);
+}
+
+// One segment of work: planes [z0, z1) of the tile at (x0, y0) of the domain
+// described by (p, Dp).  smem holds the g staging buffers, the ring buffer and
+// the three phi planes.  Ends with a barrier, so the caller may reuse shared
+// memory afterwards.
+__device__ __forceinline__ void fused_segment(const DevParams& p, const DirPtrs& Dp, const ThreadGeo& T, float* smem,
+                                              int x0, int y0, int z0, int z1)
+{
+    float* gS = smem;                           // [2][27][NT]
+    float* rS = smem + 2 * Q3 * NT;             // [27][NRING] ring cells' g of the plane being staged
+    float2* phiS = (float2*)(rS + Q3 * NRING);  // (hi, lo) [3][RY][RX]
+    float* fS = (float*)(phiS + 3 * PLANE);     // [27][NT] f' of the plane (LBMP_FUSED_FSMEM)
+    float* dS = fS + LBMP_FUSED_FSMEM * Q3 * NT;  // [27][NT] dh (LBMP_FUSED_DHSMEM)
+    const int tid = T.tid, oslot = T.oslot, rslot = T.rslot;
+    Column own, ring;
+    set_column(own, p, pmod(x0 + T.tx, p.nx), pmod(y0 + T.ty, p.ny));
+    set_column(ring, p, pmod(x0 + T.lx, p.nx), pmod(y0 + T.ly, p.ny));
+    const bool valid = (x0 + T.tx < p.nx) && (y0 + T.ty < p.ny);
+    int sP = 0, sC = 1, sN = 2;
+    stage_issue(p, Dp, own, ring, tid, z0 - 1, gS + Q3 * NT, rS);
+    stage_finish(tid, oslot, rslot, gS + Q3 * NT, rS, phiS + sP * PLANE);
+    stage_issue(p, Dp, own, ring, tid, z0, gS, rS);
+    stage_finish(tid, oslot, rslot, gS, rS, phiS + sC * PLANE);
+    for (int z = z0; z < z1; ++z) {
+        const int cur = (z - z0) & 1;
+        // g(z+1) and the ring copies in flight while f'(z) is loaded
+        stage_issue(p, Dp, own, ring, tid, z + 1, gS + (cur ^ 1) * Q3 * NT, rS);
+        Plane P;
+        set_plane(P, p, z);
+        FlowMoments m;
+#if LBMP_FUSED_FSMEM
+        if (P.lo || P.hi)
+            Unroll<Q3>::run(FCopy<true>{Dp, own, P, fS + tid});
+        else
+            Unroll<Q3>::run(FCopy<false>{Dp, own, P, fS + tid});
+        cp_async_commit();
+        stage_finish(tid, oslot, rslot, gS + (cur ^ 1) * Q3 * NT, rS, phiS + sN * PLANE);
+        {
+            float fr[Q3];
+#pragma unroll
+            for (int a = 0; a < Q3; ++a) fr[a] = fS[a * NT + tid];
+            flow_moments<3>(m, fr);
+        }
+#else
+        float fr[Q3];
+        if (P.lo || P.hi)
+            Unroll<Q3>::run(PullLoad<true>{Dp.fin, own, P, fr});
+        else
+            Unroll<Q3>::run(PullLoad<false>{Dp.fin, own, P, fr});
+        stage_finish(tid, oslot, rslot, gS + (cur ^ 1) * Q3 * NT, rS, phiS + sN * PLANE);
+        flow_moments<3>(m, fr);
+#endif
+        __syncthreads();
+        if (valid) {
+            const float2* pm = phiS + sP * PLANE + oslot;
+            const float2* pc = phiS + sC * PLANE + oslot;
+            const float2* pn = phiS + sN * PLANE + oslot;
+            const float2 centre = pc[0];
+            float grad[3], lap;
+            stencil_from<3>(
+                [&](int a) {
+                    const int cz = Lat<3>::cz(a);
+                    return (cz < 0 ? pm : (cz == 0 ? pc : pn))[Lat<3>::cy(a) * RX + Lat<3>::cx(a)];
+                },
+                centre, grad, lap);
+            CellState s;
+            float dh[27];
+            flow_collide<3>(p, centre.x, grad, lap, m, s, dh);
+            const int self = P.zs[1] + own.ys[1] + own.xs[1];
+#if LBMP_FUSED_DHSMEM
+#pragma unroll
+            for (int a = 0; a < Q3; ++a) dS[a * NT + tid] = dh[a];
+            collide_outputs<3>(p, s, DhStrided{dS + tid, NT}, m, GFromStrided{gS + cur * Q3 * NT + tid, NT},
+                               centre.x, centre.y, PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self});
+#else
+            collide_outputs<3>(p, s, DhArray{dh}, m, GFromStrided{gS + cur * Q3 * NT + tid, NT}, centre.x,
+                               centre.y, PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self});
+#endif
+        }
+        __syncthreads();
+        const int t = sP;
+        sP = sC;
+        sC = sN;
+        sN = t;
+    }
+}
+
+__global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_fused3_kernel(DevParams p, FusedArgs A, DirPtrs Dp)
+{
+    extern __shared__ float smem[];
+    const ThreadGeo T = thread_geo();
+    for (int item = blockIdx.x; item < A.nitems; item += gridDim.x) {
+        const int tile = item % (A.tiles_x * A.tiles_y);
+        const int chunk = item / (A.tiles_x * A.tiles_y);
+        const int z0 = chunk * A.chunk;
+        fused_segment(p, Dp, T, smem, (tile % A.tiles_x) * TX, (tile / A.tiles_x) * TY, z0,
+                      min(z0 + A.chunk, p.nz));
+    }
+}
+
+// Batch form: the work items of every member (same order as above within a
+// member, members concatenated) are split over one persistent grid.  A CTA
+// stages the parameters and the 108 direction bases of its current member in
+// shared memory; members whose steps have run out are skipped.
+__global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_batch3_kernel(const BatchDomain* __restrict__ table,
+                                                                          int ndom, int nitems)
+{
+    extern __shared__ float smem[];
+    __shared__ DevParams sp;
+    __shared__ DirPtrs sd;
+    __shared__ int s_dom, s_tx, s_ty, s_chunk, s_begin, s_active;
+    const ThreadGeo T = thread_geo();
+    int cur = -1;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        __syncthreads();  // every thread has read the previous item's shared values
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = ndom - 1;  // last member with item_begin <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (table[mid].item_begin <= item)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            s_dom = lo;
+        }
+        __syncthreads();
+        const int d = s_dom;
+        if (d != cur) {
+            const BatchDomain& B = table[d];
+            if (threadIdx.x == 0) {
+                sp = B.p;
+                s_tx = B.tiles_x;
+                s_ty = B.tiles_y;
+                s_chunk = B.chunk;
+                s_begin = B.item_begin;
+                s_active = B.steps_left > 0;
+            }
+            const int par = B.parity;
+            for (int k = threadIdx.x; k < 4 * Q3; k += blockDim.x) {
+                const int set = k / Q3, a = k % Q3;
+                const size_t off = (size_t)a * (size_t)B.p.N;
+                if (set == 0) sd.fin[a] = B.f[par] + off;
+                if (set == 1) sd.gin[a] = B.g[par] + off;
+                if (set == 2) sd.fout[a] = B.f[par ^ 1] + off;
+                if (set == 3) sd.gout[a] = B.g[par ^ 1] + off;
+            }
+            cur = d;
+            __syncthreads();
+        }
+        if (!s_active) continue;  // uniform
+        const int local = item - s_begin;
+        const int tiles = s_tx * s_ty;
+        const int tile = local % tiles;
+        const int z0 = (local / tiles) * s_chunk;
+        fused_segment(sp, sd, T, smem, (tile % s_tx) * TX, (tile / s_tx) * TY, z0, min(z0 + s_chunk, sp.nz));
+    }
+}
+
+struct LaunchCfg {
+    int device = -1;
+    int per_sm = 0, sms = 0;
+};
+LaunchCfg g_cfg;
+
+}  // namespace
+
+#if LBMP_FUSED3_WITH_COMMON
+// every FP32 domain; shifted 16-bit storage in 3-D (2-D runs the reference pair)
+bool fused_supported(const lbmp_handle* h) { return h->params.storage == LBMP_FP32 || h->D == 3; }
+
+__global__ void batch_epilogue_kernel(BatchDomain* table, int ndom)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d < ndom && table[d].steps_left > 0) {
+        table[d].parity ^= 1;
+        table[d].steps_left -= 1;
+    }
+}
+
+cudaError_t launch_batch_epilogue(BatchDomain* table, int ndom, cudaStream_t stream)
+{
+    if (ndom <= 0) return cudaSuccess;
+    batch_epilogue_kernel<<<(ndom + 127) / 128, 128, 0, stream>>>(table, ndom);
+    return cudaGetLastError();
+}
+#endif
+
+namespace {
+
+int g_batch_dev = -1, g_batch_cap = 0;
+
+// attributes and occupancy of the batch kernel (not capturable: call before capture)
+cudaError_t prepare_batch(int device)
+{
+    if (g_batch_dev != device) {
+        cudaError_t e = cudaFuncSetAttribute(step_batch3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_batch3_kernel, NT, kSmemBytes);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+        if (e != cudaSuccess) return e;
+        g_batch_cap = (per_sm > 0 ? per_sm : 1) * sms;
+        g_batch_dev = device;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_batch(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream)
+{
+    if (g_batch_dev != device) return cudaErrorNotReady;  // prepare first
+    if (nitems <= 0) return cudaSuccess;
+    const int grid = nitems < g_batch_cap ? nitems : g_batch_cap;
+    step_batch3_kernel<<<grid, NT, kSmemBytes, stream>>>(table, ndom, nitems);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+const Batch3Ops LBMP_BATCH3_OPS = {TX, TY, prepare_batch, launch_batch};
+
+cudaError_t LBMP_FUSED3_LAUNCH(lbmp_handle* h)
+{
+    if (g_cfg.device != h->device) {
+        cudaError_t e = cudaFuncSetAttribute(step_fused3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_fused3_kernel, NT, kSmemBytes);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+        if (e != cudaSuccess) return e;
+        g_cfg.per_sm = per_sm > 0 ? per_sm : 1;
+        g_cfg.sms = sms;
+        g_cfg.device = h->device;
+    }
+    DirPtrs D;
+    const int s = h->parity, d = 1 - h->parity;
+    for (int a = 0; a < Q3; ++a) {
+        const size_t off = (size_t)a * (size_t)h->N;
+        D.fin[a] = h->f[s] + off;
+        D.gin[a] = h->g[s] + off;
+        D.fout[a] = h->f[d] + off;
+        D.gout[a] = h->g[d] + off;
+    }
+    FusedArgs A;
+    A.tiles_x = (h->grid.nx + TX - 1) / TX;
+    A.tiles_y = (h->grid.ny + TY - 1) / TY;
+    const LaunchShape L = launch_shape(h, A.tiles_x * A.tiles_y, h->grid.nz, g_cfg.per_sm, g_cfg.sms);
+    A.chunk = L.chunk;
+    A.nitems = L.nitems;
+    step_fused3_kernel<<<L.grid, NT, kSmemBytes, h->stream>>>(h->dp, A, D);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmp

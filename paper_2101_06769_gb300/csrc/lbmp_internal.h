@@ -26,6 +26,7 @@ struct lbmp_handle {
     int kernel;        // LBMP_OPT_KERNEL: 0 default, 1 reference pair, 2 bulk-copy staging
     int opt_chunk;     // LBMP_OPT_CHUNK: planes (rows) per work item, 0 = automatic
     int opt_ctas;      // LBMP_OPT_CTAS_PER_SM: resident CTAs per SM of the grid, 0 = occupancy maximum
+    int opt_tile;      // LBMP_OPT_TILE: tile shape of the FP32 D3Q27 fused kernel (0 32x4, 1 16x8, 2 8x16)
     int probe[3];
     // observables scratch (partial sums per block) and result slot
     double* red;
@@ -81,7 +82,9 @@ inline size_t set_bytes(const lbmp_handle* h)
 // kernel launchers (return cudaError_t of the launch)
 cudaError_t launch_phi_pass(lbmp_handle* h);
 cudaError_t launch_step_simple(lbmp_handle* h);
-cudaError_t launch_step_fused(lbmp_handle* h);
+cudaError_t launch_step_fused3(lbmp_handle* h);        // FP32 D3Q27, 32 x 4 tiles
+cudaError_t launch_step_fused3_t16x8(lbmp_handle* h);  // FP32 D3Q27, 16 x 8 tiles
+cudaError_t launch_step_fused3_t8x16(lbmp_handle* h);  // FP32 D3Q27, 8 x 16 tiles
 cudaError_t launch_init(lbmp_handle* h, int case_id, const double* args, unsigned long long seed);
 cudaError_t launch_set_state(lbmp_handle* h, const double* dev_f, const double* dev_g);
 cudaError_t launch_get_state(lbmp_handle* h, double* dev_f, double* dev_g);
@@ -90,8 +93,17 @@ cudaError_t launch_get_state(lbmp_handle* h, double* dev_f, double* dev_g);
 cudaError_t launch_observables(lbmp_handle* h, double* dev_out);
 cudaError_t launch_mass(lbmp_handle* h, double* dev_out4);  // writes 4 doubles, [0] = mass
 bool fused_supported(const lbmp_handle* h);
-int batch3_tile_x();
-int batch3_tile_y();
+// batch kernel of one tile shape of the FP32 D3Q27 fused step
+struct Batch3Ops {
+    int tile_x, tile_y;
+    cudaError_t (*prepare)(int device);  // attributes and occupancy (not capturable)
+    cudaError_t (*launch)(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream);
+};
+extern const Batch3Ops batch3_ops_32x4, batch3_ops_16x8, batch3_ops_8x16;
+inline const Batch3Ops& batch3_ops(int tile)
+{
+    return tile == 1 ? batch3_ops_16x8 : (tile == 2 ? batch3_ops_8x16 : batch3_ops_32x4);
+}
 cudaError_t launch_step_fused2(lbmp_handle* h);
 cudaError_t launch_step_fused16(lbmp_handle* h);  // shifted 16-bit storage, D3Q27
 bool bulk_supported(const lbmp_handle* h);         // FP32 D3Q27 with nx % 4 == 0
@@ -101,8 +113,6 @@ cudaError_t launch_step(lbmp_handle* h);
 int batch2_tile_x();
 cudaError_t prepare_batch2(int device);
 cudaError_t launch_batch2(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream);
-cudaError_t prepare_batch3(int device);
-cudaError_t launch_batch3(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream);
 cudaError_t launch_batch_epilogue(BatchDomain* table, int ndom, cudaStream_t stream);
 // record a message for lbmp_last_error() and return code
 int set_error(int code, const char* msg);

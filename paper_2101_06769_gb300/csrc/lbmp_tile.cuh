@@ -4,8 +4,14 @@
 
 #include "lbmp_internal.h"
 
+// The tile shape is fixed per translation unit (LBMP_FUSED_TX / _TY); a unit
+// that builds another shape names its own namespace (LBMP_TILE_NS).
+#ifndef LBMP_TILE_NS
+#define LBMP_TILE_NS tile
+#endif
+
 namespace lbmp {
-namespace tile {
+namespace LBMP_TILE_NS {
 
 // tile shape and CTAs per SM (compile-time; the defaults are the measured best)
 #ifndef LBMP_FUSED_TX
@@ -170,5 +176,5 @@ __device__ __forceinline__ ThreadGeo thread_geo()
     return T;
 }
 
-}  // namespace tile
+}  // namespace LBMP_TILE_NS
 }  // namespace lbmp

@@ -25,14 +25,18 @@ LBMP_API int lbmp_autotune(lbmp_handle* h, int reps, lbmp_tune_entry* table, int
     for (int c = 4; c <= 128; c *= 2)
         if (c <= nmarch) chunks[nc++] = c;
     const int ctas[3] = {0, 1, 2};
-    const int saved_chunk = h->opt_chunk, saved_ctas = h->opt_ctas;
+    // tile shapes exist for the FP32 D3Q27 cp.async kernel only
+    const int ntiles = (h->D == 3 && h->params.storage == LBMP_FP32 && h->kernel == 0) ? 3 : 1;
+    const int saved_chunk = h->opt_chunk, saved_ctas = h->opt_ctas, saved_tile = h->opt_tile;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     double best = 1e300;
-    int best_chunk = saved_chunk, best_ctas = saved_ctas, n = 0;
+    int best_chunk = saved_chunk, best_ctas = saved_ctas, best_tile = ntiles > 1 ? saved_tile : 0, n = 0;
+    for (int t = 0; t < ntiles && e == cudaSuccess; ++t)
     for (int i = 0; i < nc && e == cudaSuccess; ++i)
         for (int j = 0; j < 3 && e == cudaSuccess; ++j) {
+            h->opt_tile = ntiles > 1 ? t : saved_tile;
             h->opt_chunk = chunks[i];
             h->opt_ctas = ctas[j];
             e = lbmp::launch_step(h);  // warm-up
@@ -44,12 +48,13 @@ LBMP_API int lbmp_autotune(lbmp_handle* h, int reps, lbmp_tune_entry* table, int
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
             if (e != cudaSuccess) break;
             const double per = (double)ms / reps;
-            if (table && n < max_entries) table[n] = lbmp_tune_entry{chunks[i], ctas[j], per};
+            if (table && n < max_entries) table[n] = lbmp_tune_entry{chunks[i], ctas[j], per, h->opt_tile};
             ++n;
             if (per < best) {
                 best = per;
                 best_chunk = chunks[i];
                 best_ctas = ctas[j];
+                best_tile = h->opt_tile;
             }
         }
     if (e0) cudaEventDestroy(e0);
@@ -57,12 +62,14 @@ LBMP_API int lbmp_autotune(lbmp_handle* h, int reps, lbmp_tune_entry* table, int
     if (e != cudaSuccess) {
         h->opt_chunk = saved_chunk;
         h->opt_ctas = saved_ctas;
+        h->opt_tile = saved_tile;
         char buf[256];
         snprintf(buf, sizeof buf, "autotune: %s", cudaGetErrorString(e));
         return lbmp::set_error(LBMP_ERR_CUDA, buf);
     }
     h->opt_chunk = best_chunk;
     h->opt_ctas = best_ctas;
+    h->opt_tile = best_tile;
     if (n_entries) *n_entries = n;
     return LBMP_OK;
 }

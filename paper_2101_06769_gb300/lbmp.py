@@ -18,7 +18,7 @@ FP32, FP16_SHIFTED, BF16_SHIFTED = 0, 1, 2
 CASE = {"rt": 0, "drop_static": 1, "flat": 2, "poiseuille": 3, "drop_sheet": 4, "shear_wave": 5,
         "uniform": 6}
 FLAG_WE_LIGHT, FLAG_DYNAMIC_VISC, FLAG_UNIFORM_FORCE = 1, 2, 4
-OPT_KERNEL, OPT_CHUNK, OPT_CTAS_PER_SM, OPT_WAIT_LIMIT_NS, OPT_TEST_STALL = 0, 1, 2, 3, 4
+OPT_KERNEL, OPT_CHUNK, OPT_CTAS_PER_SM, OPT_WAIT_LIMIT_NS, OPT_TEST_STALL, OPT_TILE = 0, 1, 2, 3, 4, 5
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5: "UNSTABLE",
           -6: "UNSUPPORTED"}
 
@@ -27,7 +27,8 @@ EXPORTS = ("lbmp_create", "lbmp_destroy", "lbmp_last_error", "lbmp_get_derived",
            "lbmp_step", "lbmp_sync", "lbmp_observables", "lbmp_get_state", "lbmp_set_state",
            "lbmp_state_bytes", "lbmp_upload", "lbmp_download", "lbmp_set_option", "lbmp_mass_noalloc",
            "lbmp_batch_create", "lbmp_batch_destroy", "lbmp_batch_add", "lbmp_batch_remove",
-           "lbmp_batch_step", "lbmp_batch_members", "lbmp_autotune", "lbmp_device_name")
+           "lbmp_batch_step", "lbmp_batch_members", "lbmp_autotune", "lbmp_device_name",
+           "lbmp_batch_autotune")
 
 
 class Grid(C.Structure):
@@ -57,7 +58,7 @@ class Obs(C.Structure):
 
 
 class TuneEntry(C.Structure):
-    _fields_ = [("chunk", C.c_int), ("ctas_per_sm", C.c_int), ("ms", C.c_double)]
+    _fields_ = [("chunk", C.c_int), ("ctas_per_sm", C.c_int), ("ms", C.c_double), ("tile", C.c_int)]
 
 
 class LbmpError(RuntimeError):
@@ -103,6 +104,7 @@ def load(path=None):
     L.lbmp_batch_members.argtypes = [vp, C.POINTER(vp), C.POINTER(C.c_long), C.c_int]
     L.lbmp_autotune.argtypes = [vp, C.c_int, C.POINTER(TuneEntry), C.c_int, C.POINTER(C.c_int)]
     L.lbmp_device_name.argtypes = [C.c_char_p, C.c_int]
+    L.lbmp_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(TuneEntry), C.c_int, C.POINTER(C.c_int)]
     _lib = L
     return L
 
@@ -179,7 +181,8 @@ class Domain:
         cache=True the choice is stored per (device, lattice, storage, grid,
         boundaries) in a JSON file (LBMP_TUNE_CACHE, default
         ~/.cache/lbmp/tune.json) and reused without trials.  Returns
-        (chunk, ctas_per_sm, trials) with trials a list of (chunk, ctas, ms)."""
+        (chunk, ctas_per_sm, trials) with trials a list of
+        (chunk, ctas, ms, tile); the chosen tile is applied as LBMP_OPT_TILE."""
         from . import tune
         return tune.autotune(self, reps=reps, cache=cache)
 
@@ -276,3 +279,14 @@ class Batch:
         left = (C.c_long * max(1, n))()
         load().lbmp_batch_members(self._h, hs, left, n)
         return [(self._members.get(hs[k]), int(left[k])) for k in range(n)]
+
+    def autotune(self, reps=3):
+        """Pick the batch kernels' tile shape and planes per work item for the
+        current members (lbmp_batch_autotune); returns the best trial
+        (chunk, ms, tile) and the list of trials."""
+        table = (TuneEntry * 64)()
+        n = C.c_int(0)
+        _check(load().lbmp_batch_autotune(self._h, int(reps), table, 64, C.byref(n)))
+        trials = [(table[k].chunk, table[k].ms, table[k].tile) for k in range(min(n.value, 64))]
+        best = min(trials, key=lambda t: t[1]) if trials else None
+        return best, trials

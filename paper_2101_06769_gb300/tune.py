@@ -9,7 +9,7 @@ import ctypes as C
 import json
 import os
 
-from .lbmp import OPT_CHUNK, OPT_CTAS_PER_SM, TuneEntry, _check, load
+from .lbmp import OPT_CHUNK, OPT_CTAS_PER_SM, OPT_TILE, TuneEntry, _check, load
 
 
 def cache_path():
@@ -45,10 +45,11 @@ def write_cache(path, data):
     os.replace(tmp, path)
 
 
-def apply(dom, chunk, ctas):
+def apply(dom, chunk, ctas, tile=0):
     L = load()
     _check(L.lbmp_set_option(dom.handle, OPT_CHUNK, int(chunk)))
     _check(L.lbmp_set_option(dom.handle, OPT_CTAS_PER_SM, int(ctas)))
+    _check(L.lbmp_set_option(dom.handle, OPT_TILE, int(tile)))
 
 
 def autotune(dom, reps=5, cache=True):
@@ -57,17 +58,17 @@ def autotune(dom, reps=5, cache=True):
     if cache:
         hit = read_cache(path).get(key)
         if hit:
-            apply(dom, hit["chunk"], hit["ctas_per_sm"])
+            apply(dom, hit["chunk"], hit["ctas_per_sm"], hit.get("tile", 0))
             return hit["chunk"], hit["ctas_per_sm"], []
-    table = (TuneEntry * 64)()
+    table = (TuneEntry * 256)()
     n = C.c_int(0)
-    _check(load().lbmp_autotune(dom.handle, int(reps), table, 64, C.byref(n)))
-    trials = [(table[k].chunk, table[k].ctas_per_sm, table[k].ms) for k in range(min(n.value, 64))]
+    _check(load().lbmp_autotune(dom.handle, int(reps), table, 256, C.byref(n)))
+    trials = [(table[k].chunk, table[k].ctas_per_sm, table[k].ms, table[k].tile) for k in range(min(n.value, 256))]
     if not trials:
         return 0, 0, []
     best = min(trials, key=lambda t: t[2])
     if cache:
         data = read_cache(path)
-        data[key] = {"chunk": best[0], "ctas_per_sm": best[1], "ms": best[2]}
+        data[key] = {"chunk": best[0], "ctas_per_sm": best[1], "ms": best[2], "tile": best[3]}
         write_cache(path, data)
     return best[0], best[1], trials

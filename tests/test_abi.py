@@ -49,8 +49,10 @@ def test_struct_layout_matches_header():
 #include "lbmp.h"
 #define O(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
 int main(void) {
-  printf("lbmp_grid %zu\nlbmp_params %zu\nlbmp_obs %zu\nlbmp_derived %zu\n", sizeof(lbmp_grid),
-         sizeof(lbmp_params), sizeof(lbmp_obs), sizeof(lbmp_derived));
+  printf("lbmp_grid %zu\nlbmp_params %zu\nlbmp_obs %zu\nlbmp_derived %zu\nlbmp_tune_entry %zu\n",
+         sizeof(lbmp_grid), sizeof(lbmp_params), sizeof(lbmp_obs), sizeof(lbmp_derived),
+         sizeof(lbmp_tune_entry));
+  O(lbmp_tune_entry, ms); O(lbmp_tune_entry, tile);
   O(lbmp_grid, periodic); O(lbmp_params, force_x); O(lbmp_params, storage); O(lbmp_params, flags);
   O(lbmp_obs, tip_bubble); O(lbmp_obs, step); O(lbmp_obs, health); O(lbmp_derived, force_x);
   return 0;
@@ -75,6 +77,9 @@ int main(void) {
     assert int(vals["lbmp_obs.step"]) == lbmp.Obs.step.offset
     assert int(vals["lbmp_obs.health"]) == lbmp.Obs.health.offset
     assert int(vals["lbmp_derived.force_x"]) == lbmp.Derived.force_x.offset
+    assert int(vals["lbmp_tune_entry"]) == C.sizeof(lbmp.TuneEntry)
+    assert int(vals["lbmp_tune_entry.ms"]) == lbmp.TuneEntry.ms.offset
+    assert int(vals["lbmp_tune_entry.tile"]) == lbmp.TuneEntry.tile.offset
 
 
 def test_invalid_arguments_rejected_without_device_work(lib):

@@ -150,3 +150,28 @@ def test_fused_2d_matches_oracle(kernel):
         fg, gg, pg = d.get_state()
         for x, y in ((fg, fo), (gg, go), (pg, po)):
             assert np.abs(x - y).max() / np.abs(y).max() <= 1e-5
+
+
+def test_batch_autotune_keeps_results():
+    """The batch autotuner's trials advance no member, and after tuning the
+    batch steps each member like stepping it alone with the chosen tile shape
+    (the tile builds agree to within rounding; same bar as the tile tests)."""
+    from paper_2101_06769_gb300.lbmp import OPT_TILE
+    b = Batch()
+    doms = [make(m) for m in MEMBERS]
+    for d in doms:
+        b.add(d, 12)
+    before = [d.get_state() for d in doms]
+    best, trials = b.autotune(reps=1)
+    assert best is not None and len(trials) == 12
+    for d, st in zip(doms, before):
+        assert all(np.array_equal(x, y) for x, y in zip(d.get_state(), st))
+    b.step(12)
+    for m, d in zip(MEMBERS, doms):
+        r = make(m)
+        r.set_option(OPT_TILE, best[2])
+        r.step(12)
+        for x, y in zip(d.get_state(), r.get_state()):
+            scale = np.abs(y).max()
+            assert np.abs(x - y).max() <= 5e-6 * (scale if scale > 0 else 1.0)
+    b.close()
