@@ -63,7 +63,7 @@ TRAFFIC = {
     # same workload, step_fused3s_kernel<StoreF16>: 973.99 MB read + 901.00 MB written
     ("rt3d", "fp16"): {"bytes_per_cell": 1874.99e6 / 8388608, "sources": "846e1678ee0eb821"},
 }
-TRAFFIC_SOURCES = ["lbmp_common.cuh", "lbmp_tile.cuh", "lbmp_fused.cu", "lbmp_fused16.cu"]
+TRAFFIC_SOURCES = ["lbmp_common.cuh", "lbmp_tile.cuh", "lbmp_fused3_body.cuh", "lbmp_fused.cu", "lbmp_fused16.cu"]
 
 
 def kernel_source_hash():
@@ -344,8 +344,29 @@ def measure_forms(args, wl, stream, peak, pg):
     out["batched"]["speedup_vs_alone"] = mlups / mlups_alone
     for d in doms:
         d.close()
+    out["serving"] = measure_serving(stream, mlups)
     out["_launches"] = launches
     return out
+
+
+def measure_serving(stream, capacity_mlups, n=64, load=1.2):
+    """The serving loop (continuous batching) on the reduced serving stream:
+    n seeded requests (RT or drop-on-sheet, 2-D 64^2-256^2 or 3-D
+    64^3-128^3, We, Re and density ratio drawn as in the serving workload,
+    200-2000 steps), Poisson arrivals at `load` times the capacity implied by
+    the batched form's measured MLUPS."""
+    from paper_2101_06769_gb300 import serve
+    kw = dict(sides2=(64, 128, 256), sides3=(64, 96, 128), steps_range=(200, 2000))
+    probe = serve.request_stream(n, seed=7, **kw)
+    work = sum(r.cells * r.steps for r in probe) / n
+    rate = load * capacity_mlups * 1e6 / work
+    reqs = serve.request_stream(n, seed=7, rate=rate, **kw)
+    srv = serve.Server(stream=stream.cuda_stream, round_steps=64)
+    res = srv.run(reqs, max_wall=180.0)
+    srv.close()
+    res.update({"offered_load": load, "rate_rps": rate,
+                "stream": "%d requests, seed 7, 2-D 64^2-256^2 / 3-D 64^3-128^3, 200-2000 steps, Poisson" % n})
+    return res
 
 
 def main():
