@@ -345,11 +345,22 @@ def measure_forms(args, wl, stream, peak, pg):
     for d in doms:
         d.close()
     out["serving"] = measure_serving(stream, mlups)
+    # the same stream under a cap on the resident state: FP32 against 16-bit
+    # storage of the D3Q27 requests (224 instead of 432 B/cell: more requests
+    # resident), in a memory-bound regime (0.5 GB: the largest requests fit
+    # only in 16-bit form) and a compute-bound one (2 GB)
+    out["serving_budget"] = {}
+    for gb in (0.5, 2.0):
+        budget = int(gb * (1 << 30))
+        out["serving_budget"]["%gGB" % gb] = {
+            "state_budget_bytes": budget,
+            "fp32": measure_serving(stream, mlups, storage=0, state_budget=budget),
+            "fp16": measure_serving(stream, mlups, storage=1, state_budget=budget)}
     out["_launches"] = launches
     return out
 
 
-def measure_serving(stream, capacity_mlups, n=64, load=1.2):
+def measure_serving(stream, capacity_mlups, n=64, load=1.2, storage=0, state_budget=None):
     """The serving loop (continuous batching) on the reduced serving stream:
     n seeded requests (RT or drop-on-sheet, 2-D 64^2-256^2 or 3-D
     64^3-128^3, We, Re and density ratio drawn as in the serving workload,
@@ -360,11 +371,19 @@ def measure_serving(stream, capacity_mlups, n=64, load=1.2):
     probe = serve.request_stream(n, seed=7, **kw)
     work = sum(r.cells * r.steps for r in probe) / n
     rate = load * capacity_mlups * 1e6 / work
-    reqs = serve.request_stream(n, seed=7, rate=rate, **kw)
-    srv = serve.Server(stream=stream.cuda_stream, round_steps=64)
+    reqs = serve.request_stream(n, seed=7, rate=rate, storage=storage, **kw)
+    srv = serve.Server(stream=stream.cuda_stream, round_steps=64, state_budget=state_budget)
+    peak = [0]
+    admit = srv._admit
+
+    def admit_and_count(r, now):
+        admit(r, now)
+        peak[0] = max(peak[0], len(srv.running))
+
+    srv._admit = admit_and_count
     res = srv.run(reqs, max_wall=180.0)
     srv.close()
-    res.update({"offered_load": load, "rate_rps": rate,
+    res.update({"offered_load": load, "rate_rps": rate, "peak_resident": peak[0],
                 "stream": "%d requests, seed 7, 2-D 64^2-256^2 / 3-D 64^3-128^3, 200-2000 steps, Poisson" % n})
     return res
 

@@ -6,11 +6,13 @@
 // epilogue flips the parities and counts the steps down.  Nothing a step
 // needs comes from the host, so the kernels of a run of steps are captured
 // once in a CUDA graph and the graph is replayed until the membership (or the
-// set of members with steps left) changes.  Within a step the D3Q27 and the
-// D2Q9 batch kernels run on two forked streams (independent members), joined
-// before the epilogue.  The tile shape of the D3Q27 kernel and the planes
-// (rows) per work item are options of the batch, picked by
-// lbmp_batch_autotune.
+// set of members with steps left) changes.  Members are grouped by kind --
+// FP32 D3Q27, FP16 D3Q27, BF16 D3Q27 (shifted storage), FP32 D2Q9 -- each
+// kind a contiguous segment of the table with its own work numbering and its
+// own persistent kernel.  Within a step the D3Q27 kernels run on the batch
+// stream and the D2Q9 kernel on a forked second stream, joined before the
+// epilogue.  The tile shape of the FP32 D3Q27 kernel and the planes (rows)
+// per work item are options of the batch, picked by lbmp_batch_autotune.
 #include <stdio.h>
 #include <string.h>
 
@@ -29,6 +31,17 @@ struct Member {
     long left;
 };
 
+// member kinds, in table order
+enum Kind { kF32x3 = 0, kF16x3 = 1, kBF16x3 = 2, kF32x2 = 3, kKinds = 4 };
+
+int kind_of(const lbmp_handle* h)
+{
+    if (h->D == 2) return h->params.storage == LBMP_FP32 ? kF32x2 : -1;
+    if (h->params.storage == LBMP_FP16_SHIFTED) return kF16x3;
+    if (h->params.storage == LBMP_BF16_SHIFTED) return kBF16x3;
+    return kF32x3;
+}
+
 }  // namespace
 
 struct lbmp_batch {
@@ -40,9 +53,9 @@ struct lbmp_batch {
     int tile, chunk;                 // D3Q27 tile shape (LBMP_OPT_TILE values), planes per item (0 = 16)
     int device;
     std::vector<Member> members;
-    lbmp::BatchDomain* d_table;       // device, kMaxMembers entries: 3-D members, then 2-D members
+    lbmp::BatchDomain* d_table;       // device, kMaxMembers entries, grouped by kind
     std::vector<lbmp::BatchDomain> h_table;
-    int ndom3, nitems3, ndom2, nitems2;
+    int dom0[kKinds], ndom[kKinds], nitems[kKinds];  // table segment and work items per kind
     bool dirty;
     cudaGraphExec_t g_long, g_one;
 };
@@ -58,20 +71,37 @@ void drop_graphs(lbmp_batch* b)
     b->g_long = b->g_one = nullptr;
 }
 
-// the step kernels of one step (no epilogue): D3Q27 members on the batch
-// stream, D2Q9 members on the side stream when both kinds are present
+int total_dom(const lbmp_batch* b)
+{
+    int n = 0;
+    for (int k = 0; k < kKinds; ++k) n += b->ndom[k];
+    return n;
+}
+
+const lbmp::Batch3Ops& ops3_of(const lbmp_batch* b, int kind)
+{
+    if (kind == kF16x3) return lbmp::batch3_ops_f16;
+    if (kind == kBF16x3) return lbmp::batch3_ops_bf16;
+    return lbmp::batch3_ops(b->tile);
+}
+
+// the step kernels of one step (no epilogue): D3Q27 kinds on the batch
+// stream, D2Q9 members on the side stream when both are present
 cudaError_t step_kernels(lbmp_batch* b)
 {
     cudaError_t e = cudaSuccess;
-    const bool fork = b->ndom3 && b->ndom2;
+    const bool any3 = b->ndom[kF32x3] || b->ndom[kF16x3] || b->ndom[kBF16x3];
+    const bool fork = any3 && b->ndom[kF32x2];
     if (fork) {
         e = cudaEventRecord(b->fork, b->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
     }
-    if (e == cudaSuccess && b->ndom3)
-        e = lbmp::batch3_ops(b->tile).launch(b->d_table, b->ndom3, b->nitems3, b->device, b->stream);
-    if (e == cudaSuccess && b->ndom2)
-        e = lbmp::launch_batch2(b->d_table + b->ndom3, b->ndom2, b->nitems2, b->device, fork ? b->side : b->stream);
+    for (int k = kF32x3; k <= kBF16x3 && e == cudaSuccess; ++k)
+        if (b->ndom[k])
+            e = ops3_of(b, k).launch(b->d_table + b->dom0[k], b->ndom[k], b->nitems[k], b->device, b->stream);
+    if (e == cudaSuccess && b->ndom[kF32x2])
+        e = lbmp::launch_batch2(b->d_table + b->dom0[kF32x2], b->ndom[kF32x2], b->nitems[kF32x2], b->device,
+                                fork ? b->side : b->stream);
     if (e == cudaSuccess && fork) {
         e = cudaEventRecord(b->join, b->side);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join, 0);
@@ -86,7 +116,7 @@ cudaError_t capture(lbmp_batch* b, int steps, cudaGraphExec_t* out)
     if (e != cudaSuccess) return e;
     for (int k = 0; k < steps && e == cudaSuccess; ++k) {
         e = step_kernels(b);
-        if (e == cudaSuccess) e = lbmp::launch_batch_epilogue(b->d_table, b->ndom3 + b->ndom2, b->stream);
+        if (e == cudaSuccess) e = lbmp::launch_batch_epilogue(b->d_table, total_dom(b), b->stream);
     }
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e == cudaSuccess) e = e2;
@@ -95,20 +125,20 @@ cudaError_t capture(lbmp_batch* b, int steps, cudaGraphExec_t* out)
     return e;
 }
 
-// Rebuild the device table from the members with steps left (3-D members
-// first, then 2-D, each with its own work numbering), and (graphs) the graphs.
+// Rebuild the device table from the members with steps left (grouped by
+// kind, each kind with its own work numbering), and (graphs) the graphs.
 cudaError_t rebuild(lbmp_batch* b, bool graphs = true)
 {
     drop_graphs(b);
     b->h_table.clear();
-    b->ndom3 = b->nitems3 = b->ndom2 = b->nitems2 = 0;
-    for (int D = 3; D >= 2; --D) {
+    for (int kind = 0; kind < kKinds; ++kind) {
+    b->dom0[kind] = (int)b->h_table.size();
+    const int D = kind == kF32x2 ? 2 : 3;
     int item = 0;
-    const lbmp::Batch3Ops& ops3 = lbmp::batch3_ops(b->tile);
-    const int TX = D == 3 ? ops3.tile_x : lbmp::batch2_tile_x(), TY = D == 3 ? ops3.tile_y : 1;
+    const int TX = D == 3 ? ops3_of(b, kind).tile_x : lbmp::batch2_tile_x(), TY = D == 3 ? ops3_of(b, kind).tile_y : 1;
     const int chunk = b->chunk > 0 ? b->chunk : 16;
     for (const Member& m : b->members) {
-        if (m.left <= 0 || m.h->D != D) continue;
+        if (m.left <= 0 || kind_of(m.h) != kind) continue;
         const lbmp_handle* h = m.h;
         lbmp::BatchDomain d;
         memset(&d, 0, sizeof d);
@@ -129,19 +159,15 @@ cudaError_t rebuild(lbmp_batch* b, bool graphs = true)
         item += d.items;
         b->h_table.push_back(d);
     }
-    if (D == 3) {
-        b->ndom3 = (int)b->h_table.size();
-        b->nitems3 = item;
-    } else {
-        b->ndom2 = (int)b->h_table.size() - b->ndom3;
-        b->nitems2 = item;
+    b->ndom[kind] = (int)b->h_table.size() - b->dom0[kind];
+    b->nitems[kind] = item;
     }
-    }
-    const int ndom = b->ndom3 + b->ndom2;
+    const int ndom = total_dom(b);
     cudaError_t e = cudaSuccess;
     if (ndom > 0) {
-        if (b->ndom3) e = lbmp::batch3_ops(b->tile).prepare(b->device);
-        if (e == cudaSuccess && b->ndom2) e = lbmp::prepare_batch2(b->device);
+        for (int k = kF32x3; k <= kBF16x3 && e == cudaSuccess; ++k)
+            if (b->ndom[k]) e = ops3_of(b, k).prepare(b->device);
+        if (e == cudaSuccess && b->ndom[kF32x2]) e = lbmp::prepare_batch2(b->device);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(b->d_table, b->h_table.data(), sizeof(lbmp::BatchDomain) * ndom,
                                 cudaMemcpyHostToDevice, b->stream);
@@ -179,7 +205,7 @@ LBMP_API int lbmp_batch_create(size_t hbm_budget, void* cuda_stream, lbmp_batch*
     b->tile = 0;
     b->chunk = 0;
     b->d_table = nullptr;
-    b->ndom3 = b->nitems3 = b->ndom2 = b->nitems2 = 0;
+    for (int k = 0; k < kKinds; ++k) b->dom0[k] = b->ndom[k] = b->nitems[k] = 0;
     b->dirty = true;
     b->g_long = b->g_one = nullptr;
     cudaError_t e = cudaGetDevice(&b->device);
@@ -223,8 +249,8 @@ LBMP_API int lbmp_batch_add(lbmp_batch* b, lbmp_handle* h, long steps)
     if (steps <= 0) return batch_fail(LBMP_ERR_INVALID_ARG, "steps must be > 0");
     if (h->device != b->device) return batch_fail(LBMP_ERR_INVALID_ARG, "domain lives on another device");
     if ((int)b->members.size() >= kMaxMembers) return batch_fail(LBMP_ERR_INVALID_ARG, "batch is full");
-    if (h->params.storage != LBMP_FP32)
-        return batch_fail(LBMP_ERR_UNSUPPORTED, "batch members must use FP32 storage");
+    if (kind_of(h) < 0)
+        return batch_fail(LBMP_ERR_UNSUPPORTED, "D2Q9 batch members must use FP32 storage");
     size_t used = 0;
     for (const Member& m : b->members) {
         if (m.h == h) return batch_fail(LBMP_ERR_INVALID_ARG, "domain is already a member");
@@ -264,7 +290,7 @@ LBMP_API int lbmp_batch_step(lbmp_batch* b, long n, int* n_finished)
     cudaError_t e = cudaSuccess;
     if (b->dirty) e = rebuild(b);
     if (e != cudaSuccess) return batch_cuda_fail(e, "batch rebuild");
-    const int ndom = b->ndom3 + b->ndom2;
+    const int ndom = total_dom(b);
     if (ndom == 0 || n == 0) return LBMP_OK;
     // never run more steps than the longest member still needs
     long need = 0;
@@ -278,11 +304,11 @@ LBMP_API int lbmp_batch_step(lbmp_batch* b, long n, int* n_finished)
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return batch_cuda_fail(e, "batch step");
     // write the device bookkeeping back to the member handles (table order:
-    // 3-D members, then 2-D members, each in membership order)
+    // kinds in order, each in membership order)
     int finished = 0, t = 0;
-    for (int D = 3; D >= 2; --D)
+    for (int kind = 0; kind < kKinds; ++kind)
     for (Member& m : b->members) {
-        if (m.left <= 0 || m.h->D != D) continue;
+        if (m.left <= 0 || kind_of(m.h) != kind) continue;
         const lbmp::BatchDomain& d = b->h_table[t++];
         const long done = m.left - d.steps_left;
         m.h->parity = d.parity;
@@ -315,7 +341,7 @@ LBMP_API int lbmp_batch_autotune(lbmp_batch* b, int reps, lbmp_tune_entry* table
             b->tile = t;
             b->chunk = chunks[i];
             e = rebuild(b, false);  // table only; trial launches have no epilogue
-            if (e != cudaSuccess || b->ndom3 + b->ndom2 == 0) break;
+            if (e != cudaSuccess || total_dom(b) == 0) break;
             e = step_kernels(b);  // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
             for (int r = 0; r < reps && e == cudaSuccess; ++r) e = step_kernels(b);

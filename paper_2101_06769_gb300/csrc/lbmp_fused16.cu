@@ -346,6 +346,105 @@ __global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_fused3s_kernel(DevPa
     }
 }
 
+// Batch form (FP16 / BF16 members of a batch): as the FP32 batch kernel, a
+// CTA looks up the member of each work item in the device table and stages
+// its parameters and direction bases in shared memory.
+template <class St>
+__global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_batch3s_kernel(const BatchDomain* __restrict__ table,
+                                                                           int ndom, int nitems)
+{
+    extern __shared__ __align__(16) float smem16[];
+    __shared__ DevParams sp;
+    __shared__ DirPtrs16 sd;
+    __shared__ int s_dom, s_tx, s_ty, s_chunk, s_begin, s_active;
+    const ThreadGeo T = thread_geo();
+    int cur = -1;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        __syncthreads();  // every thread has read the previous item's shared values
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = ndom - 1;  // last member with item_begin <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (table[mid].item_begin <= item)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            s_dom = lo;
+        }
+        __syncthreads();
+        const int d = s_dom;
+        if (d != cur) {
+            const BatchDomain& B = table[d];
+            const int par = B.parity;
+            const size_t N = (size_t)B.p.N;
+            if (threadIdx.x == 0) {
+                sp = B.p;
+                s_tx = B.tiles_x;
+                s_ty = B.tiles_y;
+                s_chunk = B.chunk;
+                s_begin = B.item_begin;
+                s_active = B.steps_left > 0;
+                sd.rfin = B.f[par];
+                sd.rgin = B.g[par];
+                sd.rfout = B.f[par ^ 1];
+                sd.rgout = B.g[par ^ 1];
+            }
+            for (int k = threadIdx.x; k < 4 * Q3; k += blockDim.x) {
+                const int set = k / Q3, a = k % Q3;
+                const size_t off = (size_t)(a - (a > C3)) * N;
+                unsigned short* base = (unsigned short*)((set == 0 || set == 2 ? B.f : B.g)[set < 2 ? par : par ^ 1] + N);
+                unsigned short* q = a != C3 ? base + off : nullptr;
+                if (set == 0) sd.fin[a] = q;
+                if (set == 1) sd.gin[a] = q;
+                if (set == 2) sd.fout[a] = q;
+                if (set == 3) sd.gout[a] = q;
+            }
+            cur = d;
+            __syncthreads();
+        }
+        if (!s_active) continue;  // uniform
+        const int local = item - s_begin;
+        const int tiles = s_tx * s_ty;
+        const int tile = local % tiles;
+        const int z0 = (local / tiles) * s_chunk;
+        fused_segment16<St>(sp, sd, T, smem16, (tile % s_tx) * TX, (tile / s_tx) * TY, z0, min(z0 + s_chunk, sp.nz));
+    }
+}
+
+template <class St>
+struct BatchCfg16 {
+    static int dev, cap;
+    static cudaError_t prepare(int device)
+    {
+        if (dev != device) {
+            cudaError_t e = cudaFuncSetAttribute(step_batch3s_kernel<St>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kSmem16);
+            if (e != cudaSuccess) return e;
+            int per_sm = 0, sms = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_batch3s_kernel<St>, NT, kSmem16);
+            if (e != cudaSuccess) return e;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+            if (e != cudaSuccess) return e;
+            cap = (per_sm > 0 ? per_sm : 1) * sms;
+            dev = device;
+        }
+        return cudaSuccess;
+    }
+    static cudaError_t launch(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream)
+    {
+        if (dev != device) return cudaErrorNotReady;  // prepare first
+        if (nitems <= 0) return cudaSuccess;
+        const int grid = nitems < cap ? nitems : cap;
+        step_batch3s_kernel<St><<<grid, NT, kSmem16, stream>>>(table, ndom, nitems);
+        return cudaGetLastError();
+    }
+};
+template <class St>
+int BatchCfg16<St>::dev = -1;
+template <class St>
+int BatchCfg16<St>::cap = 0;
+
 struct Cfg16 {
     int device = -1;
     int per_sm = 0, sms = 0;
@@ -399,6 +498,9 @@ cudaError_t launch16(lbmp_handle* h, Cfg16& cfg)
 Cfg16 g_cfg_f16, g_cfg_bf16;
 
 }  // namespace
+
+const Batch3Ops batch3_ops_f16 = {TX, TY, BatchCfg16<StoreF16>::prepare, BatchCfg16<StoreF16>::launch};
+const Batch3Ops batch3_ops_bf16 = {TX, TY, BatchCfg16<StoreBF16>::prepare, BatchCfg16<StoreBF16>::launch};
 
 cudaError_t launch_step_fused16(lbmp_handle* h)
 {

@@ -100,6 +100,7 @@ struct Batch3Ops {
     cudaError_t (*launch)(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream);
 };
 extern const Batch3Ops batch3_ops_32x4, batch3_ops_16x8, batch3_ops_8x16;
+extern const Batch3Ops batch3_ops_f16, batch3_ops_bf16;  // shifted 16-bit members (32 x 4 tiles)
 inline const Batch3Ops& batch3_ops(int tile)
 {
     return tile == 1 ? batch3_ops_16x8 : (tile == 2 ? batch3_ops_8x16 : batch3_ops_32x4);

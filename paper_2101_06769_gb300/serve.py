@@ -34,6 +34,7 @@ class Request:
     args: list
     steps: int
     seed: int
+    storage: int = 0              # lbmp_storage of the domain (16-bit forms for D3Q27 only)
     arrival: float = 0.0          # seconds after the start of the run
     admitted: float = float("nan")
     done: float = float("nan")
@@ -46,16 +47,19 @@ class Request:
 
     def state_bytes(self):
         q = 27 if self.D == 3 else 9
-        return 4 * 4 * q * self.cells  # two population sets, two families, FP32
+        if self.storage == 0:
+            return 4 * 4 * q * self.cells  # two population sets, two families, FP32
+        return 4 * (4 + 2 * (q - 1)) * self.cells  # FP32 reference + 16-bit codes per set
 
     def latency(self):
         return self.done - self.arrival
 
 
-def make_request(rid, rng, D, side, kind, steps, We, Re, rho_ratio):
+def make_request(rid, rng, D, side, kind, steps, We, Re, rho_ratio, storage=0):
     """A request of the serving stream: the drop-on-sheet or RT set-up of the
     paper at a given size and non-dimensional parameter set (lattice units:
-    U0 = 0.05 for the drop, sqrt(g L) = 0.04 for RT, W = 4, M = 0.02)."""
+    U0 = 0.05 for the drop, sqrt(g L) = 0.04 for RT, W = 4, M = 0.02).
+    storage applies to D3Q27 requests (D2Q9 requests stay FP32)."""
     if D == 3:
         dims = (side, side, side)
     else:
@@ -75,12 +79,14 @@ def make_request(rid, rng, D, side, kind, steps, We, Re, rho_ratio):
         phys = dict(rho_ratio=rho_ratio, nu_ratio=15.0, We=We, Re=Re, U0=0.05, L_ref=Dd, mobility=0.02,
                     width=4.0)
         args = [Dd, 0.2 * Dd, 0.05, 1e-4]
+    st = storage if D == 3 else 0
+    phys["storage"] = st
     return Request(rid=rid, kind=kind, D=D, dims=dims, periodic=periodic, phys=phys, args=args, steps=int(steps),
-                   seed=int(rng.integers(1, 2 ** 31)))
+                   seed=int(rng.integers(1, 2 ** 31)), storage=st)
 
 
 def request_stream(n, seed=7, sides2=(64, 128, 256, 512), sides3=(64, 96, 128, 192, 256),
-                   steps_range=(2000, 20000), rate=None):
+                   steps_range=(2000, 20000), rate=None, storage=0):
     """Seeded stream of n requests: type RT or drop-on-sheet (p = 1/2), 2-D or
     3-D (p = 1/2) with the side drawn uniformly from sides2 / sides3, We
     log-uniform in [10, 8000], Re uniform in [100, 1000], density ratio
@@ -97,7 +103,7 @@ def request_stream(n, seed=7, sides2=(64, 128, 256, 512), sides3=(64, 96, 128, 1
         Re = float(rng.uniform(100.0, 1000.0))
         rr = float(math.exp(rng.uniform(math.log(3.0), math.log(1000.0))))
         steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
-        r = make_request(k, rng, D, side, kind, steps, We, Re, rr)
+        r = make_request(k, rng, D, side, kind, steps, We, Re, rr, storage=storage)
         if rate:
             t += float(rng.exponential(1.0 / rate))
         r.arrival = t
@@ -106,12 +112,14 @@ def request_stream(n, seed=7, sides2=(64, 128, 256, 512), sides3=(64, 96, 128, 1
 
 
 class Server:
-    """Admission by free HBM, one batch, rounds of `round_steps` steps."""
+    """Admission by free HBM (and an optional cap on the summed state of the
+    running requests, state_budget), one batch, rounds of `round_steps` steps."""
 
     def __init__(self, stream=None, hbm_reserve=2 << 30, round_steps=64, free_hbm=None, domain_factory=None,
-                 batch=None):
+                 batch=None, state_budget=None):
         self.stream = stream
         self.reserve = hbm_reserve
+        self.state_budget = state_budget
         self.round_steps = round_steps
         self._free_hbm = free_hbm  # callable -> free bytes (None: torch.cuda.mem_get_info)
         self._domain = domain_factory or Domain
@@ -161,7 +169,9 @@ class Server:
             # continuous admission: every arrived request that fits
             while k < len(pending) and pending[k].arrival <= now:
                 r = pending[k]
-                if r.state_bytes() + self.reserve > self.free_hbm():
+                over = (self.state_budget is not None and
+                        self.resident_bytes() + r.state_bytes() > self.state_budget)
+                if over or r.state_bytes() + self.reserve > self.free_hbm():
                     if self.running:
                         break  # wait for memory to be freed
                     r.status = "failed"  # does not fit even on an idle device
@@ -193,6 +203,9 @@ class Server:
                 "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                 "wall_s": wall, "mlups": cell_updates / wall / 1e6 if wall > 0 else 0.0,
                 "cell_updates": cell_updates}
+
+    def resident_bytes(self):
+        return sum(r.state_bytes() for r, _ in self.running.values())
 
     def _rid(self, dom):
         for rid, (r, d) in self.running.items():

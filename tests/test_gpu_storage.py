@@ -171,12 +171,32 @@ def test_rt_tips_follow_fp32():
     assert np.abs(tips[BF16_SHIFTED] - tips[FP32]).max() <= 0.5
 
 
-def test_batch_rejects_shifted_members():
+def test_batch_with_shifted_members_is_bitwise_stepping_alone():
+    """FP16 and BF16 D3Q27 members run in a batch beside FP32 members (each
+    kind its own persistent kernel); every member's state equals stepping it
+    alone.  A 16-bit D2Q9 member is refused."""
     from paper_2101_06769_gb300 import Batch
-    c = EVEN["rt3d"]
+    cases = [("rt3d", FP16_SHIFTED, 23), ("splash3d", BF16_SHIFTED, 17), ("ragged3d_walls", FP16_SHIFTED, 30),
+             ("rt3d", FP32, 19), ("rt2d", FP32, 21)]
+    alone, doms = [], []
     b = Batch()
-    d = domain(c, FP16_SHIFTED)
-    d.init(c["case"], c["args"], seed=1)
+    for name, st, n in cases:
+        c = EVEN[name]
+        r = domain(c, st)
+        r.init(c["case"], c["args"], seed=c["seed"])
+        r.step(n)
+        alone.append(r.get_state())
+        d = domain(c, st)
+        d.init(c["case"], c["args"], seed=c["seed"])
+        b.add(d, n)
+        doms.append(d)
+    while b.step(16) >= 0 and any(left for _, left in b.members()):
+        pass
+    for d, want in zip(doms, alone):
+        assert all(np.array_equal(x, y) for x, y in zip(d.get_state(), want))
+    c = EVEN["rt2d"]
+    d2 = domain(c, FP16_SHIFTED)
+    d2.init(c["case"], c["args"], seed=1)
     with pytest.raises(LbmpError):
-        b.add(d, 10)
+        b.add(d2, 10)
     b.close()

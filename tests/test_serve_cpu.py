@@ -131,3 +131,35 @@ def test_stream_distribution():
     assert all(2000 <= r.steps <= 20000 for r in reqs)
     ratios = [r.phys["rho_ratio"] for r in reqs]
     assert 3.0 <= min(ratios) and max(ratios) <= 1000.0
+
+
+def test_state_budget_limits_residency_and_16bit_doubles_it():
+    """With a cap on the summed state of running requests, 16-bit storage
+    (224 instead of 432 bytes per D3Q27 cell) lets more requests run at once
+    (up to 1.93x; discrete request sizes pack less tightly); every request is
+    still served."""
+    conc = {}
+    for storage in (0, 1):
+        reqs = [r for r in serve.request_stream(24, seed=5, sides2=(32,), sides3=(16, 24), steps_range=(50, 300),
+                                                storage=storage) if r.D == 3]
+        cap = 3 * max(serve.request_stream(24, seed=5, sides2=(32,), sides3=(16, 24),
+                                           steps_range=(50, 300))[k].state_bytes() for k in range(24))
+        batch = FakeBatch()
+        srv = serve.Server(hbm_reserve=0, round_steps=32, domain_factory=FakeDomain, batch=batch,
+                           free_hbm=lambda: 1 << 40, state_budget=cap)
+        out = srv.run(reqs, clock=FakeClock())
+        assert out["done"] == len(reqs) and out["failed"] == 0
+        conc[storage] = batch.max_concurrent
+    assert conc[1] >= 1.5 * conc[0]
+
+
+def test_request_state_bytes_by_storage():
+    reqs = serve.request_stream(16, seed=2, sides2=(32,), sides3=(16,), steps_range=(50, 60), storage=1)
+    for r in reqs:
+        q = 27 if r.D == 3 else 9
+        if r.D == 3:
+            assert r.storage == 1 and r.phys["storage"] == 1
+            assert r.state_bytes() == 4 * (4 + 2 * 26) * r.cells
+        else:
+            assert r.storage == 0 and r.phys["storage"] == 0
+            assert r.state_bytes() == 16 * q * r.cells
