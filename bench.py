@@ -39,6 +39,13 @@ WORKLOADS = {
         phys=dict(rho_ratio=1000.0, nu_ratio=15.0, We=8000.0, Re=1000.0, U0=0.05, L_ref=64.0,
                   mobility=0.02, width=4.0),
         case="drop_sheet", args=[64.0, 12.8, 0.05, 1e-4], seed=3),
+    "splash3d_large": dict(
+        desc="3-D droplet impact on a thin sheet, D3Q27, 768x768x384 (226M cells), D 128, sheet 0.1D, U0 0.05, "
+             "rho ratio 1000, nu ratio 15, We 8000, Re 1000, W 4, M 0.02",
+        D=3, dims=(768, 768, 384), periodic=(1, 1, 0),
+        phys=dict(rho_ratio=1000.0, nu_ratio=15.0, We=8000.0, Re=1000.0, U0=0.05, L_ref=128.0,
+                  mobility=0.02, width=4.0),
+        case="drop_sheet", args=[128.0, 12.8, 0.05, 1e-4], seed=5),
     "rt2d": dict(
         desc="2-D Rayleigh-Taylor, D2Q9, 64x256, periodic x, walls y, At 0.5, sqrt(gL)=0.04, Re 256, W 5, M 0.02",
         D=2, dims=(64, 256, 1), periodic=(1, 0, 1),
@@ -388,6 +395,73 @@ def measure_serving(stream, capacity_mlups, n=64, load=1.2, storage=0, state_bud
     return res
 
 
+def oracle_rates(wl, budget_s=8.0):
+    """The FP64 oracle on 1 thread and on all host cores, each on a bounded
+    slab of the workload (full x, y extent) for about budget_s seconds."""
+    import oracle as O
+    cores = O.get_threads()
+    out = {}
+    for nt in (1, cores):
+        O.set_threads(nt)
+        depth = min(wl["dims"][2], 4 if nt == 1 else 16) if wl["D"] == 3 else 1
+        if wl["D"] == 3 and wl["dims"][0] * wl["dims"][1] > 400000:
+            depth = 2
+        rate, dims, dt = _oracle_rate(wl, depth, 1)
+        steps = max(1, int(budget_s * rate * 1e6 / (dims[0] * dims[1] * dims[2])))
+        rate, dims, dt = _oracle_rate(wl, depth, steps)
+        out["threads_%d" % nt] = {"mlups": rate, "sample": "%dx%dx%d, %d steps, %.1f s" % (dims + (steps, dt))}
+    O.set_threads(cores)
+    out["cores"] = cores
+    return out
+
+
+def run_configs(args):
+    """One JSON line per workload configuration of the benchmark set: MLUPS,
+    algorithmic GB/s and roofline fraction per storage form, with the FP64
+    oracle timed on 1 and on all host cores beside it."""
+    import torch
+    from paper_2101_06769_gb300 import Domain
+    peak, _ = load_peaks()
+    stream = torch.cuda.Stream()
+    plan = [("rt2d", ["fp32"], 2000), ("rt3d", ["fp32", "fp16", "bf16"], 200),
+            ("splash3d", ["fp32", "fp16", "bf16"], 100), ("splash3d_large", ["fp16", "fp32"], 30)]
+    for name, forms, steps in plan:
+        wl = WORKLOADS[name]
+        D = wl["D"]
+        line = {"config": name, "desc": wl["desc"], "grid": list(wl["dims"]), "forms": {}}
+        for st in forms:
+            d = Domain(D, wl["dims"], wl["periodic"], stream=stream.cuda_stream, storage=STORAGE[st], **wl["phys"])
+            d.init(wl["case"], wl["args"], seed=wl["seed"])
+            d.autotune(reps=2, cache=False)
+            d.step(3)
+            ms = time_steps(lambda: d.step(1), stream, steps)
+            bpc = BYTES_PER_CELL[D] if st == "fp32" else BYTES_PER_CELL_16[D]
+            gbs = bpc * d.N / (ms * 1e-3) / 1e9
+            ob = d.observables()
+            line["forms"][st] = {"mlups": d.N / (ms * 1e-3) / 1e6, "ms_per_step": ms, "bytes_per_cell": bpc,
+                                 "achieved_gbs": gbs, "frac": gbs / peak, "state_gb": 2 * d.state_bytes() / 1e9,
+                                 "mass_drift_rel": ob.mass_drift_rel, "kinetic_energy": ob.kinetic_energy,
+                                 "max_u": ob.max_u, "steps": steps + 3}
+            d.close()
+        if not args.no_cpu_baseline:
+            line["oracle"] = oracle_rates(wl)
+        print(json.dumps(line), flush=True)
+    if args.serving_requests:
+        from paper_2101_06769_gb300 import serve
+        reqs = serve.request_stream(args.serving_requests, seed=7)
+        work = sum(r.cells * r.steps for r in reqs) / len(reqs)
+        cap = 8.5e9  # cell updates per second of the batched form (measured)
+        rate = 1.2 * cap / work
+        reqs = serve.request_stream(args.serving_requests, seed=7, rate=rate)
+        srv = serve.Server(stream=stream.cuda_stream, round_steps=256)
+        res = srv.run(reqs)
+        srv.close()
+        res.update({"config": "serving", "offered_load": 1.2, "rate_rps": rate,
+                    "stream": "%d requests, seed 7, full serving ranges" % args.serving_requests})
+        print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,6 +478,10 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16/batched form measurements")
     ap.add_argument("--form-steps", type=int, default=50)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--configs", action="store_true",
+                    help="measure every workload configuration (one JSON line each) instead of the bench line")
+    ap.add_argument("--serving-requests", type=int, default=0,
+                    help="with --configs: also serve this many requests of the full serving stream")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.grid:
@@ -414,6 +492,8 @@ def main():
         wl["desc"] = wl["desc"] + f" (grid overridden to {dims[0]}x{dims[1]}x{dims[2]})"
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.configs:
+        return run_configs(args)
 
     import torch
     ws, rank, local = dist_env()
