@@ -24,34 +24,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOADS = {
-    "rt3d": dict(
-        desc="3-D Rayleigh-Taylor, D3Q27 cumulant flow + D3Q27 phase field, 128x128x512, periodic x,y, "
-             "walls z, At 0.5, sqrt(gL)=0.04, Re 1024, W 5, M 0.02",
-        D=3, dims=(128, 128, 512), periodic=(1, 1, 0),
-        phys=dict(atwood=0.5, nu_ratio=1.0, Re=1024.0, g_accel=1.25e-5, L_ref=128.0, mobility=0.02,
-                  width=5.0),
-        case="rt", args=[256.0, 12.8, 1e-4, 1.0], seed=1),
-    "splash3d": dict(
-        desc="3-D droplet impact on a thin sheet, D3Q27, 384x384x192, D 64, sheet 0.2D, U0 0.05, "
-             "rho ratio 1000, nu ratio 15, We 8000, Re 1000, W 4, M 0.02",
-        D=3, dims=(384, 384, 192), periodic=(1, 1, 0),
-        phys=dict(rho_ratio=1000.0, nu_ratio=15.0, We=8000.0, Re=1000.0, U0=0.05, L_ref=64.0,
-                  mobility=0.02, width=4.0),
-        case="drop_sheet", args=[64.0, 12.8, 0.05, 1e-4], seed=3),
-    "splash3d_large": dict(
-        desc="3-D droplet impact on a thin sheet, D3Q27, 768x768x384 (226M cells), D 128, sheet 0.1D, U0 0.05, "
-             "rho ratio 1000, nu ratio 15, We 8000, Re 1000, W 4, M 0.02",
-        D=3, dims=(768, 768, 384), periodic=(1, 1, 0),
-        phys=dict(rho_ratio=1000.0, nu_ratio=15.0, We=8000.0, Re=1000.0, U0=0.05, L_ref=128.0,
-                  mobility=0.02, width=4.0),
-        case="drop_sheet", args=[128.0, 12.8, 0.05, 1e-4], seed=5),
-    "rt2d": dict(
-        desc="2-D Rayleigh-Taylor, D2Q9, 64x256, periodic x, walls y, At 0.5, sqrt(gL)=0.04, Re 256, W 5, M 0.02",
-        D=2, dims=(64, 256, 1), periodic=(1, 0, 1),
-        phys=dict(atwood=0.5, nu_ratio=1.0, Re=256.0, g_accel=2.5e-5, L_ref=64.0, mobility=0.02, width=5.0),
-        case="rt", args=[128.0, 6.4, 1e-4, 1.0], seed=1),
-}
+def _workloads():
+    """the benchmark workloads: the shipped JSON case files of the package"""
+    from paper_2101_06769_gb300 import cases
+    return {name: cases.as_workload(cases.load(name)) for name in cases.shipped()}
+
+
+WORKLOADS = _workloads()
 
 # algorithmic bytes per cell update: every population read once and written
 # once (phi is formed on chip and never stored by the fused kernels)

@@ -122,8 +122,9 @@ typedef struct {
  *   at the origin, laplace_dp = p_in - p_out (Sec. 3.1);
  *   tip_spike = lowest phi = 1/2 crossing on the vertical column through
  *   (nx/2, ny/2), tip_bubble = highest crossing on the column through the
- *   origin (Sec. 3.2/3.3; -1 when there is none); health != 0 when a
- *   non-finite value was met. */
+ *   origin (Sec. 3.2/3.3; -1 when there is none); health: bit 0 set when a
+ *   non-finite value was met, bit 1 when max_u exceeds 0.35 (far beyond the
+ *   low-Mach range the scheme is valid in; such a run is unstable). */
 typedef struct {
     double mass, mass_drift_rel, kinetic_energy, max_u, p_in, p_out, laplace_dp;
     double tip_spike, tip_bubble;
@@ -197,6 +198,9 @@ enum {
                                    0 = 32 x 4 (default), 1 = 16 x 8, 2 = 8 x 16 */
     LBMP_OPT_WAIT_LIMIT_NS = 3, /* bound of every wait inside a step kernel, in ns
                                    (default 2e9; range [1e3, 6e10]) */
+    LBMP_OPT_TEST_POISON = 6,   /* test only: 1 fills the population set the next
+                                   step writes with NaN (the step must overwrite
+                                   every slot; a missed slot shows in the state) */
     LBMP_OPT_TEST_STALL = 4     /* test only: 1 arms each staging barrier of the
                                    bulk-copy kernel for 16 bytes more than its copies
                                    deliver, so that its waits run out and the next

@@ -121,6 +121,9 @@ void free_handle(lbmp_handle* h)
     delete h;
 }
 
+// observables: a speed above this marks the run unstable (health bit 1)
+constexpr double kMaxSpeed = 0.35;
+
 // slot of red_out (a double) that holds the device status word (an int);
 // slots 0-5 take the observables, 12-15 the reference mass, 16- the columns
 constexpr int kStatusSlot = 8;
@@ -275,6 +278,13 @@ int lbmp_set_option(lbmp_handle* h, int option, long value)
         if (value < 1000 || value > 60000000000L) return fail(LBMP_ERR_INVALID_ARG, "wait limit must lie in [1 us, 60 s]");
         h->dp.wait_ns = (unsigned long long)value;
         return LBMP_OK;
+    case LBMP_OPT_TEST_POISON: {
+        if (value != 1) return fail(LBMP_ERR_INVALID_ARG, "test poison must be 1");
+        const int d = 1 - h->parity;
+        LBMP_CUDA(cudaMemsetAsync(h->f[d], 0xFF, lbmp::set_bytes(h), h->stream), "poison");
+        LBMP_CUDA(cudaMemsetAsync(h->g[d], 0xFF, lbmp::set_bytes(h), h->stream), "poison");
+        return LBMP_OK;
+    }
     case LBMP_OPT_TEST_STALL:
         if (value < 0 || value > 1) return fail(LBMP_ERR_INVALID_ARG, "test stall must be 0 or 1");
         h->dp.test_extra_tx = value ? 16u : 0u;
@@ -356,7 +366,7 @@ int lbmp_observables(lbmp_handle* h, lbmp_obs* out)
     out->mass = host[0];
     out->kinetic_energy = host[1];
     out->max_u = host[2];
-    out->health = host[3] != 0.0 ? 1 : 0;
+    out->health = (host[3] != 0.0 ? 1 : 0) | (!(out->max_u <= kMaxSpeed) ? 2 : 0);
     out->p_in = host[4];
     out->p_out = host[5];
     out->laplace_dp = out->p_in - out->p_out;
@@ -383,7 +393,9 @@ int lbmp_observables(lbmp_handle* h, lbmp_obs* out)
     delete[] host;
     rc = status_of(word);
     if (rc != LBMP_OK) return rc;
-    return out->health ? fail(LBMP_ERR_UNSTABLE, "non-finite values in the state") : LBMP_OK;
+    if (out->health & 1) return fail(LBMP_ERR_UNSTABLE, "non-finite values in the state");
+    if (out->health & 2) return fail(LBMP_ERR_UNSTABLE, "speed above 0.35: the run is unstable");
+    return LBMP_OK;
 }
 
 int lbmp_get_state(lbmp_handle* h, double* f, double* g, double* phi)

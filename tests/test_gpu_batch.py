@@ -175,3 +175,22 @@ def test_batch_autotune_keeps_results():
             scale = np.abs(y).max()
             assert np.abs(x - y).max() <= 5e-6 * (scale if scale > 0 else 1.0)
     b.close()
+
+
+def test_batch_writes_every_slot():
+    """Every member's target set is poisoned with NaN before each batch step;
+    no NaN survives."""
+    from paper_2101_06769_gb300.lbmp import OPT_TEST_POISON
+    b = Batch()
+    doms = [make(m) for m in MEMBERS]
+    for d in doms:
+        b.add(d, 3)
+    for _ in range(3):
+        for d in doms:
+            d.set_option(OPT_TEST_POISON, 1)
+            d.sync()  # the poison runs on the member's stream, the batch on its own
+        b.step(1)
+    for d in doms:
+        f, g, phi = d.get_state()
+        assert np.isfinite(f).all() and np.isfinite(g).all() and np.isfinite(phi).all()
+    b.close()

@@ -200,3 +200,20 @@ def test_batch_with_shifted_members_is_bitwise_stepping_alone():
     with pytest.raises(LbmpError):
         b.add(d2, 10)
     b.close()
+
+
+@pytest.mark.parametrize("st", sorted(STORAGES))
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("name", ["ragged3d_walls", "ragged3d_even", "rt2d"])
+def test_every_slot_written_shifted(name, kernel, st):
+    """As for FP32: a NaN-poisoned target set holds no NaN after a step."""
+    from paper_2101_06769_gb300.lbmp import OPT_TEST_POISON
+    c = EVEN[name]
+    d = domain(c, STORAGES[st])
+    d.init(c["case"], c["args"], seed=c["seed"])
+    d.set_kernel(kernel)
+    for _ in range(3):
+        d.set_option(OPT_TEST_POISON, 1)
+        d.step(1)
+        f, g, phi = d.get_state()
+        assert np.isfinite(f).all() and np.isfinite(g).all() and np.isfinite(phi).all()
