@@ -188,23 +188,28 @@ LBMP_API int lbmp_download(lbmp_handle *h, void *host, size_t bytes);
  *   LBMP_OPT_CTAS_PER_SM: resident CTAs per SM of the fused kernels'
  *     persistent grid, 0 = the occupancy maximum (the default), else >= 1
  *     (values above the maximum act as the maximum).
- * Launch-shape options change speed only, never results.  Returns
- * LBMP_ERR_INVALID_ARG for an unknown option or an out-of-range value. */
+ *   LBMP_OPT_WAIT_LIMIT_NS: bound of every wait inside a step kernel, in ns
+ *     (default 2e9; range [1e3, 6e10]).
+ *   LBMP_OPT_TEST_STALL (test only): 1 arms each staging barrier of the
+ *     bulk-copy kernel for 16 bytes more than its copies deliver, so that its
+ *     waits run out and the next lbmp_sync reports LBMP_ERR_TIMEOUT; 0 off.
+ *   LBMP_OPT_TILE: tile shape of the FP32 D3Q27 fused kernel: 0 = 32 x 4
+ *     (default), 1 = 16 x 8, 2 = 8 x 16.
+ *   LBMP_OPT_TEST_POISON (test only): 1 fills the population set the next
+ *     step writes with NaN (the step must overwrite every slot; a missed
+ *     slot shows in the state).
+ * CHUNK and CTAS_PER_SM change speed only, never results; each TILE value
+ * is a separately compiled build of the same kernel and agrees with the
+ * default to within rounding.  Returns LBMP_ERR_INVALID_ARG for an unknown
+ * option or an out-of-range value. */
 enum {
     LBMP_OPT_KERNEL = 0,
     LBMP_OPT_CHUNK = 1,
     LBMP_OPT_CTAS_PER_SM = 2,
-    LBMP_OPT_TILE = 5,          /* tile shape of the FP32 D3Q27 fused kernel:
-                                   0 = 32 x 4 (default), 1 = 16 x 8, 2 = 8 x 16 */
-    LBMP_OPT_WAIT_LIMIT_NS = 3, /* bound of every wait inside a step kernel, in ns
-                                   (default 2e9; range [1e3, 6e10]) */
-    LBMP_OPT_TEST_POISON = 6,   /* test only: 1 fills the population set the next
-                                   step writes with NaN (the step must overwrite
-                                   every slot; a missed slot shows in the state) */
-    LBMP_OPT_TEST_STALL = 4     /* test only: 1 arms each staging barrier of the
-                                   bulk-copy kernel for 16 bytes more than its copies
-                                   deliver, so that its waits run out and the next
-                                   lbmp_sync reports LBMP_ERR_TIMEOUT; 0 (default) off */
+    LBMP_OPT_WAIT_LIMIT_NS = 3,
+    LBMP_OPT_TEST_STALL = 4,
+    LBMP_OPT_TILE = 5,
+    LBMP_OPT_TEST_POISON = 6
 };
 LBMP_API int lbmp_set_option(lbmp_handle *h, int option, long value);
 
@@ -214,9 +219,9 @@ LBMP_API int lbmp_set_option(lbmp_handle *h, int option, long value);
  * per thread per work item -- in {automatic, 4, 8, 16, 32, 64, 128} up to
  * the marching extent, CTAs per SM in {maximum, 1, 2}) over `reps` launches
  * (>= 1) after one warm-up launch, with CUDA events on the handle's stream,
- * and keeps the fastest as the handle's options.  Trial launches read the current population set and
- * write the other one, which the next step overwrites: the state is not
- * advanced and results are unchanged.  `table` (caller-owned, may be NULL)
+ * and keeps the fastest as the handle's options.  Trial launches read the
+ * current population set and write the other one, which the next step
+ * overwrites: the state is not advanced.  `table` (caller-owned, may be NULL)
  * receives up to max_entries trials; *n_entries (may be NULL) the number of
  * trials run.  With LBMP_OPT_KERNEL = 1 nothing is tuned (n_entries = 0).
  * Synchronises the handle's stream. */
