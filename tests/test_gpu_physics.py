@@ -1,0 +1,68 @@
+"""The GPU path on the paper's validation cases at the paper's sizes (Sec.
+3.1), where the FP64 oracle is too slow to follow: the physics pins of the
+oracle (closed forms and the paper's statements) applied to the CUDA results
+directly, in FP32 and in the 16-bit storage forms."""
+import numpy as np
+import pytest
+
+from paper_2101_06769_gb300 import Domain
+from paper_2101_06769_gb300.lbmp import BF16_SHIFTED, FP16_SHIFTED, FP32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("r", [25, 35, 45])
+@pytest.mark.parametrize("sigma", [1e-3, 1e-1])
+def test_laplace_law_paper_grid(r, sigma):
+    """Sec. 3.1: static drop on 256^2, density ratio 20, nu = 0.1: the pressure
+    jump follows Delta P = sigma / r (within 5 %)."""
+    d = Domain(2, (256, 256, 1), (1, 1, 1), rho_ratio=20.0, nu_ratio=1.0, nu_h=0.1, mobility=0.02, width=5.0,
+               sigma=sigma)
+    d.init("drop_static", [float(r), 1.0, 0.0], seed=1)
+    d.step(8000)
+    ob = d.observables()
+    assert ob.health == 0
+    assert abs(ob.laplace_dp / (sigma / r) - 1) < 0.05, ob.laplace_dp / (sigma / r)
+
+
+@pytest.mark.parametrize("storage", [FP32, FP16_SHIFTED, BF16_SHIFTED])
+def test_laplace_law_3d(storage):
+    """3-D static drop: Delta P = 2 sigma / R within 5 % (64^3, R = 16), in every
+    storage form."""
+    sigma, R = 1e-3, 16.0
+    d = Domain(3, (64, 64, 64), (1, 1, 1), rho_ratio=20.0, nu_ratio=1.0, nu_h=0.1, mobility=0.02, width=4.0,
+               sigma=sigma, storage=storage)
+    d.init("drop_static", [R, 1.0, 0.0], seed=1)
+    d.step(4000)
+    ob = d.observables()
+    assert ob.health == 0 and abs(ob.mass_drift_rel) < 1e-6
+    assert abs(ob.laplace_dp / (2 * sigma / R) - 1) < 0.05, ob.laplace_dp / (2 * sigma / R)
+
+
+def test_spurious_currents_density_ratio_1000_paper_grid():
+    """Sec. 3.1: density ratio 1000, sigma = 1e-3: spurious currents of order
+    1e-6 (bound 1e-5) on the 256^2 grid."""
+    d = Domain(2, (256, 256, 1), (1, 1, 1), rho_ratio=1000.0, nu_ratio=1.0, nu_h=0.1, mobility=0.02, width=5.0,
+               sigma=1e-3)
+    d.init("drop_static", [45.0, 1.0, 0.0], seed=1)
+    d.step(8000)
+    ob = d.observables()
+    assert ob.health == 0
+    assert ob.max_u < 1e-5, ob.max_u
+
+
+@pytest.mark.parametrize("D,dims", [(2, (128, 128, 1)), (3, (64, 64, 64))])
+def test_shear_wave_viscosity(D, dims):
+    """Single-phase shear wave: the amplitude decays as exp(-nu k^2 t) with the
+    viscosity of reading A7 (within 1 %)."""
+    nu = 0.02
+    d = Domain(D, dims, (1, 1, 1), rho_ratio=3.0, nu_ratio=1.0, nu_h=nu, mobility=0.02, width=4.0, sigma=0.0)
+    d.init("shear_wave", [1e-3, 0.0], seed=1)
+    d.step(50)
+    e0 = d.observables().kinetic_energy
+    T = 2000
+    d.step(T)
+    e1 = d.observables().kinetic_energy
+    k = 2 * np.pi / dims[1]
+    nu_meas = -np.log(e1 / e0) / (2 * k * k * T)  # energy decays at twice the amplitude rate
+    assert abs(nu_meas / nu - 1) < 0.01, nu_meas
