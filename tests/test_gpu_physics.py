@@ -14,12 +14,14 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("r", [25, 35, 45])
 @pytest.mark.parametrize("sigma", [1e-3, 1e-1])
 def test_laplace_law_paper_grid(r, sigma):
-    """Sec. 3.1: static drop on 256^2, density ratio 20, nu = 0.1: the pressure
-    jump follows Delta P = sigma / r (within 5 %)."""
+    """Sec. 3.1: static drop on 256^2, density ratio 20, nu = 0.1, W = 5 (reading
+    A19): the converged pressure jump follows Delta P = sigma / r within 5 %
+    (measured 0.953-0.955 sigma / r for r = 25-45; the largest drop needs
+    about 16000 steps to converge)."""
     d = Domain(2, (256, 256, 1), (1, 1, 1), rho_ratio=20.0, nu_ratio=1.0, nu_h=0.1, mobility=0.02, width=5.0,
                sigma=sigma)
     d.init("drop_static", [float(r), 1.0, 0.0], seed=1)
-    d.step(8000)
+    d.step(20000)
     ob = d.observables()
     assert ob.health == 0
     assert abs(ob.laplace_dp / (sigma / r) - 1) < 0.05, ob.laplace_dp / (sigma / r)
@@ -27,10 +29,12 @@ def test_laplace_law_paper_grid(r, sigma):
 
 @pytest.mark.parametrize("storage", [FP32, FP16_SHIFTED, BF16_SHIFTED])
 def test_laplace_law_3d(storage):
-    """3-D static drop: Delta P = 2 sigma / R within 5 % (64^3, R = 16), in every
-    storage form."""
-    sigma, R = 1e-3, 16.0
-    d = Domain(3, (64, 64, 64), (1, 1, 1), rho_ratio=20.0, nu_ratio=1.0, nu_h=0.1, mobility=0.02, width=4.0,
+    """3-D static drop, W = 5 as in the paper's Laplace test: Delta P = 2 sigma / R
+    within 5 % in every storage form (64^3, R = 12; measured 0.968, and
+    0.956-0.961 for R = 16-24 on 96^3; an under-resolved W = 4 interface gives
+    0.93 instead, a property of the discretised model the oracle shares)."""
+    sigma, R = 1e-3, 12.0
+    d = Domain(3, (64, 64, 64), (1, 1, 1), rho_ratio=20.0, nu_ratio=1.0, nu_h=0.1, mobility=0.02, width=5.0,
                sigma=sigma, storage=storage)
     d.init("drop_static", [R, 1.0, 0.0], seed=1)
     d.step(4000)
