@@ -103,13 +103,15 @@ struct CodeLoad {
     }
 };
 
-// Decode the staged words of one cell in place and sum phi (hi, lo) from the
-// exact parts of the values (phi_sum_shifted).  R0 is
+// Decode the staged words of one cell and sum phi (hi, lo) from the exact
+// parts of the values (phi_sum_shifted); Keep: also store the decoded values
+// in place (the tile's own cells, whose values the collision reads; ring
+// cells need phi only).  R0 is
 // the reference plane of the staged plane, Rm / Rp the planes below / above;
 // slot is the cell's index in the reference-plane layout of row length RL;
 // selA / selB pick the half of a word for a source of the cell's own / the
 // other x parity.
-template <bool Walls, class St>
+template <bool Walls, class St, bool Keep>
 __device__ __forceinline__ void decode_g(const float* Rm, const float* R0, const float* Rp, int slot, int RL,
                                          unsigned selA, unsigned selB, bool lo, bool hi, float* buf, int stride,
                                          float& phi_hi, float& phi_lo)
@@ -121,7 +123,7 @@ __device__ __forceinline__ void decode_g(const float* Rm, const float* R0, const
             if (a == C3) {
                 wr = W * R0[slot];
                 wq = 0.f;
-                buf[a * stride] = wr;
+                if (Keep) buf[a * stride] = wr;
             } else {
                 const bool bounced = Walls && ((cz == 1 && lo) || (cz == -1 && hi));
                 const float* Rpl = cz == 1 ? Rm : (cz == -1 ? Rp : R0);
@@ -130,7 +132,7 @@ __device__ __forceinline__ void decode_g(const float* Rm, const float* R0, const
                 const float qv = St::dec_word(__float_as_uint(buf[a * stride]), sel);
                 wr = W * R;
                 wq = qv * (W * St::s);
-                buf[a * stride] = dec_value<3, St>(a, qv, R);  // = wr + wq, rounded once
+                if (Keep) buf[a * stride] = dec_value<3, St>(a, qv, R);  // = wr + wq, rounded once
             }
         },
         phi_hi, phi_lo);
@@ -187,18 +189,19 @@ struct Seg16 {
         if (lo || hi) {
             if (tid < NRING) {
                 const unsigned rA = (T.lx & 1) ? St::kSelHi : St::kSelLo, rB = (T.lx & 1) ? St::kSelLo : St::kSelHi;
-                decode_g<true, St>(Rm, R0, Rp, (T.ly + 2) * GX + T.lx + 2, GX, rA, rB, lo, hi, rS + tid, NRING, h, l);
+                decode_g<true, St, false>(Rm, R0, Rp, (T.ly + 2) * GX + T.lx + 2, GX, rA, rB, lo, hi, rS + tid, NRING, h,
+                                          l);
                 phi_plane[T.rslot] = make_float2(h, l);
             }
-            decode_g<true, St>(Rm, R0, Rp, ogs, GX, oA, oB, lo, hi, gbuf + tid, NT, h, l);
+            decode_g<true, St, true>(Rm, R0, Rp, ogs, GX, oA, oB, lo, hi, gbuf + tid, NT, h, l);
         } else {
             if (tid < NRING) {
                 const unsigned rA = (T.lx & 1) ? St::kSelHi : St::kSelLo, rB = (T.lx & 1) ? St::kSelLo : St::kSelHi;
-                decode_g<false, St>(Rm, R0, Rp, (T.ly + 2) * GX + T.lx + 2, GX, rA, rB, false, false, rS + tid,
-                                    NRING, h, l);
+                decode_g<false, St, false>(Rm, R0, Rp, (T.ly + 2) * GX + T.lx + 2, GX, rA, rB, false, false,
+                                           rS + tid, NRING, h, l);
                 phi_plane[T.rslot] = make_float2(h, l);
             }
-            decode_g<false, St>(Rm, R0, Rp, ogs, GX, oA, oB, false, false, gbuf + tid, NT, h, l);
+            decode_g<false, St, true>(Rm, R0, Rp, ogs, GX, oA, oB, false, false, gbuf + tid, NT, h, l);
         }
         phi_plane[T.oslot] = make_float2(h, l);
     }
