@@ -541,23 +541,19 @@ struct CellState {
     float phi, sharp;  // phi and lambda_phi 4 phi (1-phi)/W
 };
 
-// Local closure (Sec. 2.1/2.3; readings A1, A2, A7, A12, A13, A15) and the
-// relaxed second-order deviations.  Produces the 27-entry Kronecker inverse
-// of the post-collision moment differences in dh[] (h* - E(u)).
+// Local closure (Sec. 2.1/2.3; readings A1, A2, A7, A12, A13, A15): density,
+// interface normal, chemical potential, force, velocity and p_h of one cell
+// into s (every field but ew); returns rho.  Also the observables use it.
 template <int D>
-__device__ __forceinline__ void flow_collide(const DevParams& p, float phi, const float grad[3], float lap,
-                                             const FlowMoments& m, CellState& s, float dh[27])
+__device__ __forceinline__ float flow_closure(const DevParams& p, float phi, const float grad[3], float lap,
+                                              const FlowMoments& m, CellState& s, float& inv_rho, float& nu)
 {
     const float rho = p.rho_l + p.drho * phi;
-    const float inv_rho = 1.0f / rho;
-    float nu;
+    inv_rho = 1.0f / rho;
     if (p.flags & kFlagDynamicVisc)
         nu = (p.eta_l + (p.eta_h - p.eta_l) * phi) * inv_rho;
     else
         nu = p.nu_h + (p.nu_l - p.nu_h) * (1.0f - phi);
-    const float omega = 1.0f / (3.0f * nu + 0.5f);
-    const float om1 = 1.0f - omega;
-
     // interface normal, chemical potential, force
     const float g2 = grad[0] * grad[0] + grad[1] * grad[1] + (D == 3 ? grad[2] * grad[2] : 0.f);
     const float inv_g = 1.0f / fmaxf(sqrtf(g2), 1e-4f);
@@ -572,23 +568,38 @@ __device__ __forceinline__ void flow_collide(const DevParams& p, float phi, cons
         F[D - 1] -= (rho - p.rho_bar) * p.g_accel;
 
     // u = J/(rho cs2) + F/(2 rho)
-    float V[3];
     for (int i = 0; i < 3; ++i) {
         s.u[i] = (D == 2 && i == 2) ? 0.f : (3.0f * m.J[i] + 0.5f * F[i]) * inv_rho;
         s.n[i] = (D == 2 && i == 2) ? 0.f : grad[i] * inv_g;
         s.G[i] = (D == 2 && i == 2) ? 0.f : p.drho * grad[i] / 3.0f;
         s.F[i] = F[i];
-        V[i] = s.G[i] + F[i];
     }
     const float ux = s.u[0], uy = s.u[1], uz = s.u[2];
     s.uG = ux * s.G[0] + uy * s.G[1] + uz * s.G[2];
     s.uF = ux * F[0] + uy * F[1] + uz * F[2];
-    const float uV = s.uG + s.uF;
     s.uu = ux * ux + uy * uy + uz * uz;
     s.rcs2 = rho / 3.0f;
     s.ph = m.P + 0.5f * s.uG;
     s.phi = phi;
     s.sharp = p.lam_sharp * phi * (1.0f - phi);
+    return rho;
+}
+
+// The closure above and the relaxed second-order deviations.  Produces the
+// 27-entry Kronecker inverse of the post-collision moment differences in
+// dh[] (h* - E(u)).
+template <int D>
+__device__ __forceinline__ void flow_collide(const DevParams& p, float phi, const float grad[3], float lap,
+                                             const FlowMoments& m, CellState& s, float dh[27])
+{
+    float inv_rho, nu;
+    flow_closure<D>(p, phi, grad, lap, m, s, inv_rho, nu);
+    const float omega = 1.0f / (3.0f * nu + 0.5f);
+    const float om1 = 1.0f - omega;
+    const float ux = s.u[0], uy = s.u[1], uz = s.u[2];
+    float V[3];
+    for (int i = 0; i < 3; ++i) V[i] = s.G[i] + s.F[i];
+    const float uV = s.uG + s.uF;
 
     // second moments of f^p minus theta cs2 delta, i.e. with 1/cs2 = 3:
     // [3 Pi_ij - P delta_ij + (u_i V_j + u_j V_i)/2 - 3 u_i u_j u.V/2] / rho - u_i u_j

@@ -449,9 +449,8 @@ __device__ void cell_macro(const DevParams& p, const Pop<D, St>& f, const float*
     FlowMoments m;
     flow_moments<D>(m, fr);
     CellState s;
-    float dh[27];
-    flow_collide<D>(p, nh[Q / 2], grad, lap, m, s, dh);
-    rho = p.rho_l + p.drho * nh[Q / 2];
+    float inv_rho, nu;
+    rho = flow_closure<D>(p, nh[Q / 2], grad, lap, m, s, inv_rho, nu);
     for (int k = 0; k < 3; ++k) u[k] = s.u[k];
     ph = s.ph;
 }
