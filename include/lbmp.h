@@ -258,9 +258,9 @@ typedef struct lbmp_batch lbmp_batch;
  * private stream, since the legacy default stream cannot be captured). */
 LBMP_API int lbmp_batch_create(size_t hbm_budget, void *cuda_stream, lbmp_batch **out);
 LBMP_API int lbmp_batch_destroy(lbmp_batch *b);
-/* Admit h for `steps` more steps (> 0).  Members may be FP32 D2Q9, FP32
- * D3Q27 or shifted 16-bit D3Q27 domains (each kind runs its own persistent
- * kernel); a 16-bit D2Q9 domain gives LBMP_ERR_UNSUPPORTED.  LBMP_ERR_NOMEM
+/* Admit h for `steps` more steps (> 0).  Members may be D2Q9 or D3Q27
+ * domains in any storage form (each lattice and storage kind runs its own
+ * persistent kernel).  LBMP_ERR_NOMEM
  * when it would exceed the budget, LBMP_ERR_INVALID_ARG when h is already a
  * member or the batch is full (1024 members). */
 LBMP_API int lbmp_batch_add(lbmp_batch *b, lbmp_handle *h, long steps);

@@ -150,7 +150,7 @@ int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 cudaError_t launch_step(lbmp_handle* h)
 {
     if (h->kernel == 1 || !fused_supported(h)) return launch_step_simple(h);
-    if (h->params.storage != LBMP_FP32) return launch_step_fused16(h);
+    if (h->params.storage != LBMP_FP32) return h->D == 3 ? launch_step_fused16(h) : launch_step_fused2s(h);
     if (h->D == 2) return launch_step_fused2(h);
     if (h->kernel == 2 && bulk_supported(h)) return launch_step_fused_bulk(h);
     if (h->opt_tile == 1) return launch_step_fused3_t16x8(h);

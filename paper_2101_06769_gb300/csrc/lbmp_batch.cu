@@ -7,11 +7,11 @@
 // needs comes from the host, so the kernels of a run of steps are captured
 // once in a CUDA graph and the graph is replayed until the membership (or the
 // set of members with steps left) changes.  Members are grouped by kind --
-// FP32 D3Q27, FP16 D3Q27, BF16 D3Q27 (shifted storage), FP32 D2Q9 -- each
-// kind a contiguous segment of the table with its own work numbering and its
-// own persistent kernel.  Within a step the D3Q27 kernels run on the batch
-// stream and the D2Q9 kernel on a forked second stream, joined before the
-// epilogue.  The tile shape of the FP32 D3Q27 kernel and the planes (rows)
+// FP32, FP16 and BF16 (shifted storage) D3Q27, then the same for D2Q9 --
+// each kind a contiguous segment of the table with its own work numbering
+// and its own persistent kernel.  Within a step the D3Q27 kernels run on the
+// batch stream and the D2Q9 kernels on a forked second stream, joined before
+// the epilogue.  The tile shape of the FP32 D3Q27 kernel and the planes (rows)
 // per work item are options of the batch, picked by lbmp_batch_autotune.
 #include <stdio.h>
 #include <string.h>
@@ -31,15 +31,14 @@ struct Member {
     long left;
 };
 
-// member kinds, in table order
-enum Kind { kF32x3 = 0, kF16x3 = 1, kBF16x3 = 2, kF32x2 = 3, kKinds = 4 };
+// member kinds, in table order: D3Q27 kinds first, then D2Q9 kinds
+enum Kind { kF32x3 = 0, kF16x3 = 1, kBF16x3 = 2, kF32x2 = 3, kF16x2 = 4, kBF16x2 = 5, kKinds = 6 };
 
 int kind_of(const lbmp_handle* h)
 {
-    if (h->D == 2) return h->params.storage == LBMP_FP32 ? kF32x2 : -1;
-    if (h->params.storage == LBMP_FP16_SHIFTED) return kF16x3;
-    if (h->params.storage == LBMP_BF16_SHIFTED) return kBF16x3;
-    return kF32x3;
+    const int st = h->params.storage;
+    if (h->D == 2) return st == LBMP_FP16_SHIFTED ? kF16x2 : (st == LBMP_BF16_SHIFTED ? kBF16x2 : kF32x2);
+    return st == LBMP_FP16_SHIFTED ? kF16x3 : (st == LBMP_BF16_SHIFTED ? kBF16x3 : kF32x3);
 }
 
 }  // namespace
@@ -82,6 +81,8 @@ const lbmp::Batch3Ops& ops3_of(const lbmp_batch* b, int kind)
 {
     if (kind == kF16x3) return lbmp::batch3_ops_f16;
     if (kind == kBF16x3) return lbmp::batch3_ops_bf16;
+    if (kind == kF16x2) return lbmp::batch2_ops_f16;
+    if (kind == kBF16x2) return lbmp::batch2_ops_bf16;
     return lbmp::batch3_ops(b->tile);
 }
 
@@ -91,7 +92,8 @@ cudaError_t step_kernels(lbmp_batch* b)
 {
     cudaError_t e = cudaSuccess;
     const bool any3 = b->ndom[kF32x3] || b->ndom[kF16x3] || b->ndom[kBF16x3];
-    const bool fork = any3 && b->ndom[kF32x2];
+    const bool any2 = b->ndom[kF32x2] || b->ndom[kF16x2] || b->ndom[kBF16x2];
+    const bool fork = any3 && any2;
     if (fork) {
         e = cudaEventRecord(b->fork, b->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
@@ -102,6 +104,10 @@ cudaError_t step_kernels(lbmp_batch* b)
     if (e == cudaSuccess && b->ndom[kF32x2])
         e = lbmp::launch_batch2(b->d_table + b->dom0[kF32x2], b->ndom[kF32x2], b->nitems[kF32x2], b->device,
                                 fork ? b->side : b->stream);
+    for (int k = kF16x2; k <= kBF16x2 && e == cudaSuccess; ++k)
+        if (b->ndom[k])
+            e = ops3_of(b, k).launch(b->d_table + b->dom0[k], b->ndom[k], b->nitems[k], b->device,
+                                     fork ? b->side : b->stream);
     if (e == cudaSuccess && fork) {
         e = cudaEventRecord(b->join, b->side);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join, 0);
@@ -133,9 +139,10 @@ cudaError_t rebuild(lbmp_batch* b, bool graphs = true)
     b->h_table.clear();
     for (int kind = 0; kind < kKinds; ++kind) {
     b->dom0[kind] = (int)b->h_table.size();
-    const int D = kind == kF32x2 ? 2 : 3;
+    const int D = kind >= kF32x2 ? 2 : 3;
     int item = 0;
-    const int TX = D == 3 ? ops3_of(b, kind).tile_x : lbmp::batch2_tile_x(), TY = D == 3 ? ops3_of(b, kind).tile_y : 1;
+    const int TX = kind == kF32x2 ? lbmp::batch2_tile_x() : ops3_of(b, kind).tile_x;
+    const int TY = D == 3 ? ops3_of(b, kind).tile_y : 1;
     const int chunk = b->chunk > 0 ? b->chunk : 16;
     for (const Member& m : b->members) {
         if (m.left <= 0 || kind_of(m.h) != kind) continue;
@@ -168,6 +175,8 @@ cudaError_t rebuild(lbmp_batch* b, bool graphs = true)
         for (int k = kF32x3; k <= kBF16x3 && e == cudaSuccess; ++k)
             if (b->ndom[k]) e = ops3_of(b, k).prepare(b->device);
         if (e == cudaSuccess && b->ndom[kF32x2]) e = lbmp::prepare_batch2(b->device);
+        for (int k = kF16x2; k <= kBF16x2 && e == cudaSuccess; ++k)
+            if (b->ndom[k]) e = ops3_of(b, k).prepare(b->device);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(b->d_table, b->h_table.data(), sizeof(lbmp::BatchDomain) * ndom,
                                 cudaMemcpyHostToDevice, b->stream);
@@ -249,8 +258,6 @@ LBMP_API int lbmp_batch_add(lbmp_batch* b, lbmp_handle* h, long steps)
     if (steps <= 0) return batch_fail(LBMP_ERR_INVALID_ARG, "steps must be > 0");
     if (h->device != b->device) return batch_fail(LBMP_ERR_INVALID_ARG, "domain lives on another device");
     if ((int)b->members.size() >= kMaxMembers) return batch_fail(LBMP_ERR_INVALID_ARG, "batch is full");
-    if (kind_of(h) < 0)
-        return batch_fail(LBMP_ERR_UNSUPPORTED, "D2Q9 batch members must use FP32 storage");
     size_t used = 0;
     for (const Member& m : b->members) {
         if (m.h == h) return batch_fail(LBMP_ERR_INVALID_ARG, "domain is already a member");

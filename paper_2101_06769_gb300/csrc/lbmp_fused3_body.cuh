@@ -302,8 +302,8 @@ LaunchCfg g_cfg;
 }  // namespace
 
 #if LBMP_FUSED3_WITH_COMMON
-// every FP32 domain; shifted 16-bit storage in 3-D (2-D runs the reference pair)
-bool fused_supported(const lbmp_handle* h) { return h->params.storage == LBMP_FP32 || h->D == 3; }
+// every domain has a fused kernel (FP32 and shifted 16-bit, D3Q27 and D2Q9)
+bool fused_supported(const lbmp_handle*) { return true; }
 
 __global__ void batch_epilogue_kernel(BatchDomain* table, int ndom)
 {

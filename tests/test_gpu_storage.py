@@ -14,6 +14,15 @@ ratio 8 between the formats.  Observable-level bars follow the storage
 requirement: Laplace pressure jump within 1 % of the oracle, relative mass
 drift within 1e-6 over the run, and Rayleigh-Taylor tip positions within a
 fraction of a cell of the FP32 run.
+
+One case sits outside those f' figures by construction: ragged2d_even is a
+nearly quiescent walled 2-D field, |f'| <= 5.2e-5 with no pressure level to
+speak of, so f' has no rest-shaped bulk for the shift to cancel and every
+stored f' value carries the format's precision relative to itself.  Its
+100-step f' error then grows toward the coherent bound n u (n = 100 steps,
+u the half-ulp: 2.4e-2 FP16, 0.195 BF16); measured 1.27e-3 (FP16) and
+2.94e-2 (BF16), identical for the fused kernel and the reference pair.  Its
+f' bounds keep the factor ~2 margin over those measurements.
 """
 import numpy as np
 import pytest
@@ -29,6 +38,7 @@ pytestmark = pytest.mark.gpu
 STORAGES = {"fp16": FP16_SHIFTED, "bf16": BF16_SHIFTED}
 TOL_F = {"fp16": 2e-3, "bf16": 1.6e-2}     # f'
 TOL_G = {"fp16": 2e-4, "bf16": 1.6e-3}     # g and phi
+TOL_F_CASE = {("ragged2d_even", "fp16"): 3e-3, ("ragged2d_even", "bf16"): 6e-2}
 
 EVEN = dict(CASES)
 for k in [k for k, c in EVEN.items() if c["dims"][0] % 2]:
@@ -38,6 +48,12 @@ EVEN["ragged3d_walls"] = dict(D=3, dims=(38, 29, 23), periodic=(1, 1, 0),
                               phys=dict(rho_ratio=10.0, nu_ratio=5.0, nu_h=0.02, sigma=5e-3, g_accel=1e-5,
                                         mobility=0.03, width=4.0),
                               case="rt", args=[11.0, 3.0, 1e-2, 1.0], seed=6)
+# 2-D, even nx spanning three 128-cell segments (the last one ragged), walls
+# in y and the dynamic-viscosity reading
+EVEN["ragged2d_even"] = dict(D=2, dims=(262, 47, 1), periodic=(1, 0, 1),
+                             phys=dict(rho_ratio=10.0, nu_ratio=5.0, nu_h=0.02, sigma=5e-3, g_accel=1e-5,
+                                       mobility=0.03, width=4.0, flags=2),
+                             case="rt", args=[23.0, 3.0, 1e-2, 1.0], seed=6)
 EVEN["ragged3d_even"] = dict(D=3, dims=(38, 29, 23), periodic=(1, 1, 1),
                              phys=dict(rho_ratio=20.0, nu_ratio=2.0, nu_h=0.05, sigma=1e-2, mobility=0.02,
                                        width=4.0),
@@ -96,11 +112,13 @@ def test_step_parity_100_shifted(name, st):
     fo, go, po = o.get_state()
     fg, gg, pg = d.get_state()
     ef, eg, ep = rel_err(fg, fo), rel_err(gg, go), rel_err(pg, po)
-    assert ef <= TOL_F[st] and eg <= TOL_G[st] and ep <= TOL_G[st], (name, st, ef, eg, ep)
+    tf = TOL_F_CASE.get((name, st), TOL_F[st])
+    assert ef <= tf and eg <= TOL_G[st] and ep <= TOL_G[st], (name, st, ef, eg, ep)
 
 
 @pytest.mark.parametrize("st", sorted(STORAGES))
-@pytest.mark.parametrize("name", ["splash3d", "ragged3d_walls", "thin3d", "ragged3d_even"])
+@pytest.mark.parametrize("name", ["splash3d", "ragged3d_walls", "thin3d", "ragged3d_even", "rt2d", "drop2d",
+                                  "ragged2d_even"])
 def test_fused_and_reference_agree_bitwise_shifted(name, st):
     """The fused 16-bit kernel and the reference pair decode, collide and
     encode with the same FP32 operations in the same order."""
@@ -172,12 +190,13 @@ def test_rt_tips_follow_fp32():
 
 
 def test_batch_with_shifted_members_is_bitwise_stepping_alone():
-    """FP16 and BF16 D3Q27 members run in a batch beside FP32 members (each
-    kind its own persistent kernel); every member's state equals stepping it
-    alone.  A 16-bit D2Q9 member is refused."""
+    """FP16 and BF16 members of both lattices run in a batch beside FP32
+    members (each lattice and storage kind its own persistent kernel); every
+    member's state equals stepping it alone."""
     from paper_2101_06769_gb300 import Batch
     cases = [("rt3d", FP16_SHIFTED, 23), ("splash3d", BF16_SHIFTED, 17), ("ragged3d_walls", FP16_SHIFTED, 30),
-             ("rt3d", FP32, 19), ("rt2d", FP32, 21)]
+             ("rt3d", FP32, 19), ("rt2d", FP32, 21), ("rt2d", FP16_SHIFTED, 26), ("ragged2d_even", BF16_SHIFTED, 13),
+             ("drop2d", FP16_SHIFTED, 9)]
     alone, doms = [], []
     b = Batch()
     for name, st, n in cases:
@@ -194,17 +213,12 @@ def test_batch_with_shifted_members_is_bitwise_stepping_alone():
         pass
     for d, want in zip(doms, alone):
         assert all(np.array_equal(x, y) for x, y in zip(d.get_state(), want))
-    c = EVEN["rt2d"]
-    d2 = domain(c, FP16_SHIFTED)
-    d2.init(c["case"], c["args"], seed=1)
-    with pytest.raises(LbmpError):
-        b.add(d2, 10)
     b.close()
 
 
 @pytest.mark.parametrize("st", sorted(STORAGES))
 @pytest.mark.parametrize("kernel", [0, 1])
-@pytest.mark.parametrize("name", ["ragged3d_walls", "ragged3d_even", "rt2d"])
+@pytest.mark.parametrize("name", ["ragged3d_walls", "ragged3d_even", "rt2d", "ragged2d_even"])
 def test_every_slot_written_shifted(name, kernel, st):
     """As for FP32: a NaN-poisoned target set holds no NaN after a step."""
     from paper_2101_06769_gb300.lbmp import OPT_TEST_POISON
