@@ -7,7 +7,9 @@ cumulant lattice Boltzmann step of Hosseini, Safari & Thevenin (arXiv
 baseline leg of ``bench.py`` may import it; the CUDA library never does.
 
 Arrays use the exchange format both implementations agree on:
-direction a = (cx+1) + 3(cy+1) + 9(cz+1), layout [a][z][y][x].
+direction a = (cx+1) + 3(cy+1) + 9(cz+1), layout [a][z][y][x].  With
+FLAG_PHASE_REDUCED the phase field g lives on the rest and face directions
+only (D3Q7 / D2Q5), in the same relative order.
 """
 import ctypes as C
 import os
@@ -21,6 +23,7 @@ CASE = {"rt": 0, "drop_static": 1, "flat": 2, "poiseuille": 3, "drop_sheet": 4,
 FLAG_WE_LIGHT = 1 << 0
 FLAG_DYNAMIC_VISC = 1 << 1
 FLAG_UNIFORM_FORCE = 1 << 2
+FLAG_PHASE_REDUCED = 1 << 3
 
 
 class Phys(C.Structure):
@@ -73,6 +76,12 @@ def lib():
         L.lbmo_kron_inverse.argtypes = [C.c_int, _dp, _dp, _dp]
         L.lbmo_collide_cell.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp, C.c_double,
                                         _dp, _dp, C.c_void_p]
+        L.lbmo_collide_cell_prev.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp, C.c_double,
+                                             C.c_void_p, _dp, _dp, C.c_void_p]
+        L.lbmo_phase_lattice.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_void_p,
+                                         C.POINTER(C.c_double)]
+        L.lbmo_phase_q.argtypes = [C.c_void_p]
+        L.lbmo_phase_q.restype = C.c_int
         L.lbmo_splitmix64.restype = C.c_ulonglong
         L.lbmo_splitmix64.argtypes = [C.c_ulonglong, C.c_ulonglong]
         _lib = L
@@ -101,6 +110,16 @@ def lattice(D: int):
     w = np.zeros(27)
     lib().lbmo_lattice(D, C.byref(Q), c.ctypes.data, w.ctypes.data)
     return c[:Q.value].copy(), w[:Q.value].copy()
+
+
+def phase_lattice(D: int, reduced: bool):
+    """(c, w, cs2) of the phase-field lattice: the flow lattice, or D3Q7 / D2Q5."""
+    Q = C.c_int()
+    cs2 = C.c_double()
+    c = np.zeros((27, 3), dtype=np.int32)
+    w = np.zeros(27)
+    lib().lbmo_phase_lattice(D, int(bool(reduced)), C.byref(Q), c.ctypes.data, w.ctypes.data, C.byref(cs2))
+    return c[:Q.value].copy(), w[:Q.value].copy(), cs2.value
 
 
 def splitmix64(seed: int, counter: int) -> int:
@@ -146,6 +165,7 @@ class Oracle:
         self._h = lib().lbmo_create(D, d, p, C.byref(make_phys(**phys)))
         if not self._h:
             raise ValueError(lib().lbmo_last_error().decode())
+        self.Qg = int(lib().lbmo_phase_q(self._h))
 
     def close(self):
         if self._h:
@@ -180,9 +200,13 @@ class Oracle:
     def step(self, n=1):
         lib().lbmo_step(self._h, int(n))
 
+    @property
+    def gshape(self):
+        return (self.Qg,) + self.shape[1:]
+
     def get_state(self):
         f = np.zeros(self.shape)
-        g = np.zeros(self.shape)
+        g = np.zeros(self.gshape)
         phi = np.zeros(self.shape[1:])
         lib().lbmo_get_state(self._h, f.ctypes.data, g.ctypes.data, phi.ctypes.data)
         return f, g, phi
@@ -210,14 +234,17 @@ class Oracle:
         lib().lbmo_fd(self._h, field.ravel(), grad.ravel(), lap.ravel())
         return grad, lap
 
-    def collide_cell(self, f, g, phi, grad, lap):
+    def collide_cell(self, f, g, phi, grad, lap, phiu_prev=None):
+        """One cell's collision; phiu_prev: the previous step's phi u (reduced
+        phase lattice; None = no time derivative).  diag[14:17] = phi u."""
         fo = np.zeros(self.Q)
-        go = np.zeros(self.Q)
-        diag = np.zeros(16)
-        lib().lbmo_collide_cell(self._h, np.ascontiguousarray(f, dtype=np.float64),
-                                np.ascontiguousarray(g, dtype=np.float64), float(phi),
-                                np.ascontiguousarray(grad, dtype=np.float64), float(lap),
-                                fo, go, diag.ctypes.data)
+        go = np.zeros(self.Qg)
+        diag = np.zeros(17)
+        prev = None if phiu_prev is None else np.ascontiguousarray(phiu_prev, dtype=np.float64)
+        lib().lbmo_collide_cell_prev(self._h, np.ascontiguousarray(f, dtype=np.float64),
+                                     np.ascontiguousarray(g, dtype=np.float64), float(phi),
+                                     np.ascontiguousarray(grad, dtype=np.float64), float(lap),
+                                     None if prev is None else prev.ctypes.data, fo, go, diag.ctypes.data)
         return fo, go, diag
 
 

@@ -27,6 +27,12 @@
  *   A15 F_b = -(rho - (rho_h+rho_l)/2) g e_vertical
  *   A16 We = rho_h L U^2/sigma   A17 half-way bounce-back, mirrored phi ghosts
  *   A18 tanh initial profiles    A21 D2Q9 restriction of the 3-D relations
+ * and, for the reduced phase lattice of Sec. 2.2 (LBMO_FLAG_PHASE_REDUCED):
+ *   P1  D3Q7 (w 1/4 rest, 1/8 faces, cs2 = 1/4) / D2Q5 (1/3, 1/6, cs2 = 1/3)
+ *   P2  d/dt(phi u) = (phi u)^n - (phi u)^(n-1); before the first step the
+ *       previous value is the current one (init and set_state)
+ *   P3  tau_bar_phi = M/cs2 + 1/2 with the phase lattice's cs2; C_bar takes
+ *       the factor lambda of A4, like S_bar
  */
 #include "lbmo.h"
 
@@ -52,6 +58,7 @@ typedef struct {
     int D, Q;
     int c[27][3];
     double w[27];
+    double cs2;
 } lattice;
 
 static double w1(int c) { return c == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
@@ -67,6 +74,45 @@ static void lattice_build(int D, lattice *L)
         L->c[a][2] = cz;
         L->w[a] = w1(cx) * w1(cy) * (D == 3 ? w1(cz) : 1.0);
     }
+    L->cs2 = CS2;
+}
+
+/* Lattice of the phase field.  The full lattice, or (reduced) its rest and
+ * face directions in the same relative order, with the D3Q7 / D2Q5 weights
+ * (reading P1): sum w = 1, sum w c = 0, sum w c c = cs2 I. */
+static void phase_lattice_build(int D, int reduced, lattice *L)
+{
+    lattice full;
+    lattice_build(D, &full);
+    if (!reduced) {
+        *L = full;
+        return;
+    }
+    L->D = D;
+    L->Q = 0;
+    for (int a = 0; a < full.Q; ++a) {
+        int moving = abs(full.c[a][0]) + abs(full.c[a][1]) + abs(full.c[a][2]);
+        if (moving > 1) continue;
+        for (int i = 0; i < 3; ++i) L->c[L->Q][i] = full.c[a][i];
+        if (D == 3)
+            L->w[L->Q] = moving ? 1.0 / 8.0 : 1.0 / 4.0;
+        else
+            L->w[L->Q] = moving ? 1.0 / 6.0 : 1.0 / 3.0;
+        L->Q += 1;
+    }
+    L->cs2 = (D == 3) ? 0.25 : 1.0 / 3.0;
+}
+
+void lbmo_phase_lattice(int D, int reduced, int *Q, int *c, double *w, double *cs2)
+{
+    lattice L;
+    phase_lattice_build(D, reduced, &L);
+    *Q = L.Q;
+    for (int a = 0; a < L.Q; ++a) {
+        for (int i = 0; i < 3; ++i) c[3 * a + i] = L.c[a][i];
+        w[a] = L.w[a];
+    }
+    *cs2 = L.cs2;
 }
 
 void lbmo_lattice(int D, int *Q, int *c, double *w)
@@ -82,9 +128,10 @@ void lbmo_lattice(int D, int *Q, int *c, double *w)
 
 /* ------------------------------------------------------------ the state */
 struct lbmo {
-    int D, Q, n[3], per[3], vert;
+    int D, Q, Qg, n[3], per[3], vert;
     long N;
-    lattice L;
+    lattice L, Lg;      /* flow lattice, phase-field lattice */
+    double *phiu_prev;  /* reduced phase lattice: phi u of the previous step, [3][cell] */
     lbmo_phys phys;
     lbmo_derived d;
     double rate_shear, rate_bulk, r3, r4, r5, r6;
@@ -100,10 +147,11 @@ struct lbmo {
  *   nu_h  = U_ref L / Re (Re = rho_h U L / mu_h)
  *   sigma = rho L U^2 / We (Sec. 3.4, reading A16)
  *   beta = 12 sigma / W, kappa = 3 sigma W / 2 (Sec. 2.1)
- *   tau_bar_phi = M / cs2 + 1/2 (Sec. 2.2), lambda = 1 - 1/(2 tau_bar_phi) (A4) */
+ *   tau_bar_phi = M / cs2 + 1/2 (Sec. 2.2), lambda = 1 - 1/(2 tau_bar_phi) (A4),
+ *   cs2 of the phase-field lattice (P3) */
 int lbmo_derive(int D, const lbmo_phys *p, lbmo_derived *o)
 {
-    (void)D;
+    const double cs2g = ((p->flags & LBMO_FLAG_PHASE_REDUCED) && D == 3) ? 0.25 : CS2;
     memset(o, 0, sizeof *o);
     o->rho_h = 1.0;
     if (p->atwood > 0.0) {
@@ -141,7 +189,7 @@ int lbmo_derive(int D, const lbmo_phys *p, lbmo_derived *o)
     o->M = p->mobility;
     o->beta = 12.0 * o->sigma / o->W;
     o->kappa = 1.5 * o->sigma * o->W;
-    o->tau_phi = o->M / CS2 + 0.5;
+    o->tau_phi = o->M / cs2g + 0.5;
     o->lambda_phi = 1.0 - 1.0 / (2.0 * o->tau_phi);
     o->g_accel = p->g_accel;
     o->force_x = p->force_x;
@@ -161,6 +209,8 @@ lbmo *lbmo_create(int D, const int dims[3], const int periodic[3], const lbmo_ph
     s->D = D;
     lattice_build(D, &s->L);
     s->Q = s->L.Q;
+    phase_lattice_build(D, (p->flags & LBMO_FLAG_PHASE_REDUCED) ? 1 : 0, &s->Lg);
+    s->Qg = s->Lg.Q;
     for (int i = 0; i < 3; ++i) {
         s->n[i] = dims[i];
         s->per[i] = periodic[i] ? 1 : 0;
@@ -173,12 +223,14 @@ lbmo *lbmo_create(int D, const int dims[3], const int periodic[3], const lbmo_ph
     s->rate_shear = -1.0;
     s->rate_bulk = s->r3 = s->r4 = s->r5 = s->r6 = 1.0;
     size_t bytes = sizeof(double) * (size_t)s->Q * (size_t)s->N;
+    size_t gbytes = sizeof(double) * (size_t)s->Qg * (size_t)s->N;
     s->f = (double *)calloc(1, bytes);
-    s->g = (double *)calloc(1, bytes);
+    s->g = (double *)calloc(1, gbytes);
     s->fn = (double *)calloc(1, bytes);
-    s->gn = (double *)calloc(1, bytes);
+    s->gn = (double *)calloc(1, gbytes);
     s->phi = (double *)calloc((size_t)s->N, sizeof(double));
-    if (!s->f || !s->g || !s->fn || !s->gn || !s->phi) {
+    s->phiu_prev = (double *)calloc(3 * (size_t)s->N, sizeof(double));
+    if (!s->f || !s->g || !s->fn || !s->gn || !s->phi || !s->phiu_prev) {
         lbmo_destroy(s);
         set_err("out of memory");
         return NULL;
@@ -195,6 +247,7 @@ void lbmo_destroy(lbmo *s)
     free(s->fn);
     free(s->gn);
     free(s->phi);
+    free(s->phiu_prev);
     free(s);
 }
 
@@ -503,6 +556,14 @@ static double gamma_eq(const lattice *L, int a, const double u[3])
 void lbmo_collide_cell(const lbmo *s, const double *f, const double *g, double phi, const double grad[3], double lap,
                        double *fout, double *gout, double *diag)
 {
+    lbmo_collide_cell_prev(s, f, g, phi, grad, lap, NULL, fout, gout, diag);
+}
+
+int lbmo_phase_q(const lbmo *s) { return s->Qg; }
+
+void lbmo_collide_cell_prev(const lbmo *s, const double *f, const double *g, double phi, const double grad[3],
+                            double lap, const double *phiu_prev, double *fout, double *gout, double *diag)
+{
     const lattice *L = &s->L;
     const lbmo_derived *d = &s->d;
     const int Q = L->Q, D = L->D;
@@ -541,11 +602,28 @@ void lbmo_collide_cell(const lbmo *s, const double *f, const double *g, double p
     for (int a = 0; a < Q; ++a) fout[a] = c.rho * CS2 * (hs[a] + L->w[a] * (theta - 1.0)) + 0.5 * Xi[a];
 
     /* phase field: BGK towards g_eq with the sharpening source (Sec. 2.2) */
+    const lattice *Lg = &s->Lg;
+    const int reduced = (s->phys.flags & LBMO_FLAG_PHASE_REDUCED) != 0;
     double X = 4.0 * phi * (1.0 - phi) / d->W;
-    for (int a = 0; a < Q; ++a) {
-        double geq = phi * gamma_eq(L, a, u);
-        double cn = L->c[a][0] * c.n[0] + L->c[a][1] * c.n[1] + L->c[a][2] * c.n[2];
-        gout[a] = g[a] - (g[a] - geq) / d->tau_phi + d->lambda_phi * L->w[a] * cn * X;
+    double phiu[3], dphiu[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < 3; ++i) {
+        phiu[i] = phi * u[i];
+        if (reduced && phiu_prev) dphiu[i] = phiu[i] - phiu_prev[i]; /* d/dt(phi u), reading P2 */
+    }
+    for (int a = 0; a < Lg->Q; ++a) {
+        double cn = Lg->c[a][0] * c.n[0] + Lg->c[a][1] * c.n[1] + Lg->c[a][2] * c.n[2];
+        double geq, corr = 0.0;
+        if (reduced) {
+            /* first-order equilibrium w phi (1 + c.u/cs2) and the correction
+             * C_bar = lambda (w/cs2) c . d/dt(phi u) (Sec. 2.2) */
+            double cu = Lg->c[a][0] * u[0] + Lg->c[a][1] * u[1] + Lg->c[a][2] * u[2];
+            double cd = Lg->c[a][0] * dphiu[0] + Lg->c[a][1] * dphiu[1] + Lg->c[a][2] * dphiu[2];
+            geq = Lg->w[a] * phi * (1.0 + cu / Lg->cs2);
+            corr = d->lambda_phi * Lg->w[a] * cd / Lg->cs2;
+        } else {
+            geq = phi * gamma_eq(L, a, u);
+        }
+        gout[a] = g[a] - (g[a] - geq) / d->tau_phi + d->lambda_phi * Lg->w[a] * cn * X + corr;
     }
     if (diag) {
         diag[0] = c.rho;
@@ -556,13 +634,14 @@ void lbmo_collide_cell(const lbmo *s, const double *f, const double *g, double p
         for (int i = 0; i < 3; ++i) diag[7 + i] = c.F[i];
         diag[10] = sumXi;
         for (int i = 0; i < 3; ++i) diag[11 + i] = sumcXi[i];
+        for (int i = 0; i < 3; ++i) diag[14 + i] = phiu[i];
     }
 }
 
 /* ------------------------------------------------------------- stepping */
 static void update_phi(lbmo *s)
 {
-    const int Q = s->Q;
+    const int Q = s->Qg;
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < s->N; ++i) {
         double p = 0.0;
@@ -571,45 +650,50 @@ static void update_phi(lbmo *s)
     }
 }
 
+/* push population value v of direction a (velocity c) of the cell at xyz into
+ * the array set out (Q directions): to the downstream cell, or back into the
+ * same cell in the opposite direction across a half-way wall (A17) */
+static void push(const lbmo *s, double *out, int Q, const int c[3], int a, const int xyz[3], long i, double v)
+{
+    int dst[3], wall = 0;
+    for (int k = 0; k < 3; ++k) {
+        int p = xyz[k] + c[k];
+        if (p < 0 || p >= s->n[k]) {
+            if (s->per[k])
+                p = (p + s->n[k]) % s->n[k];
+            else
+                wall = 1;
+        }
+        dst[k] = p;
+    }
+    if (wall)
+        out[(size_t)(Q - 1 - a) * s->N + i] = v;
+    else
+        out[(size_t)a * s->N + cell_index(s, dst[0], dst[1], dst[2])] = v;
+}
+
 static void step_once(lbmo *s)
 {
-    const lattice *L = &s->L;
-    const int Q = s->Q;
+    const lattice *L = &s->L, *Lg = &s->Lg;
+    const int Q = s->Q, Qg = s->Qg;
     const long N = s->N;
+    const int reduced = (s->phys.flags & LBMO_FLAG_PHASE_REDUCED) != 0;
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < N; ++i) {
         int x = (int)(i % s->n[0]), y = (int)((i / s->n[0]) % s->n[1]), z = (int)(i / ((long)s->n[0] * s->n[1]));
-        double fl[27], gl[27], fo[27], go[27], grad[3], lap;
-        for (int a = 0; a < Q; ++a) {
-            fl[a] = s->f[(size_t)a * N + i];
-            gl[a] = s->g[(size_t)a * N + i];
-        }
+        double fl[27], gl[27], fo[27], go[27], grad[3], lap, diag[17], prev[3];
+        for (int a = 0; a < Q; ++a) fl[a] = s->f[(size_t)a * N + i];
+        for (int a = 0; a < Qg; ++a) gl[a] = s->g[(size_t)a * N + i];
+        for (int k = 0; k < 3; ++k) prev[k] = s->phiu_prev[(size_t)k * N + i];
         fd_cell(s, s->phi, x, y, z, grad, &lap);
-        lbmo_collide_cell(s, fl, gl, s->phi[i], grad, lap, fo, go, NULL);
+        lbmo_collide_cell_prev(s, fl, gl, s->phi[i], grad, lap, reduced ? prev : NULL, fo, go, diag);
+        /* this step's phi u becomes the previous value of the next step (P2);
+         * each cell reads and writes only its own entry */
+        for (int k = 0; k < 3; ++k) s->phiu_prev[(size_t)k * N + i] = diag[14 + k];
         /* push streaming; half-way bounce-back at walls */
         int xyz[3] = {x, y, z};
-        for (int a = 0; a < Q; ++a) {
-            int dst[3], wall = 0;
-            for (int k = 0; k < 3; ++k) {
-                int v = xyz[k] + L->c[a][k];
-                if (v < 0 || v >= s->n[k]) {
-                    if (s->per[k])
-                        v = (v + s->n[k]) % s->n[k];
-                    else
-                        wall = 1;
-                }
-                dst[k] = v;
-            }
-            if (wall) {
-                int ab = Q - 1 - a;
-                s->fn[(size_t)ab * N + i] = fo[a];
-                s->gn[(size_t)ab * N + i] = go[a];
-            } else {
-                long j = cell_index(s, dst[0], dst[1], dst[2]);
-                s->fn[(size_t)a * N + j] = fo[a];
-                s->gn[(size_t)a * N + j] = go[a];
-            }
-        }
+        for (int a = 0; a < Q; ++a) push(s, s->fn, Q, L->c[a], a, xyz, i, fo[a]);
+        for (int a = 0; a < Qg; ++a) push(s, s->gn, Qg, Lg->c[a], a, xyz, i, go[a]);
     }
     double *t = s->f;
     s->f = s->fn;
@@ -629,17 +713,37 @@ void lbmo_step(lbmo *s, long n)
 void lbmo_get_state(const lbmo *s, double *f, double *g, double *phi)
 {
     size_t bytes = sizeof(double) * (size_t)s->Q * (size_t)s->N;
+    size_t gbytes = sizeof(double) * (size_t)s->Qg * (size_t)s->N;
     if (f) memcpy(f, s->f, bytes);
-    if (g) memcpy(g, s->g, bytes);
+    if (g) memcpy(g, s->g, gbytes);
     if (phi) memcpy(phi, s->phi, sizeof(double) * (size_t)s->N);
+}
+
+/* phi u of every cell from the current state (the u the next step's closure
+ * computes): the previous value before the first step (reading P2) */
+static void reset_phiu(lbmo *s)
+{
+    const long N = s->N;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < N; ++i) {
+        int x = (int)(i % s->n[0]), y = (int)((i / s->n[0]) % s->n[1]), z = (int)(i / ((long)s->n[0] * s->n[1]));
+        double fl[27], grad[3], lap;
+        for (int a = 0; a < s->Q; ++a) fl[a] = s->f[(size_t)a * N + i];
+        fd_cell(s, s->phi, x, y, z, grad, &lap);
+        closure c;
+        local_closure(s, fl, s->phi[i], grad, lap, &c);
+        for (int k = 0; k < 3; ++k) s->phiu_prev[(size_t)k * N + i] = s->phi[i] * c.u[k];
+    }
 }
 
 void lbmo_set_state(lbmo *s, const double *f, const double *g)
 {
     size_t bytes = sizeof(double) * (size_t)s->Q * (size_t)s->N;
+    size_t gbytes = sizeof(double) * (size_t)s->Qg * (size_t)s->N;
     memcpy(s->f, f, bytes);
-    memcpy(s->g, g, bytes);
+    memcpy(s->g, g, gbytes);
     update_phi(s);
+    reset_phiu(s);
 }
 
 /* --------------------------------------------------------- initial state */
@@ -662,7 +766,8 @@ static double tanh_profile(double dist, double W) { return 0.5 * (1.0 + tanh(2.0
 
 int lbmo_init(lbmo *s, int case_id, const double *args, int nargs, unsigned long long seed)
 {
-    const lattice *L = &s->L;
+    const lattice *L = &s->L, *Lg = &s->Lg;
+    const int reduced = (s->phys.flags & LBMO_FLAG_PHASE_REDUCED) != 0;
     const lbmo_derived *d = &s->d;
     const int D = s->D, Q = s->Q, v = s->vert;
     const long N = s->N;
@@ -765,10 +870,18 @@ int lbmo_init(lbmo *s, int case_id, const double *args, int nargs, unsigned long
             double G = gamma_eq(L, a, u);
             /* f'_eq = w p_h + rho cs2 (Gamma - w)   (Sec. 2.3, App. A) */
             s->f[(size_t)a * N + i] = L->w[a] * p + rho * CS2 * (G - L->w[a]);
-            s->g[(size_t)a * N + i] = phi * G;
+            if (!reduced) s->g[(size_t)a * N + i] = phi * G;
+        }
+        if (reduced) {
+            /* first-order phase-field equilibrium (Sec. 2.2) */
+            for (int a = 0; a < Lg->Q; ++a) {
+                double cu = Lg->c[a][0] * u[0] + Lg->c[a][1] * u[1] + Lg->c[a][2] * u[2];
+                s->g[(size_t)a * N + i] = Lg->w[a] * phi * (1.0 + cu / Lg->cs2);
+            }
         }
     }
     update_phi(s);
+    reset_phiu(s);
     s->step = 0;
     return 0;
 }

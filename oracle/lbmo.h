@@ -14,12 +14,17 @@
  *   opposite(a)      = Q-1-a
  *   arrays           [a][z][y][x], x fastest; cell index x + nx*(y + ny*z)
  *   state            post-streaming populations f'(x,t) and g(x,t) of Sec. 2.2/2.3
+ *   reduced phase lattice (LBMO_FLAG_PHASE_REDUCED): g lives on the rest and
+ *                    face directions only (D3Q7 / D2Q5), in the same relative
+ *                    order, r = 0..Qg-1, opposite(r) = Qg-1-r
  *
  * Parity status: every function below is pinned by tests under tests/
  * (lattice moments, finite-difference exactness, cumulant relations against
  * the general moment-cumulant formula, mass conservation, rest state,
  * moment identities, shear-wave decay, flat-interface profile, Laplace law,
- * layered Poiseuille flow, splitmix64 published outputs).
+ * layered Poiseuille flow, splitmix64 published outputs; for the reduced
+ * phase lattice: isotropy, equilibrium and update moments, Galilean
+ * invariance of an advected interface, mass, Laplace law).
  */
 #ifndef LBMO_H
 #define LBMO_H
@@ -43,7 +48,11 @@ enum {
 enum {
     LBMO_FLAG_WE_LIGHT = 1u << 0,      /* We built on rho_l instead of rho_h        */
     LBMO_FLAG_DYNAMIC_VISC = 1u << 1,  /* interpolate eta linearly, nu = eta/rho     */
-    LBMO_FLAG_UNIFORM_FORCE = 1u << 2  /* body force = force_x along x (no gravity)  */
+    LBMO_FLAG_UNIFORM_FORCE = 1u << 2, /* body force = force_x along x (no gravity)  */
+    /* phase field on D3Q7 / D2Q5 with the first-order equilibrium and the
+     * correction term C_bar of Sec. 2.2 (instead of the second-order
+     * equilibrium on the flow lattice) */
+    LBMO_FLAG_PHASE_REDUCED = 1u << 3
 };
 
 typedef struct {
@@ -96,6 +105,9 @@ int lbmo_get_threads(void);
 
 /* ---- pieces exposed for the pin tests ---- */
 void lbmo_lattice(int D, int *Q, int *c /* Q*3 */, double *w /* Q */);
+/* lattice of the phase field: the flow lattice (reduced = 0) or D3Q7 / D2Q5
+ * (reduced = 1); cs2 = its squared sound speed */
+void lbmo_phase_lattice(int D, int reduced, int *Q, int *c /* Q*3 */, double *w /* Q */, double *cs2);
 /* isotropic finite differences (Sec. 2.2) of an arbitrary field on the grid of s */
 void lbmo_fd(const lbmo *s, const double *field, double *grad /* 3*N */, double *lap /* N */);
 /* central moments (27, index a + 3b + 9c) of populations h about velocity u */
@@ -107,6 +119,13 @@ void lbmo_kron_inverse(int D, const double *kappa, const double u[3], double *h)
  * diag (may be NULL) receives: rho, u[3], p_h, theta, omega, F[3], sumXi, sumcXi[3] */
 void lbmo_collide_cell(const lbmo *s, const double *f, const double *g, double phi,
                        const double grad[3], double lap, double *fout, double *gout, double *diag);
+/* the same with the previous step's phi u of the cell (reduced phase lattice:
+ * d/dt(phi u) = phi u - phiu_prev; NULL = 0).  diag (size >= 17) also
+ * receives this step's phi u at diag[14..16]. */
+void lbmo_collide_cell_prev(const lbmo *s, const double *f, const double *g, double phi, const double grad[3],
+                            double lap, const double *phiu_prev, double *fout, double *gout, double *diag);
+/* number of phase-field populations of s (Qg) */
+int lbmo_phase_q(const lbmo *s);
 unsigned long long lbmo_splitmix64(unsigned long long seed, unsigned long long counter);
 
 #ifdef __cplusplus
