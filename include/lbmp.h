@@ -86,7 +86,16 @@ enum {
 enum {
     LBMP_FLAG_WE_LIGHT = 1u << 0,     /* sigma = rho_l L U^2/We (the paper's printed We) */
     LBMP_FLAG_DYNAMIC_VISC = 1u << 1, /* eta(phi) linear, nu = eta/rho */
-    LBMP_FLAG_UNIFORM_FORCE = 1u << 2 /* body force = force_x along x instead of gravity */
+    LBMP_FLAG_UNIFORM_FORCE = 1u << 2, /* body force = force_x along x instead of gravity */
+    /* Phase field on the reduced lattice D3Q7 / D2Q5 (rest and face
+     * directions, weights 1/4, 1/8 and cs2 = 1/4 in 3-D; 1/3, 1/6 and
+     * cs2 = 1/3 in 2-D) with the first-order equilibrium w phi (1 + c.u/cs2)
+     * and the correction term (1 - 1/(2 tau)) (w/cs2) c . d/dt(phi u) of
+     * Sec. 2.2, d/dt(phi u) the backward difference of a stored per-cell
+     * phi u (the previous value equals the current one before the first step
+     * after lbmp_init / lbmp_set_state).  The flow lattice is unchanged.
+     * FP32 storage only (LBMP_ERR_UNSUPPORTED otherwise); not a batch member. */
+    LBMP_FLAG_PHASE_REDUCED = 1u << 3
 };
 
 typedef struct {
@@ -162,14 +171,16 @@ LBMP_API int lbmp_sync(lbmp_handle *h);
  * LBMP_ERR_UNSTABLE when the state holds non-finite values. */
 LBMP_API int lbmp_observables(lbmp_handle *h, lbmp_obs *out);
 
-/* Host copies of the state in the exchange format (synchronise).  f and g
- * hold Q*N doubles, phi N doubles; any of them may be NULL in get_state. */
+/* Host copies of the state in the exchange format (synchronise).  f holds
+ * Q*N doubles, g Qg*N (Qg = Q, or 2D+1 with LBMP_FLAG_PHASE_REDUCED: the
+ * rest and face directions in the same relative order, opposite(r) =
+ * Qg-1-r), phi N doubles; any of them may be NULL in get_state. */
 LBMP_API int lbmp_get_state(lbmp_handle *h, double *f, double *g, double *phi);
 LBMP_API int lbmp_set_state(lbmp_handle *h, const double *f, const double *g);
 
 /* Raw transfers of the device state in its native storage layout (an opaque
- * byte image, valid only for a handle of the same grid, lattice and
- * storage).  Asynchronous on the handle's stream; host memory should be
+ * byte image, valid only for a handle of the same grid, lattice, storage and
+ * phase lattice; with LBMP_FLAG_PHASE_REDUCED it includes the stored phi u).  Asynchronous on the handle's stream; host memory should be
  * pinned.  bytes must equal lbmp_state_bytes(h). */
 LBMP_API size_t lbmp_state_bytes(const lbmp_handle *h);
 LBMP_API int lbmp_upload(lbmp_handle *h, const void *host, size_t bytes);

@@ -38,9 +38,9 @@ int cuda_fail(cudaError_t e, const char* where)
 //   rho_h = 1; rho_l = 1/ratio or (1-At)/(1+At);
 //   U = U0, or sqrt(g L) for gravity-driven cases; nu_h = U L / Re;
 //   sigma = rho_h L U^2 / We (rho_l with LBMP_FLAG_WE_LIGHT);
-//   beta = 12 sigma/W, kappa = 3 sigma W/2; tau_phi = M/cs2 + 1/2,
-//   lambda_phi = 1 - 1/(2 tau_phi).
-int derive(const lbmp_params& p, lbmp_derived& d)
+//   beta = 12 sigma/W, kappa = 3 sigma W/2; tau_phi = M/cs2 + 1/2 with the
+//   phase lattice's cs2 (1/4 on D3Q7, else 1/3), lambda_phi = 1 - 1/(2 tau_phi).
+int derive(const lbmp_params& p, int D, lbmp_derived& d)
 {
     memset(&d, 0, sizeof d);
     d.rho_h = 1.0;
@@ -73,7 +73,8 @@ int derive(const lbmp_params& p, lbmp_derived& d)
     d.M = p.mobility;
     d.beta = 12.0 * d.sigma / d.W;
     d.kappa = 1.5 * d.sigma * d.W;
-    d.tau_phi = 3.0 * d.M + 0.5;
+    const double cs2g = ((p.flags & LBMP_FLAG_PHASE_REDUCED) && D == 3) ? 0.25 : 1.0 / 3.0;
+    d.tau_phi = d.M / cs2g + 0.5;
     d.lambda_phi = 1.0 - 0.5 / d.tau_phi;
     d.g_accel = p.g_accel;
     d.force_x = p.force_x;
@@ -102,6 +103,7 @@ void fill_devparams(lbmp_handle* h)
     q.kappa = (float)d.kappa;
     q.inv_tau_phi = (float)(1.0 / d.tau_phi);
     q.lam_sharp = (float)(d.lambda_phi * 4.0 / d.W);
+    q.lam_corr = (float)(d.lambda_phi * ((h->reduced && h->D == 3) ? 4.0 : 3.0));
     q.g_accel = (float)d.g_accel;
     q.force_x = (float)d.force_x;
     q.flags = h->params.flags;
@@ -116,6 +118,7 @@ void free_handle(lbmp_handle* h)
         if (h->g[k]) cudaFree(h->g[k]);
     }
     if (h->phi) cudaFree(h->phi);
+    if (h->phiu) cudaFree(h->phiu);
     if (h->red) cudaFree(h->red);
     if (h->red_out) cudaFree(h->red_out);
     delete h;
@@ -184,7 +187,9 @@ int lbmp_create(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* 
     // shifted codes are staged as 32-bit words holding two neighbouring cells
     if (params->storage != LBMP_FP32 && (grid->nx & 1))
         return fail(LBMP_ERR_INVALID_ARG, "16-bit storage needs an even nx");
-    if (params->flags & ~7u) return fail(LBMP_ERR_INVALID_ARG, "unknown flag bits");
+    if (params->flags & ~15u) return fail(LBMP_ERR_INVALID_ARG, "unknown flag bits");
+    if ((params->flags & LBMP_FLAG_PHASE_REDUCED) && params->storage != LBMP_FP32)
+        return fail(LBMP_ERR_UNSUPPORTED, "the reduced phase lattice is stored in FP32 only");
 
     lbmp_handle* h = new (std::nothrow) lbmp_handle();
     if (!h) return fail(LBMP_ERR_NOMEM, "host allocation failed");
@@ -192,10 +197,12 @@ int lbmp_create(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* 
     h->grid = *grid;
     h->D = D;
     h->Q = (D == 3) ? 27 : 9;
+    h->reduced = (params->flags & LBMP_FLAG_PHASE_REDUCED) != 0;
+    h->Qg = h->reduced ? 2 * D + 1 : h->Q;
     h->params = *params;
     h->N = N;
     h->stream = (cudaStream_t)cuda_stream;
-    int rc = derive(*params, h->der);
+    int rc = derive(*params, D, h->der);
     if (rc != LBMP_OK) {
         delete h;
         return rc;
@@ -211,12 +218,13 @@ int lbmp_create(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* 
         delete h;
         return cuda_fail(e, "cudaGetDevice");
     }
-    const size_t pop = lbmp::set_bytes(h);
+    const size_t pop = lbmp::set_bytes(h), gpop = lbmp::gset_bytes(h);
     for (int k = 0; k < 2; ++k) {
         e = cudaMalloc(&h->f[k], pop);
-        if (e == cudaSuccess) e = cudaMalloc(&h->g[k], pop);
+        if (e == cudaSuccess) e = cudaMalloc(&h->g[k], gpop);
         if (e != cudaSuccess) break;
     }
+    if (e == cudaSuccess && h->reduced) e = cudaMalloc(&h->phiu, lbmp::phiu_bytes(h));
     if (e == cudaSuccess) e = cudaMalloc(&h->phi, 2 * sizeof(float) * (size_t)N);
     h->red_blocks = 1024;
     if (e == cudaSuccess) e = cudaMalloc(&h->red, sizeof(double) * 4 * h->red_blocks);
@@ -282,7 +290,7 @@ int lbmp_set_option(lbmp_handle* h, int option, long value)
         if (value != 1) return fail(LBMP_ERR_INVALID_ARG, "test poison must be 1");
         const int d = 1 - h->parity;
         LBMP_CUDA(cudaMemsetAsync(h->f[d], 0xFF, lbmp::set_bytes(h), h->stream), "poison");
-        LBMP_CUDA(cudaMemsetAsync(h->g[d], 0xFF, lbmp::set_bytes(h), h->stream), "poison");
+        LBMP_CUDA(cudaMemsetAsync(h->g[d], 0xFF, lbmp::gset_bytes(h), h->stream), "poison");
         return LBMP_OK;
     }
     case LBMP_OPT_TEST_STALL:
@@ -402,14 +410,14 @@ int lbmp_get_state(lbmp_handle* h, double* f, double* g, double* phi)
 {
     int rc = check_handle(h);
     if (rc) return rc;
-    const size_t n = (size_t)h->Q * (size_t)h->N;
+    const size_t n = (size_t)h->Q * (size_t)h->N, ng = (size_t)h->Qg * (size_t)h->N;
     double *df = nullptr, *dg = nullptr;
     cudaError_t e = cudaSuccess;
     if (f) e = cudaMallocAsync(&df, n * sizeof(double), h->stream);
-    if (e == cudaSuccess && g) e = cudaMallocAsync(&dg, n * sizeof(double), h->stream);
+    if (e == cudaSuccess && g) e = cudaMallocAsync(&dg, ng * sizeof(double), h->stream);
     if (e == cudaSuccess) e = lbmp::launch_get_state(h, df, dg);
     if (e == cudaSuccess && f) e = cudaMemcpyAsync(f, df, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess && g) e = cudaMemcpyAsync(g, dg, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && g) e = cudaMemcpyAsync(g, dg, ng * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (df) cudaFreeAsync(df, h->stream);
     if (dg) cudaFreeAsync(dg, h->stream);
     if (e == cudaSuccess && phi) {
@@ -433,12 +441,12 @@ int lbmp_set_state(lbmp_handle* h, const double* f, const double* g)
     int rc = check_handle(h);
     if (rc) return rc;
     if (!f || !g) return fail(LBMP_ERR_INVALID_ARG, "null state array");
-    const size_t n = (size_t)h->Q * (size_t)h->N;
+    const size_t n = (size_t)h->Q * (size_t)h->N, ng = (size_t)h->Qg * (size_t)h->N;
     double *df = nullptr, *dg = nullptr;
     cudaError_t e = cudaMallocAsync(&df, n * sizeof(double), h->stream);
-    if (e == cudaSuccess) e = cudaMallocAsync(&dg, n * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dg, ng * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(df, f, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dg, g, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dg, g, ng * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->red_out + kStatusSlot, 0, sizeof(double), h->stream);
     if (e == cudaSuccess) e = lbmp::launch_set_state(h, df, dg);
     if (e == cudaSuccess) e = lbmp::launch_mass(h, h->red_out + 12);
@@ -452,7 +460,7 @@ int lbmp_set_state(lbmp_handle* h, const double* f, const double* g)
 size_t lbmp_state_bytes(const lbmp_handle* h)
 {
     if (!h) return 0;
-    return 2 * lbmp::set_bytes(h);
+    return lbmp::set_bytes(h) + lbmp::gset_bytes(h) + lbmp::phiu_bytes(h);
 }
 
 int lbmp_upload(lbmp_handle* h, const void* host, size_t bytes)
@@ -460,10 +468,11 @@ int lbmp_upload(lbmp_handle* h, const void* host, size_t bytes)
     int rc = check_handle(h);
     if (rc) return rc;
     if (!host || bytes != lbmp_state_bytes(h)) return fail(LBMP_ERR_INVALID_ARG, "bad upload size");
-    const size_t half = bytes / 2;
-    LBMP_CUDA(cudaMemcpyAsync(h->f[h->parity], host, half, cudaMemcpyHostToDevice, h->stream), "upload f");
-    LBMP_CUDA(cudaMemcpyAsync(h->g[h->parity], (const char*)host + half, half, cudaMemcpyHostToDevice, h->stream),
-              "upload g");
+    const size_t nf = lbmp::set_bytes(h), ng = lbmp::gset_bytes(h), nu = lbmp::phiu_bytes(h);
+    const char* src = (const char*)host;
+    LBMP_CUDA(cudaMemcpyAsync(h->f[h->parity], src, nf, cudaMemcpyHostToDevice, h->stream), "upload f");
+    LBMP_CUDA(cudaMemcpyAsync(h->g[h->parity], src + nf, ng, cudaMemcpyHostToDevice, h->stream), "upload g");
+    if (nu) LBMP_CUDA(cudaMemcpyAsync(h->phiu, src + nf + ng, nu, cudaMemcpyHostToDevice, h->stream), "upload phi u");
     return LBMP_OK;
 }
 
@@ -472,10 +481,11 @@ int lbmp_download(lbmp_handle* h, void* host, size_t bytes)
     int rc = check_handle(h);
     if (rc) return rc;
     if (!host || bytes != lbmp_state_bytes(h)) return fail(LBMP_ERR_INVALID_ARG, "bad download size");
-    const size_t half = bytes / 2;
-    LBMP_CUDA(cudaMemcpyAsync(host, h->f[h->parity], half, cudaMemcpyDeviceToHost, h->stream), "download f");
-    LBMP_CUDA(cudaMemcpyAsync((char*)host + half, h->g[h->parity], half, cudaMemcpyDeviceToHost, h->stream),
-              "download g");
+    const size_t nf = lbmp::set_bytes(h), ng = lbmp::gset_bytes(h), nu = lbmp::phiu_bytes(h);
+    char* dst = (char*)host;
+    LBMP_CUDA(cudaMemcpyAsync(dst, h->f[h->parity], nf, cudaMemcpyDeviceToHost, h->stream), "download f");
+    LBMP_CUDA(cudaMemcpyAsync(dst + nf, h->g[h->parity], ng, cudaMemcpyDeviceToHost, h->stream), "download g");
+    if (nu) LBMP_CUDA(cudaMemcpyAsync(dst + nf + ng, h->phiu, nu, cudaMemcpyDeviceToHost, h->stream), "download phi u");
     return LBMP_OK;
 }
 

@@ -56,6 +56,32 @@ enum : unsigned {
     kFlagWeLight = 1u << 0,
     kFlagDynamicVisc = 1u << 1,
     kFlagUniformForce = 1u << 2,
+    kFlagPhaseReduced = 1u << 3,
+};
+
+// Lattice of the phase field g.  PR = false: the flow lattice with the
+// second-order equilibrium.  PR = true: the rest and face directions only
+// (D3Q7: weights 1/4, 1/8, cs2 = 1/4; D2Q5: 1/3, 1/6, cs2 = 1/3), with the
+// first-order equilibrium w phi (1 + c.u/cs2) and the correction term
+// C_bar = lambda (w/cs2) c . d/dt(phi u) that Sec. 2.2 gives for it.  Slot r
+// holds the flow-lattice direction full(r); the slots keep the canonical
+// order, so opposite(r) = Q-1-r.
+template <int D, bool PR>
+struct PhaseLat {
+    static constexpr int Q = PR ? 2 * D + 1 : Lat<D>::Q;
+    static constexpr int C = Q / 2;
+    __host__ __device__ static constexpr int full(int r)
+    {
+        if (!PR) return r;
+        if (D == 3) return r == 3 ? 13 : (r < 3 ? (r == 0 ? 4 : (r == 1 ? 10 : 12)) : (r == 4 ? 14 : (r == 5 ? 16 : 22)));
+        return r == 2 ? 4 : (r < 2 ? (r == 0 ? 1 : 3) : (r == 3 ? 5 : 7));
+    }
+    __host__ __device__ static constexpr float w(int r)
+    {
+        if (!PR) return Lat<D>::w(r);
+        return r == C ? (D == 3 ? 0.25f : 1.f / 3.f) : (D == 3 ? 0.125f : 1.f / 6.f);
+    }
+    static constexpr float inv_cs2 = (PR && D == 3) ? 4.f : 3.f;
 };
 
 // Everything a step kernel needs, by value (fits the kernel-parameter space).
@@ -68,6 +94,7 @@ struct DevParams {
     float beta2, kappa;     // 2 beta, kappa of the chemical potential
     float inv_tau_phi;      // 1/tau_bar_phi
     float lam_sharp;        // lambda_phi * 4 / W
+    float lam_corr;         // lambda_phi / cs2 of the phase lattice (reduced phase lattice)
     float g_accel, force_x;
     unsigned flags;
     int* status;            // device status word of the handle (kStatus* bits), or null
@@ -149,6 +176,23 @@ __device__ __forceinline__ long long pull_index(const DevParams& p, int a, int x
     return (long long)dir * p.N + c;
 }
 
+// pull_src / push_dst for slot r of the phase lattice (slot of the opposite
+// direction across a wall)
+template <int D, bool PR>
+__device__ __forceinline__ long long pull_src_g(const DevParams& p, int r, int x, int y, int z, long long self,
+                                                int& slot)
+{
+    if constexpr (!PR) {
+        return pull_src<D>(p, r, x, y, z, self, slot);
+    } else {
+        const int a = PhaseLat<D, true>::full(r);
+        int dir;
+        const long long c = pull_src<D>(p, a, x, y, z, self, dir);
+        slot = dir == a ? r : PhaseLat<D, true>::Q - 1 - r;
+        return c;
+    }
+}
+
 // Inverse of pull_src: the slot (cell, a) written by the cell (x,y,z) is read
 // as population dir of the returned cell (downstream x + c_a, or the cell
 // itself in the opposite direction when x + c_a lies across a wall).
@@ -182,6 +226,21 @@ __device__ __forceinline__ long long push_dst(const DevParams& p, int a, int x, 
             yd = yd < 0 ? yd + p.ny : yd - p.ny;
         }
         return (long long)yd * p.nx + xd;
+    }
+}
+
+template <int D, bool PR>
+__device__ __forceinline__ long long push_dst_g(const DevParams& p, int r, int x, int y, int z, long long self,
+                                                int& slot)
+{
+    if constexpr (!PR) {
+        return push_dst<D>(p, r, x, y, z, self, slot);
+    } else {
+        const int a = PhaseLat<D, true>::full(r);
+        int dir;
+        const long long c = push_dst<D>(p, a, x, y, z, self, dir);
+        slot = dir == a ? r : PhaseLat<D, true>::Q - 1 - r;
+        return c;
     }
 }
 
@@ -449,6 +508,32 @@ __device__ __forceinline__ void phi_sum(const Get& get, float& hi, float& lo)
     const float lsum = (l.x + l.y) + e;
     hi = t + lsum;
     lo = lsum - (hi - t);
+}
+
+// phi of the reduced phase lattice: the rest value, then the face pairs
+// (equal weights, so TwoSum rather than Fast2Sum), as a compensated pair
+template <int D, class Get>
+__device__ __forceinline__ void phi_sum_red(const Get& get, float& hi, float& lo)
+{
+    constexpr int Q = 2 * D + 1;
+    float2 h = f2(get(D), 0.f), l = f2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < D; ++k) two_sum2(h, l, f2(get(k), get(Q - 1 - k)));
+    const float t = h.x + h.y;
+    const float bb = t - h.x;
+    const float e = (h.x - (t - bb)) + (h.y - bb);
+    const float lsum = (l.x + l.y) + e;
+    hi = t + lsum;
+    lo = lsum - (hi - t);
+}
+
+template <int D, bool PR, class Get>
+__device__ __forceinline__ void phi_sum_phase(const Get& get, float& hi, float& lo)
+{
+    if constexpr (PR)
+        phi_sum_red<D>(get, hi, lo);
+    else
+        phi_sum<D>(get, hi, lo);
 }
 
 // Isotropic differences (Sec. 2.2) from the Q neighbour values
@@ -798,11 +883,31 @@ struct DhStrided {
     __device__ __forceinline__ float operator[](int a) const { return base[a * stride]; }
 };
 
-template <int D, class GSrc, class Out, class DH>
+// Reduced phase lattice: d/dt(phi u) of cell i as the backward difference
+// phi u - (phi u of the previous step), and this step's phi u stored in its
+// place ([k][cell]; each cell reads and writes only its own entries).
+template <int D>
+__device__ __forceinline__ void phiu_step(const DevParams& p, const CellState& s, float* __restrict__ phiu,
+                                          long long i, float d[3])
+{
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const float v = s.phi * s.u[k];
+        d[k] = v - phiu[k * p.N + i];
+        phiu[k * p.N + i] = v;
+    }
+    if (D == 2) d[2] = 0.f;
+}
+
+// PR: g on the reduced phase lattice (gin / gout index its slots), with
+// dphiu = d/dt(phi u) of the cell for the correction term.
+template <int D, bool PR = false, class GSrc, class Out, class DH>
 __device__ __forceinline__ void collide_outputs(const DevParams& p, const CellState& s, const DH& dh,
                                                 const FlowMoments& m, const GSrc& gin, float gsum_hi,
-                                                float gsum_lo, const Out& fout, const Out& gout)
+                                                float gsum_lo, const Out& fout, const Out& gout,
+                                                const float* dphiu = nullptr)
 {
+    static_assert(!(PR && Out::kTotal), "the reduced phase lattice is stored in FP32 only");
     constexpr int Q = Lat<D>::Q;
     constexpr int C = Q / 2;
     const float2 rcs2 = f2(s.rcs2, s.rcs2);
@@ -844,17 +949,46 @@ __device__ __forceinline__ void collide_outputs(const DevParams& p, const CellSt
         // f'* = rho cs2 (E - w + dh) + w p_h + Xi/2
         const float wph = w * s.ph;
         const float2 fo = fma2(rcs2, add2(ew, f2(dh[a], dh[b])), fma2(f2(0.5f, 0.5f), xi, f2(wph, wph)));
-        // g* = g + (phi Gamma - g)/tau + w (c.n) lambda 4 phi (1-phi)/W
-        const float cn0 = cx * s.n[0] + cy * s.n[1] + cz * s.n[2];
-        const float ws = w * s.sharp;
-        const float2 gi = f2(gin(a), gin(b));
-        const float2 go = fma2(f2(ws, ws), mul2(pm1, f2(cn0, cn0)), fma2(itau, fma2(phi2, wgd, neg2(gi)), gi));
         fout(a, fo.x);
         fout(b, fo.y);
-        gout(a, go.x);
-        gout(b, go.y);
         fs = add2(fs, fo);
-        two_sum2(gs, gl, go);
+        if constexpr (!PR) {
+            // g* = g + (phi Gamma - g)/tau + w (c.n) lambda 4 phi (1-phi)/W
+            const float cn0 = cx * s.n[0] + cy * s.n[1] + cz * s.n[2];
+            const float ws = w * s.sharp;
+            const float2 gi = f2(gin(a), gin(b));
+            const float2 go =
+                fma2(f2(ws, ws), mul2(pm1, f2(cn0, cn0)), fma2(itau, fma2(phi2, wgd, neg2(gi)), gi));
+            gout(a, go.x);
+            gout(b, go.y);
+            two_sum2(gs, gl, go);
+        }
+    }
+    constexpr int GC = PhaseLat<D, PR>::C;  // rest slot of g
+    if constexpr (PR) {
+        // g* = g + (g_eq - g)/tau + w c.(lambda 4 phi(1-phi)/W n + lambda/cs2 d/dt(phi u)),
+        // g_eq = w phi (1 + c.u/cs2): first-order equilibrium, sharpening source
+        // and correction term (Sec. 2.2), lanes (r, opposite)
+        constexpr float ics = PhaseLat<D, true>::inv_cs2;
+        float qv[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) qv[i] = fmaf(p.lam_corr, dphiu[i], s.sharp * s.n[i]);
+#pragma unroll
+        for (int r = 0; r < GC; ++r) {
+            const int a = PhaseLat<D, true>::full(r);
+            const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
+            const float w = PhaseLat<D, true>::w(r);
+            const float cu = cx * s.u[0] + cy * s.u[1] + cz * s.u[2];
+            const float cq = cx * qv[0] + cy * qv[1] + cz * qv[2];
+            const float wphi = w * s.phi;
+            const float t = wphi * ics * cu;
+            const float2 geq = fma2(pm1, f2(t, t), f2(wphi, wphi));
+            const float2 gi = f2(gin(r), gin(2 * GC - r));
+            const float2 go = fma2(f2(w, w), mul2(pm1, f2(cq, cq)), fma2(itau, add2(geq, neg2(gi)), gi));
+            gout(r, go.x);
+            gout(2 * GC - r, go.y);
+            two_sum2(gs, gl, go);
+        }
     }
     // target totals: P + u.G (flow) and the incoming sum (phase field); the
     // rest populations take the difference (conservation identities above),
@@ -867,7 +1001,7 @@ __device__ __forceinline__ void collide_outputs(const DevParams& p, const CellSt
         float t = gs.x + gs.y;  // combine the lanes exactly
         const float bb = t - gs.x;
         const float e = (gs.x - (t - bb)) + (gs.y - bb);
-        gout(C, (gsum_hi - t) + (gsum_lo - (gl.x + gl.y + e)));
+        gout(GC, (gsum_hi - t) + (gsum_lo - (gl.x + gl.y + e)));
     }
 }
 

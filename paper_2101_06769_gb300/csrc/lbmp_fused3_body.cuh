@@ -303,7 +303,8 @@ LaunchCfg g_cfg;
 
 #if LBMP_FUSED3_WITH_COMMON
 // every domain has a fused kernel (FP32 and shifted 16-bit, D3Q27 and D2Q9)
-bool fused_supported(const lbmp_handle*) { return true; }
+// but the reduced phase lattice, which runs the reference pair
+bool fused_supported(const lbmp_handle* h) { return !h->reduced; }
 
 __global__ void batch_epilogue_kernel(BatchDomain* table, int ndom)
 {

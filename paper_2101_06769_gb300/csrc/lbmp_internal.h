@@ -10,6 +10,8 @@
 struct lbmp_handle {
     lbmp_grid grid;
     int D, Q;
+    int Qg;            // phase-field populations: Q, or 2D+1 on the reduced phase lattice
+    bool reduced;      // LBMP_FLAG_PHASE_REDUCED
     lbmp_params params;
     lbmp_derived der;
     lbmp::DevParams dp;
@@ -21,6 +23,7 @@ struct lbmp_handle {
     float* f[2];
     float* g[2];
     float* phi;        // phi = sum g as hi [0, N) + lo [N, 2N), refreshed by the phi pass
+    float* phiu;       // reduced phase lattice: phi u of the previous step, [k < D][cell]; else null
     int parity;        // f[parity], g[parity] hold the current state
     long step;
     int kernel;        // LBMP_OPT_KERNEL: 0 default, 1 reference pair, 2 bulk-copy staging
@@ -78,9 +81,18 @@ inline size_t set_bytes(const lbmp_handle* h)
     if (h->params.storage == LBMP_FP32) return sizeof(float) * Q * N;
     return sizeof(float) * N + sizeof(unsigned short) * (Q - 1) * N;  // reference + 16-bit codes
 }
+// bytes of one phase-field population set (equals set_bytes but on the reduced phase lattice)
+inline size_t gset_bytes(const lbmp_handle* h)
+{
+    if (h->reduced) return sizeof(float) * (size_t)h->Qg * (size_t)h->N;
+    return set_bytes(h);
+}
+// bytes of the stored previous phi u (reduced phase lattice)
+inline size_t phiu_bytes(const lbmp_handle* h) { return h->reduced ? sizeof(float) * h->D * (size_t)h->N : 0; }
 
 // kernel launchers (return cudaError_t of the launch)
 cudaError_t launch_phi_pass(lbmp_handle* h);
+cudaError_t launch_phiu_reset(lbmp_handle* h);  // reduced phase lattice: previous phi u := current
 cudaError_t launch_step_simple(lbmp_handle* h);
 cudaError_t launch_step_fused3(lbmp_handle* h);        // FP32 D3Q27, 32 x 4 tiles
 cudaError_t launch_step_fused3_t16x8(lbmp_handle* h);  // FP32 D3Q27, 16 x 8 tiles

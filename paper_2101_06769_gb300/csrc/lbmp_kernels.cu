@@ -22,7 +22,7 @@ __device__ __forceinline__ float pulled_value(const DevParams& p, const Pop<D, S
     return set.load(dir, c);
 }
 
-template <int D, class St>
+template <int D, class St, bool PR>
 __global__ void phi_pass_kernel(DevParams p, Pop<D, St> g, float* __restrict__ phi)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -39,17 +39,25 @@ __global__ void phi_pass_kernel(DevParams p, Pop<D, St> g, float* __restrict__ p
             },
             hi, lo);
     } else {
-        phi_sum<D>([&](int a) { return pulled_value<D, St>(p, g, a, x, y, z, i); }, hi, lo);
+        phi_sum_phase<D, PR>(
+            [&](int r) {
+                int slot;
+                const long long c = pull_src_g<D, PR>(p, r, x, y, z, i, slot);
+                return g.load(slot, c);
+            },
+            hi, lo);
     }
     phi[i] = hi;  // phi = sum_a g_a (Sec. 2.2), as hi + lo
     phi[p.N + i] = lo;
 }
 
 // ----------------------------------------------------- reference step
-template <int D, class St>
+// phiu (reduced phase lattice): phi u of the previous step per cell, [k][cell],
+// read and replaced by this step's value (each cell touches only its own)
+template <int D, class St, bool PR>
 __global__ void __launch_bounds__(128) step_simple_kernel(DevParams p, Pop<D, St> fin, Pop<D, St> gin,
                                                           Pop<D, St> fout, Pop<D, St> gout,
-                                                          const float* __restrict__ phi)
+                                                          const float* __restrict__ phi, float* __restrict__ phiu)
 {
     constexpr int Q = Lat<D>::Q;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -73,10 +81,20 @@ __global__ void __launch_bounds__(128) step_simple_kernel(DevParams p, Pop<D, St
     CellState s;
     float dh[27];
     flow_collide<D>(p, nh[Q / 2], grad, lap, m, s, dh);
-    float gr[Q];
+    constexpr int QG = PhaseLat<D, PR>::Q;
+    float gr[QG];
 #pragma unroll
-    for (int a = 0; a < Q; ++a) gr[a] = pulled_value<D, St>(p, gin, a, x, y, z, i);
-    if constexpr (St::shifted) {
+    for (int r = 0; r < QG; ++r) {
+        int slot;
+        const long long c = pull_src_g<D, PR>(p, r, x, y, z, i, slot);
+        gr[r] = gin.load(slot, c);
+    }
+    if constexpr (PR) {
+        float dphiu[3];
+        phiu_step<D>(p, s, phiu, i, dphiu);
+        collide_outputs<D, true>(p, s, DhArray{dh}, m, GFromArray{gr}, nh[Q / 2], nl[Q / 2], SoAOut{fout.base + i, p.N},
+                                 SoAOut{gout.base + i, p.N}, dphiu);
+    } else if constexpr (St::shifted) {
         float off_f, off_g;
         rest_offsets<D, St>(p, s, dh, GFromArray{gr}, off_f, off_g);
         collide_outputs<D>(p, s, DhArray{dh}, m, GFromArray{gr}, nh[Q / 2], nl[Q / 2],
@@ -90,19 +108,20 @@ __global__ void __launch_bounds__(128) step_simple_kernel(DevParams p, Pop<D, St
 
 static unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
 
-// Calls F::template run<D, St>() for the handle's lattice and storage form.
+// Calls F::template run<D, St, PR>() for the handle's lattice, storage form
+// and phase lattice (PR: reduced, FP32 storage only).
 template <class F>
 static cudaError_t dispatch(const lbmp_handle* h, const F& f)
 {
     const int st = h->params.storage;
     if (h->D == 3) {
-        if (st == LBMP_FP16_SHIFTED) return f.template run<3, StoreF16>();
-        if (st == LBMP_BF16_SHIFTED) return f.template run<3, StoreBF16>();
-        return f.template run<3, StoreF32>();
+        if (st == LBMP_FP16_SHIFTED) return f.template run<3, StoreF16, false>();
+        if (st == LBMP_BF16_SHIFTED) return f.template run<3, StoreBF16, false>();
+        return h->reduced ? f.template run<3, StoreF32, true>() : f.template run<3, StoreF32, false>();
     }
-    if (st == LBMP_FP16_SHIFTED) return f.template run<2, StoreF16>();
-    if (st == LBMP_BF16_SHIFTED) return f.template run<2, StoreBF16>();
-    return f.template run<2, StoreF32>();
+    if (st == LBMP_FP16_SHIFTED) return f.template run<2, StoreF16, false>();
+    if (st == LBMP_BF16_SHIFTED) return f.template run<2, StoreBF16, false>();
+    return h->reduced ? f.template run<2, StoreF32, true>() : f.template run<2, StoreF32, false>();
 }
 
 template <int D, class St>
@@ -113,12 +132,12 @@ static Pop<D, St> pop_of(const lbmp_handle* h, float* base)
 
 struct PhiPassL {
     lbmp_handle* h;
-    template <int D, class St>
+    template <int D, class St, bool PR>
     cudaError_t run() const
     {
         const int B = 256;
-        phi_pass_kernel<D, St><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, pop_of<D, St>(h, h->g[h->parity]),
-                                                                       h->phi);
+        phi_pass_kernel<D, St, PR><<<grid_for(h->N, B), B, 0, h->stream>>>(
+            h->dp, pop_of<D, St>(h, h->g[h->parity]), h->phi);
         return cudaGetLastError();
     }
 };
@@ -127,14 +146,14 @@ cudaError_t launch_phi_pass(lbmp_handle* h) { return dispatch(h, PhiPassL{h}); }
 
 struct StepSimpleL {
     lbmp_handle* h;
-    template <int D, class St>
+    template <int D, class St, bool PR>
     cudaError_t run() const
     {
         const int B = 128;
         const int s = h->parity, d = 1 - h->parity;
-        step_simple_kernel<D, St><<<grid_for(h->N, B), B, 0, h->stream>>>(
+        step_simple_kernel<D, St, PR><<<grid_for(h->N, B), B, 0, h->stream>>>(
             h->dp, pop_of<D, St>(h, h->f[s]), pop_of<D, St>(h, h->g[s]), pop_of<D, St>(h, h->f[d]),
-            pop_of<D, St>(h, h->g[d]), h->phi);
+            pop_of<D, St>(h, h->g[d]), h->phi, h->phiu);
         return cudaGetLastError();
     }
 };
@@ -145,6 +164,11 @@ cudaError_t launch_step_simple(lbmp_handle* h)
     if (e != cudaSuccess) return e;
     return dispatch(h, StepSimpleL{h});
 }
+
+// rho, u and p_h of one cell as the step computes them (defined below)
+template <int D, class St>
+__device__ void cell_macro(const DevParams& p, const Pop<D, St>& f, const float* __restrict__ phi, int x, int y,
+                           int z, long long i, float& rho, float u[3], float& ph);
 
 // ---------------------------------------------------- initial conditions
 // splitmix64 (Steele, Lea & Flood 2014): output of the (counter+1)-th call of
@@ -169,7 +193,7 @@ __device__ __forceinline__ double tanh_prof(double d, double W) { return 0.5 * (
 // Initial conditions (reading A18): tanh phi profiles, f' = f'_eq(p, rho, u),
 // g = g_eq(phi, u), written to the FP32 slots the next step pulls from, or
 // (cf != null) as canonical FP64 arrays [a][cell] for the shifted encoder.
-template <int D>
+template <int D, bool PR>
 __global__ void init_kernel(DevParams p, InitArgs A, float* __restrict__ f, float* __restrict__ g,
                             double* __restrict__ cf, double* __restrict__ cg)
 {
@@ -268,9 +292,38 @@ __global__ void init_kernel(DevParams p, InitArgs A, float* __restrict__ f, floa
         } else {
             const long long slot = pull_index<D>(p, a, x, y, z, i);
             f[slot] = (float)fe;
-            g[slot] = (float)ge;
+            if (!PR) g[slot] = (float)ge;
         }
     }
+    if constexpr (PR) {
+        // reduced phase lattice: first-order equilibrium w phi (1 + c.u/cs2) (Sec. 2.2)
+        constexpr int C = PhaseLat<D, true>::C;
+#pragma unroll
+        for (int r = 0; r < PhaseLat<D, true>::Q; ++r) {
+            const int a = PhaseLat<D, true>::full(r);
+            const double w = (r == C) ? (D == 3 ? 0.25 : 1.0 / 3.0) : (D == 3 ? 0.125 : 1.0 / 6.0);
+            const double cu = Lat<D>::cx(a) * u[0] + Lat<D>::cy(a) * u[1] + Lat<D>::cz(a) * u[2];
+            int slot;
+            const long long c = pull_src_g<D, true>(p, r, x, y, z, i, slot);
+            g[(long long)slot * p.N + c] = (float)(w * phi * (1.0 + cu * (D == 3 ? 4.0 : 3.0)));
+        }
+    }
+}
+
+// Reduced phase lattice: phi u of every cell from the current state (the u
+// the next step's closure computes), the previous value before the first step
+// after init / set_state.  Needs the phi pass first.
+template <int D>
+__global__ void phiu_reset_kernel(DevParams p, Pop<D, StoreF32> f, const float* __restrict__ phi,
+                                  float* __restrict__ phiu)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= p.N) return;
+    int x, y, z;
+    cell_xyz(p, i, x, y, z);
+    float rho, u[3], ph;
+    cell_macro<D, StoreF32>(p, f, phi, x, y, z, i, rho, u, ph);
+    for (int k = 0; k < D; ++k) phiu[k * p.N + i] = phi[i] * u[k];
 }
 
 cudaError_t launch_init(lbmp_handle* h, int case_id, const double* args, unsigned long long seed)
@@ -287,13 +340,19 @@ cudaError_t launch_init(lbmp_handle* h, int case_id, const double* args, unsigne
     A.case_id = case_id;
     const int B = 128;
     if (h->params.storage == LBMP_FP32) {
-        if (h->D == 3)
-            init_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, A, h->f[h->parity], h->g[h->parity],
-                                                                   nullptr, nullptr);
+        float *f = h->f[h->parity], *g = h->g[h->parity];
+        const unsigned grid = grid_for(h->N, B);
+        if (h->D == 3 && h->reduced)
+            init_kernel<3, true><<<grid, B, 0, h->stream>>>(h->dp, A, f, g, nullptr, nullptr);
+        else if (h->D == 3)
+            init_kernel<3, false><<<grid, B, 0, h->stream>>>(h->dp, A, f, g, nullptr, nullptr);
+        else if (h->reduced)
+            init_kernel<2, true><<<grid, B, 0, h->stream>>>(h->dp, A, f, g, nullptr, nullptr);
         else
-            init_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, A, h->f[h->parity], h->g[h->parity],
-                                                                   nullptr, nullptr);
-        return cudaGetLastError();
+            init_kernel<2, false><<<grid, B, 0, h->stream>>>(h->dp, A, f, g, nullptr, nullptr);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && h->reduced) e = launch_phiu_reset(h);
+        return e;
     }
     // shifted storage: canonical FP64 state first, then the per-cell encoder
     const size_t n = (size_t)h->Q * (size_t)h->N;
@@ -301,9 +360,9 @@ cudaError_t launch_init(lbmp_handle* h, int case_id, const double* args, unsigne
     cudaError_t e = cudaMallocAsync(&c, 2 * n * sizeof(double), h->stream);
     if (e != cudaSuccess) return e;
     if (h->D == 3)
-        init_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, A, nullptr, nullptr, c, c + n);
+        init_kernel<3, false><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, A, nullptr, nullptr, c, c + n);
     else
-        init_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, A, nullptr, nullptr, c, c + n);
+        init_kernel<2, false><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, A, nullptr, nullptr, c, c + n);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_set_state(h, c, c + n);
     cudaFreeAsync(c, h->stream);
@@ -312,7 +371,7 @@ cudaError_t launch_init(lbmp_handle* h, int case_id, const double* args, unsigne
 
 // ------------------------------------------------------ state exchange
 // canonical (post-streaming, [a][cell]) FP64 <- stored state
-template <int D, class St>
+template <int D, class St, bool PR>
 __global__ void get_state_kernel(DevParams p, Pop<D, St> f, Pop<D, St> g, double* cf, double* cg)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -320,15 +379,18 @@ __global__ void get_state_kernel(DevParams p, Pop<D, St> f, Pop<D, St> g, double
     int x, y, z;
     cell_xyz(p, i, x, y, z);
 #pragma unroll
-    for (int a = 0; a < Lat<D>::Q; ++a) {
-        const long long c = (long long)a * p.N + i;
-        if (cf) cf[c] = (double)pulled_value<D, St>(p, f, a, x, y, z, i);
-        if (cg) cg[c] = (double)pulled_value<D, St>(p, g, a, x, y, z, i);
+    for (int a = 0; a < Lat<D>::Q; ++a)
+        if (cf) cf[(long long)a * p.N + i] = (double)pulled_value<D, St>(p, f, a, x, y, z, i);
+#pragma unroll
+    for (int r = 0; r < PhaseLat<D, PR>::Q; ++r) {
+        int slot;
+        const long long c = pull_src_g<D, PR>(p, r, x, y, z, i, slot);
+        if (cg) cg[(long long)r * p.N + i] = (double)g.load(slot, c);
     }
 }
 
 // stored FP32 state <- canonical FP64 (one thread per reading cell)
-template <int D>
+template <int D, bool PR>
 __global__ void set_state_f32_kernel(DevParams p, float* f, float* g, const double* cf, const double* cg)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -336,11 +398,13 @@ __global__ void set_state_f32_kernel(DevParams p, float* f, float* g, const doub
     int x, y, z;
     cell_xyz(p, i, x, y, z);
 #pragma unroll
-    for (int a = 0; a < Lat<D>::Q; ++a) {
-        const long long slot = pull_index<D>(p, a, x, y, z, i);
-        const long long c = (long long)a * p.N + i;
-        f[slot] = (float)cf[c];
-        g[slot] = (float)cg[c];
+    for (int a = 0; a < Lat<D>::Q; ++a)
+        f[pull_index<D>(p, a, x, y, z, i)] = (float)cf[(long long)a * p.N + i];
+#pragma unroll
+    for (int r = 0; r < PhaseLat<D, PR>::Q; ++r) {
+        int slot;
+        const long long c = pull_src_g<D, PR>(p, r, x, y, z, i, slot);
+        g[(long long)slot * p.N + c] = (float)cg[(long long)r * p.N + i];
     }
 }
 
@@ -390,7 +454,7 @@ __global__ void set_state_shifted_kernel(DevParams p, Pop<D, St> f, Pop<D, St> g
 struct SetStateL {
     lbmp_handle* h;
     const double *cf, *cg;
-    template <int D, class St>
+    template <int D, class St, bool PR>
     cudaError_t run() const
     {
         const int B = 128;
@@ -399,7 +463,7 @@ struct SetStateL {
             set_state_shifted_kernel<D, St><<<grid_for(h->N, B), B, 0, h->stream>>>(
                 h->dp, pop_of<D, St>(h, f), pop_of<D, St>(h, g), cf, cg);
         else
-            set_state_f32_kernel<D><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, f, g, cf, cg);
+            set_state_f32_kernel<D, PR><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, f, g, cf, cg);
         return cudaGetLastError();
     }
 };
@@ -407,11 +471,11 @@ struct SetStateL {
 struct GetStateL {
     lbmp_handle* h;
     double *cf, *cg;
-    template <int D, class St>
+    template <int D, class St, bool PR>
     cudaError_t run() const
     {
         const int B = 128;
-        get_state_kernel<D, St><<<grid_for(h->N, B), B, 0, h->stream>>>(
+        get_state_kernel<D, St, PR><<<grid_for(h->N, B), B, 0, h->stream>>>(
             h->dp, pop_of<D, St>(h, h->f[h->parity]), pop_of<D, St>(h, h->g[h->parity]), cf, cg);
         return cudaGetLastError();
     }
@@ -419,7 +483,24 @@ struct GetStateL {
 
 cudaError_t launch_set_state(lbmp_handle* h, const double* dev_f, const double* dev_g)
 {
-    return dispatch(h, SetStateL{h, dev_f, dev_g});
+    cudaError_t e = dispatch(h, SetStateL{h, dev_f, dev_g});
+    if (e == cudaSuccess && h->reduced) e = launch_phiu_reset(h);
+    return e;
+}
+
+cudaError_t launch_phiu_reset(lbmp_handle* h)
+{
+    if (!h->reduced) return cudaSuccess;
+    cudaError_t e = launch_phi_pass(h);
+    if (e != cudaSuccess) return e;
+    const int B = 128;
+    if (h->D == 3)
+        phiu_reset_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, pop_of<3, StoreF32>(h, h->f[h->parity]),
+                                                                     h->phi, h->phiu);
+    else
+        phiu_reset_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, pop_of<2, StoreF32>(h, h->f[h->parity]),
+                                                                     h->phi, h->phiu);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_get_state(lbmp_handle* h, double* dev_f, double* dev_g)
@@ -584,7 +665,7 @@ struct ObsL {
     lbmp_handle* h;
     double* out;
     bool full;  // false: mass and the other reductions only
-    template <int D, class St>
+    template <int D, class St, bool>
     cudaError_t run() const
     {
         const Pop<D, St> f = pop_of<D, St>(h, h->f[h->parity]);

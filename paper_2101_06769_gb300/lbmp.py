@@ -17,7 +17,7 @@ D2Q9, D3Q27 = 0, 1
 FP32, FP16_SHIFTED, BF16_SHIFTED = 0, 1, 2
 CASE = {"rt": 0, "drop_static": 1, "flat": 2, "poiseuille": 3, "drop_sheet": 4, "shear_wave": 5,
         "uniform": 6}
-FLAG_WE_LIGHT, FLAG_DYNAMIC_VISC, FLAG_UNIFORM_FORCE = 1, 2, 4
+FLAG_WE_LIGHT, FLAG_DYNAMIC_VISC, FLAG_UNIFORM_FORCE, FLAG_PHASE_REDUCED = 1, 2, 4, 8
 OPT_KERNEL, OPT_CHUNK, OPT_CTAS_PER_SM, OPT_WAIT_LIMIT_NS, OPT_TEST_STALL, OPT_TILE = 0, 1, 2, 3, 4, 5
 OPT_TEST_POISON = 6
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5: "UNSTABLE",
@@ -139,6 +139,8 @@ class Domain:
         self.storage = int(params.get("storage", FP32))
         self.dims = tuple(int(v) for v in dims)
         self.Q = 27 if D == 3 else 9
+        # phase-field populations: 2D+1 on the reduced phase lattice (D3Q7 / D2Q5)
+        self.Qg = 2 * D + 1 if int(params.get("flags", 0)) & FLAG_PHASE_REDUCED else self.Q
         self.N = self.dims[0] * self.dims[1] * self.dims[2]
         g = Grid(self.dims[0], self.dims[1], self.dims[2], (C.c_int * 3)(*[int(v) for v in periodic]))
         h = C.c_void_p()
@@ -154,6 +156,10 @@ class Domain:
     def shape(self):
         nx, ny, nz = self.dims
         return (self.Q, nz, ny, nx)
+
+    @property
+    def gshape(self):
+        return (self.Qg,) + self.shape[1:]
 
     def close(self):
         if getattr(self, "_h", None):
@@ -207,7 +213,7 @@ class Domain:
 
     def get_state(self):
         f = np.empty(self.shape)
-        g = np.empty(self.shape)
+        g = np.empty(self.gshape)
         phi = np.empty(self.shape[1:])
         _check(load().lbmp_get_state(self._h, f.ctypes.data, g.ctypes.data, phi.ctypes.data))
         return f, g, phi
@@ -215,7 +221,7 @@ class Domain:
     def set_state(self, f, g):
         f = np.ascontiguousarray(f, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
-        assert f.size == self.Q * self.N and g.size == self.Q * self.N
+        assert f.size == self.Q * self.N and g.size == self.Qg * self.N
         _check(load().lbmp_set_state(self._h, f.ctypes.data, g.ctypes.data))
 
     def state_bytes(self):
