@@ -37,6 +37,9 @@ WORKLOADS = _workloads()
 BYTES_PER_CELL = {3: 2 * (27 + 27) * 4, 2: 2 * (9 + 9) * 4}  # FP32
 # shifted 16-bit storage: per population set one FP32 reference + (Q-1) codes
 BYTES_PER_CELL_16 = {3: 2 * 2 * (4 + 26 * 2), 2: 2 * 2 * (4 + 8 * 2)}
+# reduced phase-field lattice (D3Q7 / D2Q5): f' and g read and written once,
+# plus the stored previous phi u (D values) read and written once
+BYTES_PER_CELL_RED = {3: 2 * 4 * (27 + 7 + 3), 2: 2 * 4 * (9 + 5 + 2)}
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
@@ -44,12 +47,15 @@ STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 # keyed by the SHA-256 of the kernel sources it was taken on, so that it is
 # reported as null once those sources change.
 TRAFFIC = {
-    # 128x128x512 rt3d, one launch of step_fused3_kernel: 1905757696 B read + 1768649984 B written
-    ("rt3d", "fp32"): {"bytes_per_cell": 3674407680 / 8388608, "sources": "63f9b76e4b73262e"},
-    # same workload, step_fused3s_kernel<StoreF16>: 978364672 B read + 900994816 B written
-    ("rt3d", "fp16"): {"bytes_per_cell": 1879359488 / 8388608, "sources": "63f9b76e4b73262e"},
+    # 128x128x512 rt3d, one launch of step_fused3_kernel: 1906610688 B read + 1769191680 B written
+    ("rt3d", "fp32"): {"bytes_per_cell": 3675802368 / 8388608, "sources": "3b769244b7b41168"},
+    # same workload, step_fused3s_kernel<StoreF16>: 976766720 B read + 901058304 B written
+    ("rt3d", "fp16"): {"bytes_per_cell": 1877825024 / 8388608, "sources": "3b769244b7b41168"},
+    # same workload, reduced phase lattice (step_fused3_kernel, D3Q7 g): 1289332736 B read + 1197356288 B written
+    ("rt3d", "reduced"): {"bytes_per_cell": 2486689024 / 8388608, "sources": "3b769244b7b41168"},
 }
-TRAFFIC_SOURCES = ["lbmp_common.cuh", "lbmp_tile.cuh", "lbmp_fused3_body.cuh", "lbmp_fused.cu", "lbmp_fused16.cu"]
+TRAFFIC_SOURCES = ["lbmp_common.cuh", "lbmp_tile.cuh", "lbmp_fused3_body.cuh", "lbmp_fused.cu", "lbmp_fused16.cu",
+                   "lbmp_fused_r.cu"]
 
 
 def kernel_source_hash():
@@ -228,7 +234,9 @@ def kernel_name(args, D):
     if args.kernel == 1:
         return "phi_pass_kernel + step_simple_kernel"
     if args.storage != "fp32":
-        return "step_fused3s_kernel<Store%s>" % args.storage.upper() if D == 3 else "step_simple_kernel"
+        return ("step_fused3s_kernel<Store%s>" if D == 3 else "step_fused2s_kernel<Store%s>") % args.storage.upper()
+    if args.phase == "reduced":
+        return "step_fused3_kernel (D3Q7 phase field)" if D == 3 else "phi_pass_kernel + step_simple_kernel"
     if D == 2:
         return "step_fused2_kernel"
     return "step_fused3b_kernel" if args.kernel == 2 else "step_fused3_kernel"
@@ -281,6 +289,29 @@ def measure_forms(args, wl, stream, peak, pg):
         out[name] = {"mlups": mlups, "ms_per_step": ms, "bytes_per_cell": bpc, "achieved_gbs": gbs,
                      "frac": gbs / peak, "mass_drift_rel": ob.mass_drift_rel, "steps": n,
                      "traffic": traffic_per_launch(args.workload, name, d.N)}
+        d.close()
+    # the reduced phase-field lattice (D3Q7 / D2Q5 with the first-order
+    # equilibrium and the correction term of Sec. 2.2) on the same workload
+    if args.storage == "fp32" and args.kernel == 0 and args.phase == "full":
+        from paper_2101_06769_gb300.lbmp import FLAG_PHASE_REDUCED
+        phys = dict(wl["phys"])
+        phys["flags"] = int(phys.get("flags", 0)) | FLAG_PHASE_REDUCED
+        d = Domain(D, wl["dims"], wl["periodic"], stream=stream.cuda_stream, **phys)
+        d.init(wl["case"], wl["args"], seed=wl["seed"])
+        if not args.no_autotune:
+            d.autotune(reps=3, cache=False)
+        d.step(5)
+        ms = time_steps(lambda: d.step(1), stream, n)
+        launches += n
+        _, mlups = aggregate(ms * n, d.N, n, pg)
+        bpc = BYTES_PER_CELL_RED[D]
+        gbs = bpc * d.N / (ms * 1e-3) / 1e9
+        ob = d.observables()
+        out["reduced_phase"] = {"mlups": mlups, "ms_per_step": ms, "bytes_per_cell": bpc, "achieved_gbs": gbs,
+                                "frac": gbs / peak, "mass_drift_rel": ob.mass_drift_rel, "steps": n,
+                                "kernel": "step_fused3_kernel (D3Q7 phase field)" if D == 3 else
+                                "step_simple_kernel (D2Q5 phase field)",
+                                "traffic": traffic_per_launch(args.workload, "reduced", d.N)}
         d.close()
     # batched form
     doms, cells, byts = [], 0, 0
@@ -454,6 +485,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--grid", default=None, help="override nx,ny,nz (profiling on a smaller case)")
     ap.add_argument("--storage", default="fp32", choices=sorted(STORAGE))
+    ap.add_argument("--phase", default="full", choices=["full", "reduced"],
+                    help="phase-field lattice: the flow lattice, or D3Q7 / D2Q5 (FP32 only)")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16/batched form measurements")
     ap.add_argument("--form-steps", type=int, default=50)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
@@ -462,6 +495,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=0,
                     help="with --configs: also serve this many requests of the full serving stream")
     args = ap.parse_args()
+    if args.phase == "reduced" and args.storage != "fp32":
+        ap.error("the reduced phase lattice is stored in FP32 only")
     wl = dict(WORKLOADS[args.workload])
     if args.grid:
         dims = tuple(int(v) for v in args.grid.split(","))
@@ -488,8 +523,11 @@ def main():
 
     stream = torch.cuda.Stream()
     D = wl["D"]
-    dom = Domain(D, wl["dims"], wl["periodic"], stream=stream.cuda_stream, storage=STORAGE[args.storage],
-                 **wl["phys"])
+    phys = dict(wl["phys"])
+    if args.phase == "reduced":
+        from paper_2101_06769_gb300.lbmp import FLAG_PHASE_REDUCED
+        phys["flags"] = int(phys.get("flags", 0)) | FLAG_PHASE_REDUCED
+    dom = Domain(D, wl["dims"], wl["periodic"], stream=stream.cuda_stream, storage=STORAGE[args.storage], **phys)
     dom.set_kernel(args.kernel)
     dom.init(wl["case"], wl["args"], seed=wl["seed"] + rank)
     cells = dom.N
@@ -526,15 +564,18 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms, mlups = aggregate(t_start.elapsed_time(t_end), cells, args.steps, pg)
     ms_per_step = total_ms / args.steps
-    launches_per_step = 2 if (args.kernel == 1) else 1
+    launches_per_step = 2 if (args.kernel == 1 or (args.phase == "reduced" and D == 2)) else 1
 
     # roofline of the step kernel: algorithmic bytes per launch / event time
     peak, peak_kind = load_peaks()
     kern_ms = statistics.mean(step_ms)
     bpc = BYTES_PER_CELL[D] if args.storage == "fp32" else BYTES_PER_CELL_16[D]
+    form = args.storage
+    if args.phase == "reduced":
+        bpc, form = BYTES_PER_CELL_RED[D], "reduced"
     bytes_launch = bpc * cells
     achieved = bytes_launch / (kern_ms * 1e-3) / 1e9
-    traffic = traffic_per_launch(args.workload, args.storage, cells) if (args.kernel == 0 and not args.grid) else None
+    traffic = traffic_per_launch(args.workload, form, cells) if (args.kernel == 0 and not args.grid) else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_kind": peak_kind, "traffic": traffic,
             "kernel": kernel_name(args, D),
@@ -563,7 +604,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl["desc"], "grid": list(wl["dims"]), "cells": cells,
-                       "storage": args.storage, "l2": "inputs larger than L2 (no flush)",
+                       "storage": args.storage, "phase_lattice": args.phase, "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas{ws}", "launch": launch},
             "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "health": ob.health, "mass_drift_rel": ob.mass_drift_rel}

@@ -155,6 +155,7 @@ cudaError_t launch_step(lbmp_handle* h)
     if (h->kernel == 1 || !fused_supported(h)) return launch_step_simple(h);
     if (h->params.storage != LBMP_FP32) return h->D == 3 ? launch_step_fused16(h) : launch_step_fused2s(h);
     if (h->D == 2) return launch_step_fused2(h);
+    if (h->reduced) return launch_step_fused3_red(h);
     if (h->kernel == 2 && bulk_supported(h)) return launch_step_fused_bulk(h);
     if (h->opt_tile == 1) return launch_step_fused3_t16x8(h);
     if (h->opt_tile == 2) return launch_step_fused3_t8x16(h);

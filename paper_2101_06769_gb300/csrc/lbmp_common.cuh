@@ -899,13 +899,47 @@ __device__ __forceinline__ void phiu_step(const DevParams& p, const CellState& s
     if (D == 2) d[2] = 0.f;
 }
 
+// Source of d/dt(phi u) for collide_outputs: phiu_step on the stored array
+// (called once, after the flow outputs, so its values are not live across
+// them), or none on the full phase lattice.
+template <int D>
+struct PhiUStep {
+    const DevParams& p;
+    float* phiu;
+    long long i;
+    __device__ __forceinline__ void operator()(const CellState& s, float d[3]) const { phiu_step<D>(p, s, phiu, i, d); }
+};
+// the same with the previous value already staged in shared memory
+// (prev[k * stride]); the new value goes to the stored array
+template <int D>
+struct PhiUStaged {
+    const DevParams& p;
+    float* phiu;
+    long long i;
+    const float* prev;
+    int stride;
+    __device__ __forceinline__ void operator()(const CellState& s, float d[3]) const
+    {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const float v = s.phi * s.u[k];
+            d[k] = v - prev[k * stride];
+            phiu[k * p.N + i] = v;
+        }
+        if (D == 2) d[2] = 0.f;
+    }
+};
+struct NoPhiU {
+    __device__ __forceinline__ void operator()(const CellState&, float d[3]) const { d[0] = d[1] = d[2] = 0.f; }
+};
+
 // PR: g on the reduced phase lattice (gin / gout index its slots), with
-// dphiu = d/dt(phi u) of the cell for the correction term.
-template <int D, bool PR = false, class GSrc, class Out, class DH>
+// dphiu(s, d) giving d/dt(phi u) of the cell for the correction term.
+template <int D, bool PR = false, class GSrc, class Out, class DH, class DPhiU = NoPhiU>
 __device__ __forceinline__ void collide_outputs(const DevParams& p, const CellState& s, const DH& dh,
                                                 const FlowMoments& m, const GSrc& gin, float gsum_hi,
                                                 float gsum_lo, const Out& fout, const Out& gout,
-                                                const float* dphiu = nullptr)
+                                                const DPhiU& dphiu_fn = DPhiU{})
 {
     static_assert(!(PR && Out::kTotal), "the reduced phase lattice is stored in FP32 only");
     constexpr int Q = Lat<D>::Q;
@@ -971,8 +1005,9 @@ __device__ __forceinline__ void collide_outputs(const DevParams& p, const CellSt
         // and correction term (Sec. 2.2), lanes (r, opposite)
         constexpr float ics = PhaseLat<D, true>::inv_cs2;
         float qv[3];
+        dphiu_fn(s, qv);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) qv[i] = fmaf(p.lam_corr, dphiu[i], s.sharp * s.n[i]);
+        for (int i = 0; i < 3; ++i) qv[i] = fmaf(p.lam_corr, qv[i], s.sharp * s.n[i]);
 #pragma unroll
         for (int r = 0; r < GC; ++r) {
             const int a = PhaseLat<D, true>::full(r);

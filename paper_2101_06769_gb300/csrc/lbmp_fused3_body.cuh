@@ -31,6 +31,10 @@
 // LBMP_BATCH3_OPS (the name of its batch-kernel table) and, for a tile shape
 // other than the default, LBMP_FUSED_TX / _TY and LBMP_TILE_NS;
 // LBMP_FUSED3_WITH_COMMON adds the pieces shared by every tile shape.
+// LBMP_PHASE_REDUCED = 1 builds the kernel for the reduced phase lattice
+// (D3Q7 g with the first-order equilibrium and the correction term, Sec. 2.2;
+// the stored previous phi u is read and replaced per cell); it has no batch
+// form.
 #pragma once
 
 #include "lbmp_internal.h"
@@ -45,9 +49,9 @@ using namespace LBMP_TILE_NS;
 
 struct DirPtrs {
     const float* fin[Q3];
-    const float* gin[Q3];
+    const float* gin[QG];
     float* fout[Q3];
-    float* gout[Q3];
+    float* gout[QG];
 };
 
 // Work items: (tile, chunk of z planes), tile index fastest, so the CTAs
@@ -57,6 +61,7 @@ struct DirPtrs {
 // paper, measured slower for that reason.
 struct FusedArgs {
     int tiles_x, tiles_y, chunk, nitems;
+    float* phiu;  // reduced phase lattice: previous phi u, [k][cell]; else null
 };
 
 template <bool Walls>
@@ -65,10 +70,10 @@ struct StageCopy {
     const Column& C;
     const Plane& P;
     float* gbuf;
-    template <int a>
+    template <int r>
     __device__ __forceinline__ void step() const
     {
-        cp_async4(gbuf + a * NT, pulled<Walls, a>(D.gin, C, P));
+        cp_async4(gbuf + r * NT, pulled_g<Walls, r>(D.gin, C, P));
     }
 };
 
@@ -92,10 +97,10 @@ struct RingCopy {
     const Column& C;
     const Plane& P;
     float* rbuf;
-    template <int a>
+    template <int r>
     __device__ __forceinline__ void step() const
     {
-        cp_async4(rbuf + a * NRING, pulled<Walls, a>(D.gin, C, P));
+        cp_async4(rbuf + r * NRING, pulled_g<Walls, r>(D.gin, C, P));
     }
 };
 
@@ -105,18 +110,26 @@ struct RingCopy {
 // cp.async.  finish: wait, then phi = (hi, lo) of every tile and ring cell
 // into phi_plane.  Each thread sums only the values it copied itself, so no
 // barrier is needed in between.
+// Reduced phase lattice: the own cells' stored phi u of plane zz is copied
+// with them into ubuf ([3][NT]), so the collision finds it in shared memory.
 __device__ __forceinline__ void stage_issue(const DevParams& p, const DirPtrs& D, const Column& own,
                                             const Column& ring, int tid, int zz, float* __restrict__ gbuf,
-                                            float* __restrict__ rbuf)
+                                            float* __restrict__ rbuf, const float* __restrict__ phiu,
+                                            float* __restrict__ ubuf)
 {
     Plane P;
     set_plane(P, p, plane_src(p, zz));
+    if constexpr (PR) {
+        const int self = P.zs[1] + own.ys[1] + own.xs[1];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) cp_async4(ubuf + k * NT + tid, phiu + k * p.N + self);
+    }
     if (P.lo || P.hi) {  // uniform across the CTA
-        Unroll<Q3>::run(StageCopy<true>{D, own, P, gbuf + tid});
-        if (tid < NRING) Unroll<Q3>::run(RingCopy<true>{D, ring, P, rbuf + tid});
+        Unroll<QG>::run(StageCopy<true>{D, own, P, gbuf + tid});
+        if (tid < NRING) Unroll<QG>::run(RingCopy<true>{D, ring, P, rbuf + tid});
     } else {
-        Unroll<Q3>::run(StageCopy<false>{D, own, P, gbuf + tid});
-        if (tid < NRING) Unroll<Q3>::run(RingCopy<false>{D, ring, P, rbuf + tid});
+        Unroll<QG>::run(StageCopy<false>{D, own, P, gbuf + tid});
+        if (tid < NRING) Unroll<QG>::run(RingCopy<false>{D, ring, P, rbuf + tid});
     }
     cp_async_commit();
 }
@@ -127,11 +140,11 @@ __device__ __forceinline__ void stage_finish(int tid, int oslot, int rslot, cons
     cp_async_wait_all();
     if (tid < NRING) {
         float hi, lo;
-        phi_sum<3>([&](int a) { return rbuf[a * NRING + tid]; }, hi, lo);
+        phi_sum_phase<3, PR>([&](int r) { return rbuf[r * NRING + tid]; }, hi, lo);
         phi_plane[rslot] = make_float2(hi, lo);
     }
     float hi, lo;
-    phi_sum<3>([&](int a) { return gbuf[a * NT + tid]; }, hi, lo);
+    phi_sum_phase<3, PR>([&](int r) { return gbuf[r * NT + tid]; }, hi, lo);
     phi_plane[oslot] = make_float2(hi, lo);
 }
 
@@ -140,27 +153,28 @@ __device__ __forceinline__ void stage_finish(int tid, int oslot, int rslot, cons
 // the three phi planes.  Ends with a barrier, so the caller may reuse shared
 // memory afterwards.
 __device__ __forceinline__ void fused_segment(const DevParams& p, const DirPtrs& Dp, const ThreadGeo& T, float* smem,
-                                              int x0, int y0, int z0, int z1)
+                                              int x0, int y0, int z0, int z1, float* __restrict__ phiu)
 {
-    float* gS = smem;                           // [2][27][NT]
-    float* rS = smem + 2 * Q3 * NT;             // [27][NRING] ring cells' g of the plane being staged
-    float2* phiS = (float2*)(rS + Q3 * NRING);  // (hi, lo) [3][RY][RX]
+    float* gS = smem;                           // [2][QG][NT]
+    float* rS = smem + 2 * QG * NT;             // [QG][NRING] ring cells' g of the plane being staged
+    float2* phiS = (float2*)(rS + QG * NRING);  // (hi, lo) [3][RY][RX]
     float* fS = (float*)(phiS + 3 * PLANE);     // [27][NT] f' of the plane (LBMP_FUSED_FSMEM)
     float* dS = fS + LBMP_FUSED_FSMEM * Q3 * NT;  // [27][NT] dh (LBMP_FUSED_DHSMEM)
+    float* uS = dS + LBMP_FUSED_DHSMEM * Q3 * NT;  // [2][3][NT] previous phi u (reduced phase lattice)
     const int tid = T.tid, oslot = T.oslot, rslot = T.rslot;
     Column own, ring;
     set_column(own, p, pmod(x0 + T.tx, p.nx), pmod(y0 + T.ty, p.ny));
     set_column(ring, p, pmod(x0 + T.lx, p.nx), pmod(y0 + T.ly, p.ny));
     const bool valid = (x0 + T.tx < p.nx) && (y0 + T.ty < p.ny);
     int sP = 0, sC = 1, sN = 2;
-    stage_issue(p, Dp, own, ring, tid, z0 - 1, gS + Q3 * NT, rS);
-    stage_finish(tid, oslot, rslot, gS + Q3 * NT, rS, phiS + sP * PLANE);
-    stage_issue(p, Dp, own, ring, tid, z0, gS, rS);
+    stage_issue(p, Dp, own, ring, tid, z0 - 1, gS + QG * NT, rS, phiu, uS + 3 * NT);
+    stage_finish(tid, oslot, rslot, gS + QG * NT, rS, phiS + sP * PLANE);
+    stage_issue(p, Dp, own, ring, tid, z0, gS, rS, phiu, uS);
     stage_finish(tid, oslot, rslot, gS, rS, phiS + sC * PLANE);
     for (int z = z0; z < z1; ++z) {
         const int cur = (z - z0) & 1;
         // g(z+1) and the ring copies in flight while f'(z) is loaded
-        stage_issue(p, Dp, own, ring, tid, z + 1, gS + (cur ^ 1) * Q3 * NT, rS);
+        stage_issue(p, Dp, own, ring, tid, z + 1, gS + (cur ^ 1) * QG * NT, rS, phiu, uS + (cur ^ 1) * 3 * NT);
         Plane P;
         set_plane(P, p, z);
         FlowMoments m;
@@ -170,7 +184,7 @@ __device__ __forceinline__ void fused_segment(const DevParams& p, const DirPtrs&
         else
             Unroll<Q3>::run(FCopy<false>{Dp, own, P, fS + tid});
         cp_async_commit();
-        stage_finish(tid, oslot, rslot, gS + (cur ^ 1) * Q3 * NT, rS, phiS + sN * PLANE);
+        stage_finish(tid, oslot, rslot, gS + (cur ^ 1) * QG * NT, rS, phiS + sN * PLANE);
         {
             float fr[Q3];
 #pragma unroll
@@ -183,7 +197,7 @@ __device__ __forceinline__ void fused_segment(const DevParams& p, const DirPtrs&
             Unroll<Q3>::run(PullLoad<true>{Dp.fin, own, P, fr});
         else
             Unroll<Q3>::run(PullLoad<false>{Dp.fin, own, P, fr});
-        stage_finish(tid, oslot, rslot, gS + (cur ^ 1) * Q3 * NT, rS, phiS + sN * PLANE);
+        stage_finish(tid, oslot, rslot, gS + (cur ^ 1) * QG * NT, rS, phiS + sN * PLANE);
         flow_moments<3>(m, fr);
 #endif
         __syncthreads();
@@ -206,11 +220,13 @@ __device__ __forceinline__ void fused_segment(const DevParams& p, const DirPtrs&
 #if LBMP_FUSED_DHSMEM
 #pragma unroll
             for (int a = 0; a < Q3; ++a) dS[a * NT + tid] = dh[a];
-            collide_outputs<3>(p, s, DhStrided{dS + tid, NT}, m, GFromStrided{gS + cur * Q3 * NT + tid, NT},
-                               centre.x, centre.y, PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self});
+            collide_outputs<3, PR>(p, s, DhStrided{dS + tid, NT}, m, GFromStrided{gS + cur * QG * NT + tid, NT},
+                                   centre.x, centre.y, PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self},
+                                   PhiUStaged<3>{p, phiu, self, uS + cur * 3 * NT + tid, NT});
 #else
-            collide_outputs<3>(p, s, DhArray{dh}, m, GFromStrided{gS + cur * Q3 * NT + tid, NT}, centre.x,
-                               centre.y, PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self});
+            collide_outputs<3, PR>(p, s, DhArray{dh}, m, GFromStrided{gS + cur * QG * NT + tid, NT}, centre.x,
+                                   centre.y, PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self},
+                                   PhiUStaged<3>{p, phiu, self, uS + cur * 3 * NT + tid, NT});
 #endif
         }
         __syncthreads();
@@ -230,10 +246,11 @@ __global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_fused3_kernel(DevPar
         const int chunk = item / (A.tiles_x * A.tiles_y);
         const int z0 = chunk * A.chunk;
         fused_segment(p, Dp, T, smem, (tile % A.tiles_x) * TX, (tile / A.tiles_x) * TY, z0,
-                      min(z0 + A.chunk, p.nz));
+                      min(z0 + A.chunk, p.nz), A.phiu);
     }
 }
 
+#if !LBMP_PHASE_REDUCED
 // Batch form: the work items of every member (same order as above within a
 // member, members concatenated) are split over one persistent grid.  A CTA
 // stages the parameters and the 108 direction bases of its current member in
@@ -289,9 +306,11 @@ __global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_batch3_kernel(const 
         const int tiles = s_tx * s_ty;
         const int tile = local % tiles;
         const int z0 = (local / tiles) * s_chunk;
-        fused_segment(sp, sd, T, smem, (tile % s_tx) * TX, (tile / s_tx) * TY, z0, min(z0 + s_chunk, sp.nz));
+        fused_segment(sp, sd, T, smem, (tile % s_tx) * TX, (tile / s_tx) * TY, z0, min(z0 + s_chunk, sp.nz),
+                      nullptr);
     }
 }
+#endif
 
 struct LaunchCfg {
     int device = -1;
@@ -302,9 +321,10 @@ LaunchCfg g_cfg;
 }  // namespace
 
 #if LBMP_FUSED3_WITH_COMMON
-// every domain has a fused kernel (FP32 and shifted 16-bit, D3Q27 and D2Q9)
-// but the reduced phase lattice, which runs the reference pair
-bool fused_supported(const lbmp_handle* h) { return !h->reduced; }
+// every domain has a fused kernel (FP32 and shifted 16-bit, D3Q27 and D2Q9;
+// the reduced phase lattice in 3-D) but the reduced phase lattice in 2-D,
+// which runs the reference pair
+bool fused_supported(const lbmp_handle* h) { return !h->reduced || h->D == 3; }
 
 __global__ void batch_epilogue_kernel(BatchDomain* table, int ndom)
 {
@@ -323,6 +343,7 @@ cudaError_t launch_batch_epilogue(BatchDomain* table, int ndom, cudaStream_t str
 }
 #endif
 
+#if !LBMP_PHASE_REDUCED
 namespace {
 
 int g_batch_dev = -1, g_batch_cap = 0;
@@ -357,6 +378,7 @@ cudaError_t launch_batch(const BatchDomain* table, int ndom, int nitems, int dev
 }  // namespace
 
 const Batch3Ops LBMP_BATCH3_OPS = {TX, TY, prepare_batch, launch_batch};
+#endif
 
 cudaError_t LBMP_FUSED3_LAUNCH(lbmp_handle* h)
 {
@@ -378,11 +400,15 @@ cudaError_t LBMP_FUSED3_LAUNCH(lbmp_handle* h)
     for (int a = 0; a < Q3; ++a) {
         const size_t off = (size_t)a * (size_t)h->N;
         D.fin[a] = h->f[s] + off;
-        D.gin[a] = h->g[s] + off;
         D.fout[a] = h->f[d] + off;
-        D.gout[a] = h->g[d] + off;
+    }
+    for (int r = 0; r < QG; ++r) {
+        const size_t off = (size_t)r * (size_t)h->N;
+        D.gin[r] = h->g[s] + off;
+        D.gout[r] = h->g[d] + off;
     }
     FusedArgs A;
+    A.phiu = h->phiu;
     A.tiles_x = (h->grid.nx + TX - 1) / TX;
     A.tiles_y = (h->grid.ny + TY - 1) / TY;
     const LaunchShape L = launch_shape(h, A.tiles_x * A.tiles_y, h->grid.nz, g_cfg.per_sm, g_cfg.sms);

@@ -90,10 +90,8 @@ __global__ void __launch_bounds__(128) step_simple_kernel(DevParams p, Pop<D, St
         gr[r] = gin.load(slot, c);
     }
     if constexpr (PR) {
-        float dphiu[3];
-        phiu_step<D>(p, s, phiu, i, dphiu);
         collide_outputs<D, true>(p, s, DhArray{dh}, m, GFromArray{gr}, nh[Q / 2], nl[Q / 2], SoAOut{fout.base + i, p.N},
-                                 SoAOut{gout.base + i, p.N}, dphiu);
+                                 SoAOut{gout.base + i, p.N}, PhiUStep<D>{p, phiu, i});
     } else if constexpr (St::shifted) {
         float off_f, off_g;
         rest_offsets<D, St>(p, s, dh, GFromArray{gr}, off_f, off_g);

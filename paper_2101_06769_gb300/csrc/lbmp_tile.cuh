@@ -33,13 +33,20 @@ namespace LBMP_TILE_NS {
 #ifndef LBMP_FUSED_DHSMEM
 #define LBMP_FUSED_DHSMEM 1
 #endif
+// 1: the phase field on the reduced lattice D3Q7 (LBMP_FLAG_PHASE_REDUCED)
+#ifndef LBMP_PHASE_REDUCED
+#define LBMP_PHASE_REDUCED 0
+#endif
 constexpr int TX = LBMP_FUSED_TX, TY = LBMP_FUSED_TY, NT = TX * TY;
 constexpr int RX = TX + 2, RY = TY + 2;
 constexpr int PLANE = RY * RX;
 constexpr int NRING = 2 * RX + 2 * TY;
 constexpr int Q3 = 27;
-constexpr size_t kSmemBytes =
-    sizeof(float) * ((2 + LBMP_FUSED_FSMEM + LBMP_FUSED_DHSMEM) * Q3 * NT + Q3 * NRING) + sizeof(float2) * 3 * PLANE;
+constexpr bool PR = LBMP_PHASE_REDUCED != 0;
+constexpr int QG = PhaseLat<3, PR>::Q;  // phase-field populations
+constexpr size_t kSmemBytes = sizeof(float) * ((2 * QG + (LBMP_FUSED_FSMEM + LBMP_FUSED_DHSMEM) * Q3) * NT +
+                                               QG * NRING + (PR ? 2 * 3 * NT : 0)) +
+                              sizeof(float2) * 3 * PLANE;
 static_assert(NRING <= NT, "one thread per ring cell");
 
 __device__ __forceinline__ void cp_async4(float* smem, const float* gmem)
@@ -119,6 +126,17 @@ struct Unroll<0> {
     {
     }
 };
+
+// pointer to the post-streaming phase-field population of slot r (the
+// flow-lattice direction PhaseLat::full(r)) of the cell (C, P)
+template <bool Walls, int r, class E>
+__device__ __forceinline__ const E* pulled_g(const E* const* base, const Column& C, const Plane& P)
+{
+    constexpr int a = PhaseLat<3, PR>::full(r);
+    constexpr int cx = Lat<3>::cx(a), cy = Lat<3>::cy(a), cz = Lat<3>::cz(a);
+    if (Walls && ((cz == 1 && P.lo) || (cz == -1 && P.hi))) return base[QG - 1 - r] + (P.zs[1] + C.ys[1] + C.xs[1]);
+    return base[r] + (P.zs[cz + 1] + C.ys[cy + 1] + C.xs[cx + 1]);
+}
 
 // post-streaming values of the 27 directions of one cell into registers
 template <bool Walls>

@@ -26,7 +26,7 @@ LBMP_API int lbmp_autotune(lbmp_handle* h, int reps, lbmp_tune_entry* table, int
         if (c <= nmarch) chunks[nc++] = c;
     const int ctas[3] = {0, 1, 2};
     // tile shapes exist for the FP32 D3Q27 cp.async kernel only
-    const int ntiles = (h->D == 3 && h->params.storage == LBMP_FP32 && h->kernel == 0) ? 3 : 1;
+    const int ntiles = (h->D == 3 && h->params.storage == LBMP_FP32 && h->kernel == 0 && !h->reduced) ? 3 : 1;
     const int saved_chunk = h->opt_chunk, saved_ctas = h->opt_ctas, saved_tile = h->opt_tile;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
