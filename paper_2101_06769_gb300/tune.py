@@ -1,7 +1,8 @@
 """Launch-shape tuning cache over lbmp_autotune (host logic only: the trials
 run in the CUDA library).
 
-The cache maps a key (device name, lattice, storage, grid, boundaries) to the
+The cache maps a key (device name, lattice, phase lattice, storage, grid,
+boundaries) to the
 chosen (chunk, ctas_per_sm).  It is a JSON file, LBMP_TUNE_CACHE or
 ~/.cache/lbmp/tune.json, written atomically (temporary file + rename).
 """
@@ -24,8 +25,11 @@ def device_name():
 
 
 def key_of(dom, device):
-    return "|".join([device, f"D{dom.D}", f"storage{dom.storage}", "x".join(map(str, dom.dims)),
-                     "p" + "".join(map(str, dom.periodic))])
+    parts = [device, f"D{dom.D}"]
+    if dom.Qg != dom.Q:  # the reduced phase lattice runs its own kernel
+        parts.append(f"g{dom.Qg}")
+    return "|".join(parts + [f"storage{dom.storage}", "x".join(map(str, dom.dims)),
+                             "p" + "".join(map(str, dom.periodic))])
 
 
 def read_cache(path):

@@ -5,8 +5,10 @@ import types
 from paper_2101_06769_gb300 import tune
 
 
-def fake_dom(D=3, dims=(128, 128, 512), storage=0, periodic=(1, 1, 0)):
-    return types.SimpleNamespace(D=D, dims=dims, storage=storage, periodic=periodic)
+def fake_dom(D=3, dims=(128, 128, 512), storage=0, periodic=(1, 1, 0), reduced=False):
+    Q = 27 if D == 3 else 9
+    return types.SimpleNamespace(D=D, dims=dims, storage=storage, periodic=periodic, Q=Q,
+                                 Qg=2 * D + 1 if reduced else Q)
 
 
 def test_key_separates_every_field():
@@ -15,8 +17,9 @@ def test_key_separates_every_field():
               tune.key_of(fake_dom(storage=1), "GB300"),
               tune.key_of(fake_dom(dims=(128, 128, 256)), "GB300"),
               tune.key_of(fake_dom(periodic=(1, 1, 1)), "GB300"),
-              tune.key_of(fake_dom(), "other GPU")]
-    assert len({base, *others}) == 6
+              tune.key_of(fake_dom(), "other GPU"),
+              tune.key_of(fake_dom(reduced=True), "GB300")]
+    assert len({base, *others}) == 7
 
 
 def test_cache_round_trip_and_corrupt_file(tmp_path):
