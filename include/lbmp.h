@@ -95,7 +95,17 @@ enum {
      * phi u (the previous value equals the current one before the first step
      * after lbmp_init / lbmp_set_state).  The flow lattice is unchanged.
      * FP32 storage only (LBMP_ERR_UNSUPPORTED otherwise); not a batch member. */
-    LBMP_FLAG_PHASE_REDUCED = 1u << 3
+    LBMP_FLAG_PHASE_REDUCED = 1u << 3,
+    /* Keep the w cs2 rho div(u) term of Xi (Sec. 2.3), which the default
+     * reading drops (div u prescribed zero): div(u) is the isotropic
+     * difference of the previous step's velocity, stored per cell (no-slip
+     * ghosts across walls; before the first step after lbmp_init /
+     * lbmp_set_state the previous velocity is the current one).  An ablation
+     * of that reading: the term cancels the pressure's response to the
+     * divergence.  FP32 storage and the full phase lattice only
+     * (LBMP_ERR_UNSUPPORTED otherwise); runs the reference pair; not a batch
+     * member. */
+    LBMP_FLAG_DIVU = 1u << 4
 };
 
 typedef struct {
@@ -180,7 +190,8 @@ LBMP_API int lbmp_set_state(lbmp_handle *h, const double *f, const double *g);
 
 /* Raw transfers of the device state in its native storage layout (an opaque
  * byte image, valid only for a handle of the same grid, lattice, storage and
- * phase lattice; with LBMP_FLAG_PHASE_REDUCED it includes the stored phi u).  Asynchronous on the handle's stream; host memory should be
+ * flags; with LBMP_FLAG_PHASE_REDUCED it includes the stored phi u, with
+ * LBMP_FLAG_DIVU the stored velocity).  Asynchronous on the handle's stream; host memory should be
  * pinned.  bytes must equal lbmp_state_bytes(h). */
 LBMP_API size_t lbmp_state_bytes(const lbmp_handle *h);
 LBMP_API int lbmp_upload(lbmp_handle *h, const void *host, size_t bytes);

@@ -24,6 +24,7 @@ FLAG_WE_LIGHT = 1 << 0
 FLAG_DYNAMIC_VISC = 1 << 1
 FLAG_UNIFORM_FORCE = 1 << 2
 FLAG_PHASE_REDUCED = 1 << 3
+FLAG_DIVU = 1 << 4
 
 
 class Phys(C.Structure):
@@ -80,6 +81,9 @@ def lib():
                                              C.c_void_p, _dp, _dp, C.c_void_p]
         L.lbmo_phase_lattice.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_void_p,
                                          C.POINTER(C.c_double)]
+        L.lbmo_collide_cell_ex.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp, C.c_double,
+                                           C.c_void_p, C.c_double, _dp, _dp, C.c_void_p]
+        L.lbmo_divu.argtypes = [C.c_void_p, _dp, _dp]
         L.lbmo_phase_q.argtypes = [C.c_void_p]
         L.lbmo_phase_q.restype = C.c_int
         L.lbmo_splitmix64.restype = C.c_ulonglong
@@ -234,18 +238,29 @@ class Oracle:
         lib().lbmo_fd(self._h, field.ravel(), grad.ravel(), lap.ravel())
         return grad, lap
 
-    def collide_cell(self, f, g, phi, grad, lap, phiu_prev=None):
+    def collide_cell(self, f, g, phi, grad, lap, phiu_prev=None, divu=0.0):
         """One cell's collision; phiu_prev: the previous step's phi u (reduced
-        phase lattice; None = no time derivative).  diag[14:17] = phi u."""
+        phase lattice; None = no time derivative); divu: div(u) for the
+        w cs2 rho div(u) term (FLAG_DIVU).  diag[14:17] = phi u."""
         fo = np.zeros(self.Q)
         go = np.zeros(self.Qg)
         diag = np.zeros(17)
         prev = None if phiu_prev is None else np.ascontiguousarray(phiu_prev, dtype=np.float64)
-        lib().lbmo_collide_cell_prev(self._h, np.ascontiguousarray(f, dtype=np.float64),
-                                     np.ascontiguousarray(g, dtype=np.float64), float(phi),
-                                     np.ascontiguousarray(grad, dtype=np.float64), float(lap),
-                                     None if prev is None else prev.ctypes.data, fo, go, diag.ctypes.data)
+        lib().lbmo_collide_cell_ex(self._h, np.ascontiguousarray(f, dtype=np.float64),
+                                   np.ascontiguousarray(g, dtype=np.float64), float(phi),
+                                   np.ascontiguousarray(grad, dtype=np.float64), float(lap),
+                                   None if prev is None else prev.ctypes.data, float(divu), fo, go,
+                                   diag.ctypes.data)
         return fo, go, diag
+
+    def divu(self, u):
+        """div(u) of a velocity field u[k][z][y][x] (k < 3) by the isotropic
+        difference, no-slip ghosts across walls"""
+        u3 = np.zeros((3,) + self.shape[1:])
+        u3[:len(u)] = u
+        out = np.zeros(self.shape[1:])
+        lib().lbmo_divu(self._h, np.ascontiguousarray(u3).ravel(), out.ravel())
+        return out
 
 
 def set_threads(n: int):

@@ -33,6 +33,10 @@
  *       previous value is the current one (init and set_state)
  *   P3  tau_bar_phi = M/cs2 + 1/2 with the phase lattice's cs2; C_bar takes
  *       the factor lambda of A4, like S_bar
+ * and, with LBMO_FLAG_DIVU (the alternative to A6):
+ *   V1  div(u) by the isotropic difference of the previous step's u (stored
+ *       per cell; before the first step the current one), with the ghost
+ *       velocity across a wall equal to minus the wall cell's (no slip)
  */
 #include "lbmo.h"
 
@@ -132,6 +136,7 @@ struct lbmo {
     long N;
     lattice L, Lg;      /* flow lattice, phase-field lattice */
     double *phiu_prev;  /* reduced phase lattice: phi u of the previous step, [3][cell] */
+    double *u_prev, *u_next; /* LBMO_FLAG_DIVU: velocity of the previous / current step, [3][cell] */
     lbmo_phys phys;
     lbmo_derived d;
     double rate_shear, rate_bulk, r3, r4, r5, r6;
@@ -230,7 +235,9 @@ lbmo *lbmo_create(int D, const int dims[3], const int periodic[3], const lbmo_ph
     s->gn = (double *)calloc(1, gbytes);
     s->phi = (double *)calloc((size_t)s->N, sizeof(double));
     s->phiu_prev = (double *)calloc(3 * (size_t)s->N, sizeof(double));
-    if (!s->f || !s->g || !s->fn || !s->gn || !s->phi || !s->phiu_prev) {
+    s->u_prev = (double *)calloc(3 * (size_t)s->N, sizeof(double));
+    s->u_next = (double *)calloc(3 * (size_t)s->N, sizeof(double));
+    if (!s->f || !s->g || !s->fn || !s->gn || !s->phi || !s->phiu_prev || !s->u_prev || !s->u_next) {
         lbmo_destroy(s);
         set_err("out of memory");
         return NULL;
@@ -248,6 +255,8 @@ void lbmo_destroy(lbmo *s)
     free(s->gn);
     free(s->phi);
     free(s->phiu_prev);
+    free(s->u_prev);
+    free(s->u_next);
     free(s);
 }
 
@@ -322,6 +331,38 @@ static void fd_cell(const lbmo *s, const double *field, int x, int y, int z, dou
     }
     for (int i = 0; i < 3; ++i) grad[i] = gs[i] / CS2;
     *lap = 2.0 * ls / CS2;
+}
+
+/* div(u) at one cell (reading V1): (1/cs2) sum_a w_a c_a . u(x + c_a); a
+ * neighbour across a wall is the mirror ghost of the wall cell with the
+ * velocity reversed (no slip at the half-way wall) */
+static double div_cell(const lbmo *s, const double *u, int x, int y, int z)
+{
+    const lattice *L = &s->L;
+    const int xyz[3] = {x, y, z};
+    double sum = 0.0;
+    for (int a = 0; a < L->Q; ++a) {
+        int q[3], sign = 1;
+        for (int k = 0; k < 3; ++k) {
+            int v = xyz[k] + L->c[a][k];
+            if ((v < 0 || v >= s->n[k]) && !s->per[k]) sign = -1;
+            q[k] = ghost_coord(xyz[k], L->c[a][k], s->n[k], s->per[k]);
+        }
+        long j = cell_index(s, q[0], q[1], q[2]);
+        double cu = 0.0;
+        for (int k = 0; k < 3; ++k) cu += L->c[a][k] * u[(size_t)k * s->N + j];
+        sum += L->w[a] * sign * cu;
+    }
+    return sum / CS2;
+}
+
+void lbmo_divu(const lbmo *s, const double *u, double *div)
+{
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < s->N; ++i) {
+        int x = (int)(i % s->n[0]), y = (int)((i / s->n[0]) % s->n[1]), z = (int)(i / ((long)s->n[0] * s->n[1]));
+        div[i] = div_cell(s, u, x, y, z);
+    }
 }
 
 void lbmo_fd(const lbmo *s, const double *field, double *grad, double *lap)
@@ -564,6 +605,12 @@ int lbmo_phase_q(const lbmo *s) { return s->Qg; }
 void lbmo_collide_cell_prev(const lbmo *s, const double *f, const double *g, double phi, const double grad[3],
                             double lap, const double *phiu_prev, double *fout, double *gout, double *diag)
 {
+    lbmo_collide_cell_ex(s, f, g, phi, grad, lap, phiu_prev, 0.0, fout, gout, diag);
+}
+
+void lbmo_collide_cell_ex(const lbmo *s, const double *f, const double *g, double phi, const double grad[3],
+                          double lap, const double *phiu_prev, double divu, double *fout, double *gout, double *diag)
+{
     const lattice *L = &s->L;
     const lbmo_derived *d = &s->d;
     const int Q = L->Q, D = L->D;
@@ -581,6 +628,7 @@ void lbmo_collide_cell_prev(const lbmo *s, const double *f, const double *g, dou
             cmu_F += (L->c[a][i] - u[i]) * c.F[i];
         }
         Xi[a] = CS2 * (G - L->w[a]) * cmu_grho + cmu_F * G;
+        if (s->phys.flags & LBMO_FLAG_DIVU) Xi[a] += L->w[a] * CS2 * c.rho * divu; /* w cs2 rho div(u), V1 */
         sumXi += Xi[a];
         for (int i = 0; i < 3; ++i) sumcXi[i] += L->c[a][i] * Xi[a];
     }
@@ -686,10 +734,13 @@ static void step_once(lbmo *s)
         for (int a = 0; a < Qg; ++a) gl[a] = s->g[(size_t)a * N + i];
         for (int k = 0; k < 3; ++k) prev[k] = s->phiu_prev[(size_t)k * N + i];
         fd_cell(s, s->phi, x, y, z, grad, &lap);
-        lbmo_collide_cell_prev(s, fl, gl, s->phi[i], grad, lap, reduced ? prev : NULL, fo, go, diag);
+        const double divu = (s->phys.flags & LBMO_FLAG_DIVU) ? div_cell(s, s->u_prev, x, y, z) : 0.0;
+        lbmo_collide_cell_ex(s, fl, gl, s->phi[i], grad, lap, reduced ? prev : NULL, divu, fo, go, diag);
         /* this step's phi u becomes the previous value of the next step (P2);
          * each cell reads and writes only its own entry */
         for (int k = 0; k < 3; ++k) s->phiu_prev[(size_t)k * N + i] = diag[14 + k];
+        /* this step's u, read by the neighbours' div(u) of the next step (V1) */
+        for (int k = 0; k < 3; ++k) s->u_next[(size_t)k * N + i] = diag[1 + k];
         /* push streaming; half-way bounce-back at walls */
         int xyz[3] = {x, y, z};
         for (int a = 0; a < Q; ++a) push(s, s->fn, Q, L->c[a], a, xyz, i, fo[a]);
@@ -698,6 +749,9 @@ static void step_once(lbmo *s)
     double *t = s->f;
     s->f = s->fn;
     s->fn = t;
+    t = s->u_prev;
+    s->u_prev = s->u_next;
+    s->u_next = t;
     t = s->g;
     s->g = s->gn;
     s->gn = t;
@@ -732,7 +786,10 @@ static void reset_phiu(lbmo *s)
         fd_cell(s, s->phi, x, y, z, grad, &lap);
         closure c;
         local_closure(s, fl, s->phi[i], grad, lap, &c);
-        for (int k = 0; k < 3; ++k) s->phiu_prev[(size_t)k * N + i] = s->phi[i] * c.u[k];
+        for (int k = 0; k < 3; ++k) {
+            s->phiu_prev[(size_t)k * N + i] = s->phi[i] * c.u[k];
+            s->u_prev[(size_t)k * N + i] = c.u[k]; /* V1: the previous u before the first step */
+        }
     }
 }
 
@@ -901,9 +958,11 @@ static void cell_macro(const lbmo *s, long i, macro *m)
     closure c;
     local_closure(s, fl, s->phi[i], grad, lap, &c);
     m->rho = c.rho;
-    /* p_h = P + sum(Xi)/2 with sum(Xi) = cs2 u . grad(rho) */
+    /* p_h = P + sum(Xi)/2 with sum(Xi) = cs2 u . grad(rho) (+ cs2 rho div(u) of
+     * the stored previous u with LBMO_FLAG_DIVU: what the next step uses) */
     double ug = c.u[0] * c.gradrho[0] + c.u[1] * c.gradrho[1] + c.u[2] * c.gradrho[2];
     m->p = c.P + 0.5 * CS2 * ug;
+    if (s->phys.flags & LBMO_FLAG_DIVU) m->p += 0.5 * CS2 * c.rho * div_cell(s, s->u_prev, x, y, z);
     for (int k = 0; k < 3; ++k) m->u[k] = c.u[k];
 }
 

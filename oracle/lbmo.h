@@ -52,7 +52,11 @@ enum {
     /* phase field on D3Q7 / D2Q5 with the first-order equilibrium and the
      * correction term C_bar of Sec. 2.2 (instead of the second-order
      * equilibrium on the flow lattice) */
-    LBMO_FLAG_PHASE_REDUCED = 1u << 3
+    LBMO_FLAG_PHASE_REDUCED = 1u << 3,
+    /* keep the w cs2 rho div(u) term of Xi (Sec. 2.3) with div(u) the
+     * isotropic difference of the previous step's velocity (alternative to
+     * reading A6, which drops it) */
+    LBMO_FLAG_DIVU = 1u << 4
 };
 
 typedef struct {
@@ -124,8 +128,15 @@ void lbmo_collide_cell(const lbmo *s, const double *f, const double *g, double p
  * receives this step's phi u at diag[14..16]. */
 void lbmo_collide_cell_prev(const lbmo *s, const double *f, const double *g, double phi, const double grad[3],
                             double lap, const double *phiu_prev, double *fout, double *gout, double *diag);
+/* the same with div(u) for the w cs2 rho div(u) term of Xi (LBMO_FLAG_DIVU) */
+void lbmo_collide_cell_ex(const lbmo *s, const double *f, const double *g, double phi, const double grad[3],
+                          double lap, const double *phiu_prev, double divu, double *fout, double *gout, double *diag);
 /* number of phase-field populations of s (Qg) */
 int lbmo_phase_q(const lbmo *s);
+/* div(u) = (1/cs2) sum_a w_a c_a . u(x + c_a) of a velocity field u ([k][cell],
+ * k < 3) on the grid of s; across a wall the ghost velocity is minus the wall
+ * cell's (no slip), elsewhere periodic */
+void lbmo_divu(const lbmo *s, const double *u, double *div);
 unsigned long long lbmo_splitmix64(unsigned long long seed, unsigned long long counter);
 
 #ifdef __cplusplus

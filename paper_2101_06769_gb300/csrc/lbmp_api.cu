@@ -119,6 +119,8 @@ void free_handle(lbmp_handle* h)
     }
     if (h->phi) cudaFree(h->phi);
     if (h->phiu) cudaFree(h->phiu);
+    for (int k = 0; k < 2; ++k)
+        if (h->uvel[k]) cudaFree(h->uvel[k]);
     if (h->red) cudaFree(h->red);
     if (h->red_out) cudaFree(h->red_out);
     delete h;
@@ -188,7 +190,10 @@ int lbmp_create(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* 
     // shifted codes are staged as 32-bit words holding two neighbouring cells
     if (params->storage != LBMP_FP32 && (grid->nx & 1))
         return fail(LBMP_ERR_INVALID_ARG, "16-bit storage needs an even nx");
-    if (params->flags & ~15u) return fail(LBMP_ERR_INVALID_ARG, "unknown flag bits");
+    if (params->flags & ~31u) return fail(LBMP_ERR_INVALID_ARG, "unknown flag bits");
+    if ((params->flags & LBMP_FLAG_DIVU) &&
+        (params->storage != LBMP_FP32 || (params->flags & LBMP_FLAG_PHASE_REDUCED)))
+        return fail(LBMP_ERR_UNSUPPORTED, "the divergence term needs FP32 storage and the full phase lattice");
     if ((params->flags & LBMP_FLAG_PHASE_REDUCED) && params->storage != LBMP_FP32)
         return fail(LBMP_ERR_UNSUPPORTED, "the reduced phase lattice is stored in FP32 only");
 
@@ -199,6 +204,7 @@ int lbmp_create(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* 
     h->D = D;
     h->Q = (D == 3) ? 27 : 9;
     h->reduced = (params->flags & LBMP_FLAG_PHASE_REDUCED) != 0;
+    h->divu = (params->flags & LBMP_FLAG_DIVU) != 0;
     h->Qg = h->reduced ? 2 * D + 1 : h->Q;
     h->params = *params;
     h->N = N;
@@ -226,6 +232,7 @@ int lbmp_create(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* 
         if (e != cudaSuccess) break;
     }
     if (e == cudaSuccess && h->reduced) e = cudaMalloc(&h->phiu, lbmp::phiu_bytes(h));
+    for (int k = 0; k < 2 && e == cudaSuccess && h->divu; ++k) e = cudaMalloc(&h->uvel[k], lbmp::uvel_bytes(h));
     if (e == cudaSuccess) e = cudaMalloc(&h->phi, 2 * sizeof(float) * (size_t)N);
     h->red_blocks = 1024;
     if (e == cudaSuccess) e = cudaMalloc(&h->red, sizeof(double) * 4 * h->red_blocks);
@@ -461,7 +468,7 @@ int lbmp_set_state(lbmp_handle* h, const double* f, const double* g)
 size_t lbmp_state_bytes(const lbmp_handle* h)
 {
     if (!h) return 0;
-    return lbmp::set_bytes(h) + lbmp::gset_bytes(h) + lbmp::phiu_bytes(h);
+    return lbmp::set_bytes(h) + lbmp::gset_bytes(h) + lbmp::phiu_bytes(h) + lbmp::uvel_bytes(h);
 }
 
 int lbmp_upload(lbmp_handle* h, const void* host, size_t bytes)
@@ -474,6 +481,10 @@ int lbmp_upload(lbmp_handle* h, const void* host, size_t bytes)
     LBMP_CUDA(cudaMemcpyAsync(h->f[h->parity], src, nf, cudaMemcpyHostToDevice, h->stream), "upload f");
     LBMP_CUDA(cudaMemcpyAsync(h->g[h->parity], src + nf, ng, cudaMemcpyHostToDevice, h->stream), "upload g");
     if (nu) LBMP_CUDA(cudaMemcpyAsync(h->phiu, src + nf + ng, nu, cudaMemcpyHostToDevice, h->stream), "upload phi u");
+    const size_t nv = lbmp::uvel_bytes(h);
+    if (nv)
+        LBMP_CUDA(cudaMemcpyAsync(h->uvel[h->parity], src + nf + ng + nu, nv, cudaMemcpyHostToDevice, h->stream),
+                  "upload u");
     return LBMP_OK;
 }
 
@@ -487,6 +498,10 @@ int lbmp_download(lbmp_handle* h, void* host, size_t bytes)
     LBMP_CUDA(cudaMemcpyAsync(dst, h->f[h->parity], nf, cudaMemcpyDeviceToHost, h->stream), "download f");
     LBMP_CUDA(cudaMemcpyAsync(dst + nf, h->g[h->parity], ng, cudaMemcpyDeviceToHost, h->stream), "download g");
     if (nu) LBMP_CUDA(cudaMemcpyAsync(dst + nf + ng, h->phiu, nu, cudaMemcpyDeviceToHost, h->stream), "download phi u");
+    const size_t nv = lbmp::uvel_bytes(h);
+    if (nv)
+        LBMP_CUDA(cudaMemcpyAsync(dst + nf + ng + nu, h->uvel[h->parity], nv, cudaMemcpyDeviceToHost, h->stream),
+                  "download u");
     return LBMP_OK;
 }
 

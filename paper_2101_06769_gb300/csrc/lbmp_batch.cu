@@ -258,7 +258,8 @@ LBMP_API int lbmp_batch_add(lbmp_batch* b, lbmp_handle* h, long steps)
     if (steps <= 0) return batch_fail(LBMP_ERR_INVALID_ARG, "steps must be > 0");
     if (h->device != b->device) return batch_fail(LBMP_ERR_INVALID_ARG, "domain lives on another device");
     if ((int)b->members.size() >= kMaxMembers) return batch_fail(LBMP_ERR_INVALID_ARG, "batch is full");
-    if (h->reduced) return batch_fail(LBMP_ERR_UNSUPPORTED, "reduced phase lattice domains are not batch members");
+    if (h->reduced || h->divu)
+        return batch_fail(LBMP_ERR_UNSUPPORTED, "reduced phase lattice and divergence-term domains are not batch members");
     size_t used = 0;
     for (const Member& m : b->members) {
         if (m.h == h) return batch_fail(LBMP_ERR_INVALID_ARG, "domain is already a member");

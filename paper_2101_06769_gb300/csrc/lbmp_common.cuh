@@ -57,6 +57,7 @@ enum : unsigned {
     kFlagDynamicVisc = 1u << 1,
     kFlagUniformForce = 1u << 2,
     kFlagPhaseReduced = 1u << 3,
+    kFlagDivU = 1u << 4,
 };
 
 // Lattice of the phase field g.  PR = false: the flow lattice with the
@@ -624,14 +625,18 @@ struct CellState {
     float uu;          // |u|^2
     float ew[3][3];    // per-axis product-equilibrium deviation e_d(c) - w1(c), [axis][c+1]
     float phi, sharp;  // phi and lambda_phi 4 phi (1-phi)/W
+    float sdiv;        // kFlagDivU: cs2 rho div(u), the zeroth moment of the w cs2 rho div(u) term of Xi
 };
 
 // Local closure (Sec. 2.1/2.3; readings A1, A2, A7, A12, A13, A15): density,
 // interface normal, chemical potential, force, velocity and p_h of one cell
 // into s (every field but ew); returns rho.  Also the observables use it.
-template <int D>
+// DV (kFlagDivU): Xi keeps its w cs2 rho div(u) term (Sec. 2.3), with divu
+// given by the caller; it adds cs2 rho div(u)/2 to p_h.
+template <int D, bool DV = false>
 __device__ __forceinline__ float flow_closure(const DevParams& p, float phi, const float grad[3], float lap,
-                                              const FlowMoments& m, CellState& s, float& inv_rho, float& nu)
+                                              const FlowMoments& m, CellState& s, float& inv_rho, float& nu,
+                                              float divu = 0.f)
 {
     const float rho = p.rho_l + p.drho * phi;
     inv_rho = 1.0f / rho;
@@ -665,6 +670,10 @@ __device__ __forceinline__ float flow_closure(const DevParams& p, float phi, con
     s.uu = ux * ux + uy * uy + uz * uz;
     s.rcs2 = rho / 3.0f;
     s.ph = m.P + 0.5f * s.uG;
+    if constexpr (DV) {
+        s.sdiv = s.rcs2 * divu;
+        s.ph = m.P + 0.5f * (s.uG + s.sdiv);
+    }
     s.phi = phi;
     s.sharp = p.lam_sharp * phi * (1.0f - phi);
     return rho;
@@ -673,12 +682,12 @@ __device__ __forceinline__ float flow_closure(const DevParams& p, float phi, con
 // The closure above and the relaxed second-order deviations.  Produces the
 // 27-entry Kronecker inverse of the post-collision moment differences in
 // dh[] (h* - E(u)).
-template <int D>
+template <int D, bool DV = false>
 __device__ __forceinline__ void flow_collide(const DevParams& p, float phi, const float grad[3], float lap,
-                                             const FlowMoments& m, CellState& s, float dh[27])
+                                             const FlowMoments& m, CellState& s, float dh[27], float divu = 0.f)
 {
     float inv_rho, nu;
-    flow_closure<D>(p, phi, grad, lap, m, s, inv_rho, nu);
+    flow_closure<D, DV>(p, phi, grad, lap, m, s, inv_rho, nu, divu);
     const float omega = 1.0f / (3.0f * nu + 0.5f);
     const float om1 = 1.0f - omega;
     const float ux = s.u[0], uy = s.u[1], uz = s.u[2];
@@ -935,13 +944,16 @@ struct NoPhiU {
 
 // PR: g on the reduced phase lattice (gin / gout index its slots), with
 // dphiu(s, d) giving d/dt(phi u) of the cell for the correction term.
-template <int D, bool PR = false, class GSrc, class Out, class DH, class DPhiU = NoPhiU>
+// DV: the w cs2 rho div(u) term of Xi (s.sdiv from flow_closure<D, true>):
+// half of it reaches f'* through p_h, half through Xi/2.
+template <int D, bool PR = false, bool DV = false, class GSrc, class Out, class DH, class DPhiU = NoPhiU>
 __device__ __forceinline__ void collide_outputs(const DevParams& p, const CellState& s, const DH& dh,
                                                 const FlowMoments& m, const GSrc& gin, float gsum_hi,
                                                 float gsum_lo, const Out& fout, const Out& gout,
                                                 const DPhiU& dphiu_fn = DPhiU{})
 {
     static_assert(!(PR && Out::kTotal), "the reduced phase lattice is stored in FP32 only");
+    static_assert(!(DV && Out::kTotal), "the divergence term is supported with FP32 storage only");
     constexpr int Q = Lat<D>::Q;
     constexpr int C = Q / 2;
     const float2 rcs2 = f2(s.rcs2, s.rcs2);
@@ -966,7 +978,8 @@ __device__ __forceinline__ void collide_outputs(const DevParams& p, const CellSt
         const float cF0 = cx * s.F[0] + cy * s.F[1] + cz * s.F[2];
         const float2 cG = fma2(pm1, f2(cG0, cG0), f2(-s.uG, -s.uG));
         const float2 cF = fma2(pm1, f2(cF0, cF0), f2(-s.uF, -s.uF));
-        const float2 xi = fma2(gd, cG, mul2(wgd, cF));
+        float2 xi = fma2(gd, cG, mul2(wgd, cF));
+        if constexpr (DV) xi = add2(xi, f2(w * s.sdiv, w * s.sdiv));
         // E(u) - w telescoped over the axes, lanes (c, -c)
         const float2 exs = f2(s.ew[0][cx + 1], s.ew[0][1 - cx]);
         const float2 eys = f2(s.ew[1][cy + 1], s.ew[1][1 - cy]);
@@ -1032,7 +1045,7 @@ __device__ __forceinline__ void collide_outputs(const DevParams& p, const CellSt
         fout.finish(m.P, s.uG);
         gout.finish(gsum_hi, gsum_lo);
     } else {
-        fout(C, (m.P + s.uG) - (fs.x + fs.y));
+        fout(C, (DV ? (m.P + s.uG) + s.sdiv : m.P + s.uG) - (fs.x + fs.y));
         float t = gs.x + gs.y;  // combine the lanes exactly
         const float bb = t - gs.x;
         const float e = (gs.x - (t - bb)) + (gs.y - bb);

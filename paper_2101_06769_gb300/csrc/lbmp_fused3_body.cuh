@@ -322,9 +322,9 @@ LaunchCfg g_cfg;
 
 #if LBMP_FUSED3_WITH_COMMON
 // every domain has a fused kernel (FP32 and shifted 16-bit, D3Q27 and D2Q9;
-// the reduced phase lattice in 3-D) but the reduced phase lattice in 2-D,
-// which runs the reference pair
-bool fused_supported(const lbmp_handle* h) { return !h->reduced || h->D == 3; }
+// the reduced phase lattice in 3-D) but the reduced phase lattice in 2-D and
+// the divergence-term variant, which run the reference pair
+bool fused_supported(const lbmp_handle* h) { return (!h->reduced || h->D == 3) && !h->divu; }
 
 __global__ void batch_epilogue_kernel(BatchDomain* table, int ndom)
 {

@@ -24,6 +24,8 @@ struct lbmp_handle {
     float* g[2];
     float* phi;        // phi = sum g as hi [0, N) + lo [N, 2N), refreshed by the phi pass
     float* phiu;       // reduced phase lattice: phi u of the previous step, [k < D][cell]; else null
+    bool divu;         // LBMP_FLAG_DIVU
+    float* uvel[2];    // LBMP_FLAG_DIVU: stored velocity [k < D][cell], uvel[parity] the previous step's; else null
     int parity;        // f[parity], g[parity] hold the current state
     long step;
     int kernel;        // LBMP_OPT_KERNEL: 0 default, 1 reference pair, 2 bulk-copy staging
@@ -89,6 +91,8 @@ inline size_t gset_bytes(const lbmp_handle* h)
 }
 // bytes of the stored previous phi u (reduced phase lattice)
 inline size_t phiu_bytes(const lbmp_handle* h) { return h->reduced ? sizeof(float) * h->D * (size_t)h->N : 0; }
+// bytes of one stored velocity field (LBMP_FLAG_DIVU)
+inline size_t uvel_bytes(const lbmp_handle* h) { return h->divu ? sizeof(float) * h->D * (size_t)h->N : 0; }
 
 // kernel launchers (return cudaError_t of the launch)
 cudaError_t launch_phi_pass(lbmp_handle* h);

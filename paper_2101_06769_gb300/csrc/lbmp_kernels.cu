@@ -52,12 +52,45 @@ __global__ void phi_pass_kernel(DevParams p, Pop<D, St> g, float* __restrict__ p
 }
 
 // ----------------------------------------------------- reference step
+// kFlagDivU: div(u) = (1/cs2) sum_a w_a c_a . u(x + c_a) of the stored
+// previous velocity us ([k][cell], k < D); a neighbour across a wall is the
+// wall cell's mirror ghost with the velocity reversed (no slip)
+template <int D>
+__device__ __forceinline__ float div_stored(const DevParams& p, const float* __restrict__ us, int x, int y, int z)
+{
+    constexpr int Q = Lat<D>::Q;
+    float acc = 0.f;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
+        const int xx = wrap_h(x + cx, p.nx);
+        long long j;
+        bool across;
+        if (D == 3) {
+            const int zr = z + cz;
+            across = !p.vert_periodic && (zr < 0 || zr >= p.nz);
+            j = ((long long)wrap_v(zr, p.nz, p.vert_periodic) * p.ny + wrap_h(y + cy, p.ny)) * p.nx + xx;
+        } else {
+            const int yr = y + cy;
+            across = !p.vert_periodic && (yr < 0 || yr >= p.ny);
+            j = (long long)wrap_v(yr, p.ny, p.vert_periodic) * p.nx + xx;
+        }
+        float cu = cx * us[j] + cy * us[p.N + j];
+        if (D == 3) cu += cz * us[2 * p.N + j];
+        acc += Lat<D>::w(a) * (across ? -cu : cu);
+    }
+    return 3.0f * acc;
+}
+
 // phiu (reduced phase lattice): phi u of the previous step per cell, [k][cell],
 // read and replaced by this step's value (each cell touches only its own)
+// us_in / us_out (kFlagDivU): the stored velocity of the previous step, read
+// at the neighbours for div(u), and this step's, written per cell
 template <int D, class St, bool PR>
 __global__ void __launch_bounds__(128) step_simple_kernel(DevParams p, Pop<D, St> fin, Pop<D, St> gin,
                                                           Pop<D, St> fout, Pop<D, St> gout,
-                                                          const float* __restrict__ phi, float* __restrict__ phiu)
+                                                          const float* __restrict__ phi, float* __restrict__ phiu,
+                                                          const float* __restrict__ us_in, float* __restrict__ us_out)
 {
     constexpr int Q = Lat<D>::Q;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -80,6 +113,18 @@ __global__ void __launch_bounds__(128) step_simple_kernel(DevParams p, Pop<D, St
     flow_moments<D>(m, fr);
     CellState s;
     float dh[27];
+    if constexpr (!PR && !St::shifted) {
+        if (p.flags & kFlagDivU) {  // the w cs2 rho div(u) term of Xi (Sec. 2.3)
+            flow_collide<D, true>(p, nh[Q / 2], grad, lap, m, s, dh, div_stored<D>(p, us_in, x, y, z));
+            for (int k = 0; k < D; ++k) us_out[k * p.N + i] = s.u[k];
+            float gd[Q];
+#pragma unroll
+            for (int a = 0; a < Q; ++a) gd[a] = pulled_value<D, St>(p, gin, a, x, y, z, i);
+            collide_outputs<D, false, true>(p, s, DhArray{dh}, m, GFromArray{gd}, nh[Q / 2], nl[Q / 2],
+                                            SoAOut{fout.base + i, p.N}, SoAOut{gout.base + i, p.N});
+            return;
+        }
+    }
     flow_collide<D>(p, nh[Q / 2], grad, lap, m, s, dh);
     constexpr int QG = PhaseLat<D, PR>::Q;
     float gr[QG];
@@ -151,7 +196,7 @@ struct StepSimpleL {
         const int s = h->parity, d = 1 - h->parity;
         step_simple_kernel<D, St, PR><<<grid_for(h->N, B), B, 0, h->stream>>>(
             h->dp, pop_of<D, St>(h, h->f[s]), pop_of<D, St>(h, h->g[s]), pop_of<D, St>(h, h->f[d]),
-            pop_of<D, St>(h, h->g[d]), h->phi, h->phiu);
+            pop_of<D, St>(h, h->g[d]), h->phi, h->phiu, h->uvel[s], h->uvel[d]);
         return cudaGetLastError();
     }
 };
@@ -163,10 +208,11 @@ cudaError_t launch_step_simple(lbmp_handle* h)
     return dispatch(h, StepSimpleL{h});
 }
 
-// rho, u and p_h of one cell as the step computes them (defined below)
+// rho, u and p_h of one cell as the step computes them (defined below);
+// ustore: the stored previous velocity for the divergence term, or null
 template <int D, class St>
 __device__ void cell_macro(const DevParams& p, const Pop<D, St>& f, const float* __restrict__ phi, int x, int y,
-                           int z, long long i, float& rho, float u[3], float& ph);
+                           int z, long long i, float& rho, float u[3], float& ph, const float* __restrict__ ustore);
 
 // ---------------------------------------------------- initial conditions
 // splitmix64 (Steele, Lea & Flood 2014): output of the (counter+1)-th call of
@@ -311,17 +357,22 @@ __global__ void init_kernel(DevParams p, InitArgs A, float* __restrict__ f, floa
 // Reduced phase lattice: phi u of every cell from the current state (the u
 // the next step's closure computes), the previous value before the first step
 // after init / set_state.  Needs the phi pass first.
+// The same for the stored velocity of the divergence term (kFlagDivU): the
+// previous velocity before the first step is the current one.
 template <int D>
 __global__ void phiu_reset_kernel(DevParams p, Pop<D, StoreF32> f, const float* __restrict__ phi,
-                                  float* __restrict__ phiu)
+                                  float* __restrict__ phiu, float* __restrict__ ustore)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= p.N) return;
     int x, y, z;
     cell_xyz(p, i, x, y, z);
     float rho, u[3], ph;
-    cell_macro<D, StoreF32>(p, f, phi, x, y, z, i, rho, u, ph);
-    for (int k = 0; k < D; ++k) phiu[k * p.N + i] = phi[i] * u[k];
+    cell_macro<D, StoreF32>(p, f, phi, x, y, z, i, rho, u, ph, nullptr);
+    for (int k = 0; k < D; ++k) {
+        if (phiu) phiu[k * p.N + i] = phi[i] * u[k];
+        if (ustore) ustore[k * p.N + i] = u[k];
+    }
 }
 
 cudaError_t launch_init(lbmp_handle* h, int case_id, const double* args, unsigned long long seed)
@@ -349,7 +400,7 @@ cudaError_t launch_init(lbmp_handle* h, int case_id, const double* args, unsigne
         else
             init_kernel<2, false><<<grid, B, 0, h->stream>>>(h->dp, A, f, g, nullptr, nullptr);
         cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess && h->reduced) e = launch_phiu_reset(h);
+        if (e == cudaSuccess) e = launch_phiu_reset(h);
         return e;
     }
     // shifted storage: canonical FP64 state first, then the per-cell encoder
@@ -482,22 +533,22 @@ struct GetStateL {
 cudaError_t launch_set_state(lbmp_handle* h, const double* dev_f, const double* dev_g)
 {
     cudaError_t e = dispatch(h, SetStateL{h, dev_f, dev_g});
-    if (e == cudaSuccess && h->reduced) e = launch_phiu_reset(h);
+    if (e == cudaSuccess) e = launch_phiu_reset(h);
     return e;
 }
 
 cudaError_t launch_phiu_reset(lbmp_handle* h)
 {
-    if (!h->reduced) return cudaSuccess;
+    if (!h->reduced && !h->divu) return cudaSuccess;
     cudaError_t e = launch_phi_pass(h);
     if (e != cudaSuccess) return e;
     const int B = 128;
     if (h->D == 3)
         phiu_reset_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, pop_of<3, StoreF32>(h, h->f[h->parity]),
-                                                                     h->phi, h->phiu);
+                                                                     h->phi, h->phiu, h->uvel[h->parity]);
     else
         phiu_reset_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, pop_of<2, StoreF32>(h, h->f[h->parity]),
-                                                                     h->phi, h->phiu);
+                                                                     h->phi, h->phiu, h->uvel[h->parity]);
     return cudaGetLastError();
 }
 
@@ -510,7 +561,7 @@ cudaError_t launch_get_state(lbmp_handle* h, double* dev_f, double* dev_g)
 // rho, u and p_h = P + cs2 u.grad(rho)/2 of one cell, as in the step.
 template <int D, class St>
 __device__ void cell_macro(const DevParams& p, const Pop<D, St>& f, const float* __restrict__ phi, int x, int y,
-                           int z, long long i, float& rho, float u[3], float& ph)
+                           int z, long long i, float& rho, float u[3], float& ph, const float* __restrict__ ustore)
 {
     constexpr int Q = Lat<D>::Q;
     float nh[Q], nl[Q];
@@ -529,7 +580,10 @@ __device__ void cell_macro(const DevParams& p, const Pop<D, St>& f, const float*
     flow_moments<D>(m, fr);
     CellState s;
     float inv_rho, nu;
-    rho = flow_closure<D>(p, nh[Q / 2], grad, lap, m, s, inv_rho, nu);
+    if (ustore)
+        rho = flow_closure<D, true>(p, nh[Q / 2], grad, lap, m, s, inv_rho, nu, div_stored<D>(p, ustore, x, y, z));
+    else
+        rho = flow_closure<D>(p, nh[Q / 2], grad, lap, m, s, inv_rho, nu);
     for (int k = 0; k < 3; ++k) u[k] = s.u[k];
     ph = s.ph;
 }
@@ -537,7 +591,7 @@ __device__ void cell_macro(const DevParams& p, const Pop<D, St>& f, const float*
 // per-block partial sums: mass, kinetic energy, max|u|, non-finite count
 template <int D, class St>
 __global__ void __launch_bounds__(256) obs_partial_kernel(DevParams p, Pop<D, St> f, const float* __restrict__ phi,
-                                                          double* __restrict__ part)
+                                                          double* __restrict__ part, const float* __restrict__ ustore)
 {
     __shared__ double sm[4][256];
     double mass = 0.0, ke = 0.0, um = 0.0, bad = 0.0;
@@ -546,7 +600,7 @@ __global__ void __launch_bounds__(256) obs_partial_kernel(DevParams p, Pop<D, St
         int x, y, z;
         cell_xyz(p, i, x, y, z);
         float rho, u[3], ph;
-        cell_macro<D, St>(p, f, phi, x, y, z, i, rho, u, ph);
+        cell_macro<D, St>(p, f, phi, x, y, z, i, rho, u, ph, ustore);
         const double uu = (double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2];
         const double ph_i = (double)phi[i] + (double)phi[p.N + i];
         mass += ph_i;
@@ -608,7 +662,7 @@ __global__ void __launch_bounds__(256) obs_final_kernel(const double* __restrict
 // mean p_h over the 3^D block at a probe cell (one block of threads per probe)
 template <int D, class St>
 __global__ void probe_kernel(DevParams p, Pop<D, St> f, const float* __restrict__ phi, int px, int py, int pz, int qx,
-                             int qy, int qz, double* __restrict__ out)
+                             int qy, int qz, double* __restrict__ out, const float* __restrict__ ustore)
 {
     __shared__ double sm[32];
     const int t = threadIdx.x;
@@ -628,7 +682,7 @@ __global__ void probe_kernel(DevParams p, Pop<D, St> f, const float* __restrict_
         }
         const long long i = ((long long)z * p.ny + y) * p.nx + x;
         float rho, u[3], ph;
-        cell_macro<D, St>(p, f, phi, x, y, z, i, rho, u, ph);
+        cell_macro<D, St>(p, f, phi, x, y, z, i, rho, u, ph, ustore);
         v = ph;
     }
     sm[t] = v;
@@ -667,13 +721,14 @@ struct ObsL {
     cudaError_t run() const
     {
         const Pop<D, St> f = pop_of<D, St>(h, h->f[h->parity]);
-        obs_partial_kernel<D, St><<<h->red_blocks, 256, 0, h->stream>>>(h->dp, f, h->phi, h->red);
+        const float* us = h->uvel[h->parity];  // the velocity the next step's div(u) uses, or null
+        obs_partial_kernel<D, St><<<h->red_blocks, 256, 0, h->stream>>>(h->dp, f, h->phi, h->red, us);
         obs_final_kernel<<<1, 256, 0, h->stream>>>(h->red, h->red_blocks, out);
         if (full) {
             const int nv = (D == 3) ? h->grid.nz : h->grid.ny;
             const int* pr = h->probe;
             probe_kernel<D, St><<<2, 32, 0, h->stream>>>(h->dp, f, h->phi, pr[0], pr[1], D == 3 ? pr[2] : 0, 0, 0,
-                                                         0, out + 4);
+                                                         0, out + 4, us);
             column_kernel<D><<<grid_for(nv, 128), 128, 0, h->stream>>>(h->dp, h->phi, out + 16);
         }
         return cudaGetLastError();
