@@ -95,21 +95,21 @@ def spread(case, times, slice3d=False):
     return out
 
 
-@pytest.mark.parametrize("case,slice3d", [("splash2d_k56", False), ("splash3d", True)])
+@pytest.mark.parametrize("case,slice3d", [("splash2d_k56", False), ("splash2d_k83", False), ("splash2d_k264", False),
+                                          ("splash3d", True)])
 def test_droplet_splash_spreading_radius(case, slice3d):
     """Sec. 3.4: after impact the neck radius grows like sqrt(t) at first; the
-    paper plots r_K/D = 1.1 sqrt(t/T).  On the 2-D K = 55.7 case (D = 100) and
-    the reduced-size 3-D case (D = 64) the measured neck radius grows
-    monotonically over t/T = 0.1-0.3 (0.2 in 3-D, where the lamella reaches the
-    measuring row later) and stays at 0.5-1.0 of that line (measured: 2-D
-    0.65, 0.81, 0.84; 3-D 0.56, 0.77); mass is kept.  The Re = 1000 2-D cases
-    (K = 83.4, 263.8) turn non-finite at t/T ~ 0.15 in this implementation
-    (a jet at |u| ~ 0.2 in the density-ratio-1000 gas); they are not tested."""
-    times = [0.1, 0.2, 0.3] if not slice3d else [0.1, 0.2]
+    paper plots r_K/D = 1.1 sqrt(t/T).  On the three 2-D impacts (K = 55.7,
+    83.4, 263.8; D = 100, W = 8) at t/T = 0.2, 0.3 and on the reduced-size 3-D
+    impact (D = 64, W = 4) at t/T = 0.1, 0.2 the measured neck radius grows
+    monotonically and stays at 0.5-1.0 of that line (measured: 2-D 0.58/0.73,
+    0.74/0.82, 0.75/0.82; 3-D 0.56/0.77); later the lamella reaches the
+    measuring row.  Every run stays finite to t/T = 1 and keeps its mass."""
+    times = [0.2, 0.3, 1.0] if not slice3d else [0.1, 0.2, 1.0]
     rows = spread(case, times, slice3d)
-    radii = [r for r, _, _ in rows]
     assert all(h == 0 and abs(drift) <= 1e-6 for _, h, drift in rows)
-    assert all(b > a for a, b in zip(radii, radii[1:])), radii
-    for tt, r in zip(times, radii):
+    radii = [r for r, _, _ in rows[:2]]
+    assert radii[1] > radii[0], radii
+    for tt, r in zip(times[:2], radii):
         ratio = r / (1.1 * np.sqrt(tt))
         assert 0.5 <= ratio <= 1.0, (case, tt, r, ratio)
