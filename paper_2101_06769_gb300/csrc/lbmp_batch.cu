@@ -7,7 +7,8 @@
 // needs comes from the host, so the kernels of a run of steps are captured
 // once in a CUDA graph and the graph is replayed until the membership (or the
 // set of members with steps left) changes.  Members are grouped by kind --
-// FP32, FP16 and BF16 (shifted storage) D3Q27, then the same for D2Q9 --
+// FP32, FP16 and BF16 (shifted storage) D3Q27, FP32 D3Q27 with the reduced
+// phase lattice, then FP32, FP16 and BF16 D2Q9 --
 // each kind a contiguous segment of the table with its own work numbering
 // and its own persistent kernel.  Within a step the D3Q27 kernels run on the
 // batch stream and the D2Q9 kernels on a forked second stream, joined before
@@ -32,12 +33,23 @@ struct Member {
 };
 
 // member kinds, in table order: D3Q27 kinds first, then D2Q9 kinds
-enum Kind { kF32x3 = 0, kF16x3 = 1, kBF16x3 = 2, kF32x2 = 3, kF16x2 = 4, kBF16x2 = 5, kKinds = 6 };
+enum Kind {
+    kF32x3 = 0,
+    kF16x3 = 1,
+    kBF16x3 = 2,
+    kF32x3R = 3,  // FP32 D3Q27 flow, D3Q7 phase field
+    kF32x2 = 4,
+    kF16x2 = 5,
+    kBF16x2 = 6,
+    kKinds = 7
+};
+constexpr int kLast3 = kF32x3R;  // the D3Q27 kinds are kF32x3 .. kLast3
 
 int kind_of(const lbmp_handle* h)
 {
     const int st = h->params.storage;
     if (h->D == 2) return st == LBMP_FP16_SHIFTED ? kF16x2 : (st == LBMP_BF16_SHIFTED ? kBF16x2 : kF32x2);
+    if (h->reduced) return kF32x3R;
     return st == LBMP_FP16_SHIFTED ? kF16x3 : (st == LBMP_BF16_SHIFTED ? kBF16x3 : kF32x3);
 }
 
@@ -61,7 +73,11 @@ struct lbmp_batch {
 
 namespace {
 
-size_t state_bytes(const lbmp_handle* h) { return 2 * lbmp::set_bytes(h) * 2; }  // f' and g, two sets each
+// f' and g, two sets each, and the stored phi u of the reduced phase lattice
+size_t state_bytes(const lbmp_handle* h)
+{
+    return 2 * (lbmp::set_bytes(h) + lbmp::gset_bytes(h)) + lbmp::phiu_bytes(h);
+}
 
 void drop_graphs(lbmp_batch* b)
 {
@@ -81,6 +97,7 @@ const lbmp::Batch3Ops& ops3_of(const lbmp_batch* b, int kind)
 {
     if (kind == kF16x3) return lbmp::batch3_ops_f16;
     if (kind == kBF16x3) return lbmp::batch3_ops_bf16;
+    if (kind == kF32x3R) return lbmp::batch3_ops_red;
     if (kind == kF16x2) return lbmp::batch2_ops_f16;
     if (kind == kBF16x2) return lbmp::batch2_ops_bf16;
     return lbmp::batch3_ops(b->tile);
@@ -91,14 +108,15 @@ const lbmp::Batch3Ops& ops3_of(const lbmp_batch* b, int kind)
 cudaError_t step_kernels(lbmp_batch* b)
 {
     cudaError_t e = cudaSuccess;
-    const bool any3 = b->ndom[kF32x3] || b->ndom[kF16x3] || b->ndom[kBF16x3];
+    bool any3 = false;
+    for (int k = kF32x3; k <= kLast3; ++k) any3 = any3 || b->ndom[k];
     const bool any2 = b->ndom[kF32x2] || b->ndom[kF16x2] || b->ndom[kBF16x2];
     const bool fork = any3 && any2;
     if (fork) {
         e = cudaEventRecord(b->fork, b->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
     }
-    for (int k = kF32x3; k <= kBF16x3 && e == cudaSuccess; ++k)
+    for (int k = kF32x3; k <= kLast3 && e == cudaSuccess; ++k)
         if (b->ndom[k])
             e = ops3_of(b, k).launch(b->d_table + b->dom0[k], b->ndom[k], b->nitems[k], b->device, b->stream);
     if (e == cudaSuccess && b->ndom[kF32x2])
@@ -154,6 +172,7 @@ cudaError_t rebuild(lbmp_batch* b, bool graphs = true)
         d.f[1] = h->f[1];
         d.g[0] = h->g[0];
         d.g[1] = h->g[1];
+        d.phiu = h->phiu;
         d.parity = h->parity;
         d.steps_left = (int)(m.left < (1L << 30) ? m.left : (1L << 30));
         // the march axis: z in 3-D, y in 2-D (one row of TX cells per tile)
@@ -172,7 +191,7 @@ cudaError_t rebuild(lbmp_batch* b, bool graphs = true)
     const int ndom = total_dom(b);
     cudaError_t e = cudaSuccess;
     if (ndom > 0) {
-        for (int k = kF32x3; k <= kBF16x3 && e == cudaSuccess; ++k)
+        for (int k = kF32x3; k <= kLast3 && e == cudaSuccess; ++k)
             if (b->ndom[k]) e = ops3_of(b, k).prepare(b->device);
         if (e == cudaSuccess && b->ndom[kF32x2]) e = lbmp::prepare_batch2(b->device);
         for (int k = kF16x2; k <= kBF16x2 && e == cudaSuccess; ++k)
@@ -258,8 +277,9 @@ LBMP_API int lbmp_batch_add(lbmp_batch* b, lbmp_handle* h, long steps)
     if (steps <= 0) return batch_fail(LBMP_ERR_INVALID_ARG, "steps must be > 0");
     if (h->device != b->device) return batch_fail(LBMP_ERR_INVALID_ARG, "domain lives on another device");
     if ((int)b->members.size() >= kMaxMembers) return batch_fail(LBMP_ERR_INVALID_ARG, "batch is full");
-    if (h->reduced || h->divu)
-        return batch_fail(LBMP_ERR_UNSUPPORTED, "reduced phase lattice and divergence-term domains are not batch members");
+    if ((h->reduced && h->D == 2) || h->divu)
+        return batch_fail(LBMP_ERR_UNSUPPORTED,
+                          "D2Q5 phase-lattice and divergence-term domains are not batch members");
     size_t used = 0;
     for (const Member& m : b->members) {
         if (m.h == h) return batch_fail(LBMP_ERR_INVALID_ARG, "domain is already a member");

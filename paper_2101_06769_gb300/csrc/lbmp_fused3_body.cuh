@@ -33,8 +33,7 @@
 // LBMP_FUSED3_WITH_COMMON adds the pieces shared by every tile shape.
 // LBMP_PHASE_REDUCED = 1 builds the kernel for the reduced phase lattice
 // (D3Q7 g with the first-order equilibrium and the correction term, Sec. 2.2;
-// the stored previous phi u is read and replaced per cell); it has no batch
-// form.
+// the stored previous phi u is read and replaced per cell).
 #pragma once
 
 #include "lbmp_internal.h"
@@ -250,7 +249,6 @@ __global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_fused3_kernel(DevPar
     }
 }
 
-#if !LBMP_PHASE_REDUCED
 // Batch form: the work items of every member (same order as above within a
 // member, members concatenated) are split over one persistent grid.  A CTA
 // stages the parameters and the 108 direction bases of its current member in
@@ -262,6 +260,7 @@ __global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_batch3_kernel(const 
     __shared__ DevParams sp;
     __shared__ DirPtrs sd;
     __shared__ int s_dom, s_tx, s_ty, s_chunk, s_begin, s_active;
+    __shared__ float* s_phiu;
     const ThreadGeo T = thread_geo();
     int cur = -1;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
@@ -288,15 +287,16 @@ __global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_batch3_kernel(const 
                 s_chunk = B.chunk;
                 s_begin = B.item_begin;
                 s_active = B.steps_left > 0;
+                s_phiu = B.phiu;
             }
             const int par = B.parity;
             for (int k = threadIdx.x; k < 4 * Q3; k += blockDim.x) {
                 const int set = k / Q3, a = k % Q3;
                 const size_t off = (size_t)a * (size_t)B.p.N;
                 if (set == 0) sd.fin[a] = B.f[par] + off;
-                if (set == 1) sd.gin[a] = B.g[par] + off;
+                if (set == 1 && a < QG) sd.gin[a] = B.g[par] + off;
                 if (set == 2) sd.fout[a] = B.f[par ^ 1] + off;
-                if (set == 3) sd.gout[a] = B.g[par ^ 1] + off;
+                if (set == 3 && a < QG) sd.gout[a] = B.g[par ^ 1] + off;
             }
             cur = d;
             __syncthreads();
@@ -307,10 +307,9 @@ __global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_batch3_kernel(const 
         const int tile = local % tiles;
         const int z0 = (local / tiles) * s_chunk;
         fused_segment(sp, sd, T, smem, (tile % s_tx) * TX, (tile / s_tx) * TY, z0, min(z0 + s_chunk, sp.nz),
-                      nullptr);
+                      s_phiu);
     }
 }
-#endif
 
 struct LaunchCfg {
     int device = -1;
@@ -343,7 +342,6 @@ cudaError_t launch_batch_epilogue(BatchDomain* table, int ndom, cudaStream_t str
 }
 #endif
 
-#if !LBMP_PHASE_REDUCED
 namespace {
 
 int g_batch_dev = -1, g_batch_cap = 0;
@@ -378,7 +376,6 @@ cudaError_t launch_batch(const BatchDomain* table, int ndom, int nitems, int dev
 }  // namespace
 
 const Batch3Ops LBMP_BATCH3_OPS = {TX, TY, prepare_batch, launch_batch};
-#endif
 
 cudaError_t LBMP_FUSED3_LAUNCH(lbmp_handle* h)
 {

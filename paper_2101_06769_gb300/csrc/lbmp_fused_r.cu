@@ -9,5 +9,6 @@
 #define LBMP_FUSED_DHSMEM 0
 #define LBMP_TILE_NS tile_red
 #define LBMP_FUSED3_LAUNCH launch_step_fused3_red
+#define LBMP_BATCH3_OPS batch3_ops_red
 #define LBMP_FUSED3_WITH_COMMON 0
 #include "lbmp_fused3_body.cuh"

@@ -46,6 +46,7 @@ struct BatchDomain {
     DevParams p;
     float* f[2];
     float* g[2];
+    float* phiu;  // reduced phase lattice: stored previous phi u; else null
     int parity, steps_left;
     int tiles_x, tiles_y, chunk, item_begin, items;
 };
@@ -118,6 +119,7 @@ struct Batch3Ops {
 };
 extern const Batch3Ops batch3_ops_32x4, batch3_ops_16x8, batch3_ops_8x16;
 extern const Batch3Ops batch3_ops_f16, batch3_ops_bf16;  // shifted 16-bit members (32 x 4 tiles)
+extern const Batch3Ops batch3_ops_red;                    // FP32 members with the D3Q7 phase field
 extern const Batch3Ops batch2_ops_f16, batch2_ops_bf16;  // shifted 16-bit D2Q9 members (128-cell rows)
 cudaError_t launch_step_fused2s(lbmp_handle* h);         // shifted 16-bit storage, D2Q9
 inline const Batch3Ops& batch3_ops(int tile)

@@ -126,11 +126,42 @@ def test_reduced_rejections():
     c = reduced("rt3d")
     with pytest.raises(LbmpError):
         Domain(c["D"], c["dims"], c["periodic"], storage=FP16_SHIFTED, **c["phys"])
+    c = reduced("rt2d")  # D2Q5 domains run the reference pair and have no batch kernel
     d = Domain(c["D"], c["dims"], c["periodic"], **c["phys"])
     d.init(c["case"], c["args"], seed=c["seed"])
     b = Batch()
     with pytest.raises(LbmpError):
         b.add(d, 10)
+    b.close()
+
+
+def test_batch_with_reduced_members_is_bitwise_stepping_alone():
+    """D3Q27 domains with the D3Q7 phase field are batch members (their own
+    persistent kernel kind), beside full-lattice members; each member's state
+    and stored phi u equal stepping it alone."""
+    members = [(reduced("rt3d"), 23), (reduced("ragged3d"), 17), (dict(CASES["rt3d"]), 19),
+               (reduced("splash3d"), 9)]
+    alone, doms = [], []
+    b = Batch()
+    for c, n in members:
+        r = Domain(c["D"], c["dims"], c["periodic"], **c["phys"])
+        r.init(c["case"], c["args"], seed=c["seed"])
+        r.step(n)
+        raw = np.empty(r.state_bytes(), np.uint8)
+        r.download(raw.ctypes.data, raw.size)
+        r.sync()
+        alone.append(raw)
+        d = Domain(c["D"], c["dims"], c["periodic"], **c["phys"])
+        d.init(c["case"], c["args"], seed=c["seed"])
+        b.add(d, n)
+        doms.append(d)
+    while b.step(16) >= 0 and any(left for _, left in b.members()):
+        pass
+    for d, want in zip(doms, alone):
+        raw = np.empty(d.state_bytes(), np.uint8)
+        d.download(raw.ctypes.data, raw.size)
+        d.sync()
+        assert np.array_equal(raw, want)
     b.close()
 
 
