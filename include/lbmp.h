@@ -187,13 +187,17 @@ LBMP_API int lbmp_observables(lbmp_handle *h, lbmp_obs *out);
  * rest and face directions in the same relative order, opposite(r) =
  * Qg-1-r), phi N doubles; any of them may be NULL in get_state. */
 LBMP_API int lbmp_get_state(lbmp_handle *h, double *f, double *g, double *phi);
+/* set_state recomputes phi and, with LBMP_FLAG_PHASE_REDUCED or
+ * LBMP_FLAG_DIVU, takes the stored previous phi u / velocity equal to the
+ * current ones (as lbmp_init does). */
 LBMP_API int lbmp_set_state(lbmp_handle *h, const double *f, const double *g);
 
 /* Raw transfers of the device state in its native storage layout (an opaque
  * byte image, valid only for a handle of the same grid, lattice, storage and
  * flags; with LBMP_FLAG_PHASE_REDUCED it includes the stored phi u, with
- * LBMP_FLAG_DIVU the stored velocity).  Asynchronous on the handle's stream; host memory should be
- * pinned.  bytes must equal lbmp_state_bytes(h). */
+ * LBMP_FLAG_DIVU the stored velocity).  Asynchronous on the handle's
+ * stream; host memory should be pinned.  bytes must equal
+ * lbmp_state_bytes(h). */
 LBMP_API size_t lbmp_state_bytes(const lbmp_handle *h);
 LBMP_API int lbmp_upload(lbmp_handle *h, const void *host, size_t bytes);
 LBMP_API int lbmp_download(lbmp_handle *h, void *host, size_t bytes);
