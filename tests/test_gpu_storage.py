@@ -231,3 +231,42 @@ def test_every_slot_written_shifted(name, kernel, st):
         d.step(1)
         f, g, phi = d.get_state()
         assert np.isfinite(f).all() and np.isfinite(g).all() and np.isfinite(phi).all()
+
+
+# (tips in cells, kinetic energy relative), largest over four time units
+OBS_TOL = {
+    ("rt3d", FP32): (0.01, 1e-3), ("rt2d", FP32): (0.01, 1e-3),
+    ("rt3d", FP16_SHIFTED): (0.01, 2e-3), ("rt2d", FP16_SHIFTED): (0.5, 2e-2),
+    ("rt3d", BF16_SHIFTED): (0.25, 0.12),
+}
+
+
+@pytest.mark.parametrize("name,st", sorted(OBS_TOL))
+def test_rt_observables_vs_oracle_over_four_time_units(name, st):
+    """Per-observable error against the FP64 oracle on the reduced RT cases
+    over four time units T = L/U (3200 / 6400 steps), every T: spike and
+    bubble tips, kinetic energy, mass drift.  Measured (largest over the four
+    samples): FP32 tips 0.0005 (3-D) / 0.0019 (2-D) cells, kinetic energy
+    1.1e-4 / 1.2e-4, drift 3e-9; FP16 tips 0.0023 / 0.25 cells, kinetic
+    energy 7.9e-4 / 1.1e-2, drift 7e-8 / 5.3e-7; BF16 (3-D) tips 0.12 cells,
+    kinetic energy 5.8e-2, drift 2e-8.  The bounds keep a factor of about two
+    on the measurements.  BF16 on the 2-D run is not bounded here: its
+    8-bit codes damp the faster-growing 2-D instability (spike 7.2 cells
+    behind the oracle and kinetic energy -37 % at 4 T, mass drift 3.5e-7),
+    so FP16 is the 16-bit form for such runs."""
+    c = EVEN[name]
+    T = int(round(c["phys"]["L_ref"] / 0.04))
+    o = O.Oracle(c["D"], c["dims"], c["periodic"], **c["phys"])
+    o.init(c["case"], c["args"], seed=c["seed"])
+    d = domain(c, st)
+    d.init(c["case"], c["args"], seed=c["seed"])
+    tip_tol, ke_tol = OBS_TOL[(name, st)]
+    for _ in range(4):
+        o.step(T)
+        d.step(T)
+        ob, og = o.observables(), d.observables()
+        assert og.health == 0
+        assert abs(og.tip_spike - ob.tip_spike) <= tip_tol, (og.tip_spike, ob.tip_spike)
+        assert abs(og.tip_bubble - ob.tip_bubble) <= tip_tol, (og.tip_bubble, ob.tip_bubble)
+        assert abs(og.kinetic_energy / ob.kinetic_energy - 1) <= ke_tol
+        assert abs(og.mass_drift_rel) <= 1e-6
