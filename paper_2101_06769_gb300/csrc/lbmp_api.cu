@@ -344,6 +344,7 @@ int lbmp_step(lbmp_handle* h, long n)
     if (rc) return rc;
     if (n < 0) return fail(LBMP_ERR_INVALID_ARG, "negative step count");
     for (long k = 0; k < n; ++k) {
+        h->dp.step = (unsigned)h->step;
         cudaError_t e = lbmp::launch_step(h);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel");
         h->parity ^= 1;

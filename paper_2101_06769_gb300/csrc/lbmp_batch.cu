@@ -168,6 +168,7 @@ cudaError_t rebuild(lbmp_batch* b, bool graphs = true)
         lbmp::BatchDomain d;
         memset(&d, 0, sizeof d);
         d.p = h->dp;
+        d.p.step = (unsigned)h->step;
         d.f[0] = h->f[0];
         d.f[1] = h->f[1];
         d.g[0] = h->g[0];

@@ -100,6 +100,7 @@ struct DevParams {
     unsigned flags;
     int* status;            // device status word of the handle (kStatus* bits), or null
     unsigned long long wait_ns;  // bound of every wait of a step kernel (nanoseconds)
+    unsigned step;               // index of the step being taken (seeds the stochastic rounding of BF16 codes)
     unsigned test_extra_tx;      // test only: extra bytes expected per staged plane (its wait runs out)
 };
 
@@ -278,15 +279,26 @@ __host__ __device__ constexpr float wden()
 }
 
 struct StoreF32 {
+    static constexpr bool stochastic = false;
     static constexpr bool shifted = false;
 };
 struct StoreF16 {
     static constexpr bool shifted = true;
+    static constexpr bool stochastic = true;  // the step's codes are rounded stochastically (enc_sr)
     static constexpr float S = 1048576.f, s = 1.f / 1048576.f;  // 2^20
     // byte-permute selectors moving the low / high half of a word to bits 0..15
     static constexpr unsigned kSelLo = 0x4410u, kSelHi = 0x4432u;
     __device__ __forceinline__ static unsigned short enc(float q) { return __half_as_ushort(__float2half_rn(q)); }
     __device__ __forceinline__ static float dec(unsigned short c) { return __half2float(__ushort_as_half(c)); }
+    // stochastic rounding: r (13 random bits) is added below the 10 bits an
+    // FP16 significand keeps of q's, then q is rounded toward zero, so q
+    // rounds away from zero with probability equal to the dropped fraction
+    // of an ulp (exact for normal FP16 codes; the scale S keeps codes of
+    // practical deviations out of the subnormal range)
+    __device__ __forceinline__ static unsigned short enc_sr(float q, unsigned r)
+    {
+        return __half_as_ushort(__float2half_rz(__uint_as_float(__float_as_uint(q) + (r & 0x1fffu))));
+    }
     __device__ __forceinline__ static float dec_word(unsigned w, unsigned sel)
     {
         return dec((unsigned short)__byte_perm(w, 0u, sel));
@@ -294,6 +306,7 @@ struct StoreF16 {
 };
 struct StoreBF16 {
     static constexpr bool shifted = true;
+    static constexpr bool stochastic = true;  // the step's codes are rounded stochastically (enc_sr)
     static constexpr float S = 1.f, s = 1.f;  // BF16 has the FP32 exponent range
     // selectors moving the low / high half of a word to bits 16..31 (zeros below)
     static constexpr unsigned kSelLo = 0x1044u, kSelHi = 0x3244u;
@@ -302,6 +315,13 @@ struct StoreBF16 {
         return __bfloat16_as_ushort(__float2bfloat16_rn(q));
     }
     __device__ __forceinline__ static float dec(unsigned short c) { return __uint_as_float((unsigned)c << 16); }
+    // stochastic rounding: q rounds away from zero with probability equal to
+    // the dropped fraction of an ulp (r uniform in [0, 2^16)), so the stored
+    // code is unbiased and an increment below half an ulp is not lost
+    __device__ __forceinline__ static unsigned short enc_sr(float q, unsigned r)
+    {
+        return (unsigned short)((__float_as_uint(q) + (r & 0xffffu)) >> 16);
+    }
     __device__ __forceinline__ static float dec_word(unsigned w, unsigned sel)
     {
         return __uint_as_float(__byte_perm(w, 0u, sel));
@@ -403,6 +423,35 @@ __device__ __forceinline__ float ref_from_total(float th, float tl, float sq)
 // conserved total th + tl in place of the rest value.  off = S v_C/W_C is
 // the cell's rest ratio (the rest value from its formula); sq accumulates
 // s sum_a W_a q_a (exact products, small terms).
+// Seed of the stochastic rounding of the codes a cell writes in one step
+// (set 0: f', 1: g): a 32-bit integer hash (two xor-shift-multiply rounds,
+// Wellons' lowbias32 constants) of the cell index, the set and the step,
+// so that every kernel writing the cell draws the same bits.
+__device__ __forceinline__ unsigned mix32(unsigned h)
+{
+    h ^= h >> 16;
+    h *= 0x7feb352du;
+    h ^= h >> 15;
+    h *= 0x846ca68bu;
+    h ^= h >> 16;
+    return h;
+}
+__device__ __forceinline__ unsigned code_seed(const DevParams& p, long long cell, int set)
+{
+    return mix32((unsigned)cell * 2u + (unsigned)set + mix32(p.step));
+}
+// the code of deviation q for direction a: round to nearest, or
+// stochastically with 16 bits drawn from the cell's (fully mixed) seed and a
+// by one odd multiplication (the high half of (seed ^ a K1) K2)
+template <class St>
+__device__ __forceinline__ unsigned short enc_code(float q, unsigned seed, int a)
+{
+    if constexpr (St::stochastic)
+        return St::enc_sr(q, ((seed ^ ((unsigned)a * 0x9e3779b9u)) * 0x85ebca6bu) >> 16);
+    else
+        return St::enc(q);
+}
+
 template <int D, class St>
 struct EncSoA {  // cell i of a Pop: R at base + i, codes at stride N
     static constexpr bool kTotal = true;
@@ -411,11 +460,12 @@ struct EncSoA {  // cell i of a Pop: R at base + i, codes at stride N
     long long N;
     float off;
     mutable float sq;
+    unsigned seed;  // code_seed of the writer cell (stochastic rounding)
     __device__ __forceinline__ void operator()(int a, float v) const
     {
         constexpr int C = Lat<D>::Q / 2;
         const float W = wint<D>(a);
-        const unsigned short c = St::enc(fmaf(v, St::S / W, -off));
+        const unsigned short c = enc_code<St>(fmaf(v, St::S / W, -off), seed, a);
         q[(a - (a > C)) * N] = c;
         sq += St::dec(c) * (W * St::s);
     }
@@ -429,10 +479,11 @@ struct EncPtr {  // per-direction code arrays (entry C unused), one cell index
     int self;
     float off;
     mutable float sq;
+    unsigned seed;  // code_seed of the writer cell (stochastic rounding)
     __device__ __forceinline__ void operator()(int a, float v) const
     {
         const float W = wint<D>(a);
-        const unsigned short c = St::enc(fmaf(v, St::S / W, -off));
+        const unsigned short c = enc_code<St>(fmaf(v, St::S / W, -off), seed, a);
         qb[a][self] = c;
         sq += St::dec(c) * (W * St::s);
     }

@@ -317,8 +317,8 @@ __device__ __forceinline__ void fused_segment16(const DevParams& p, const DirPtr
             const GFromStrided gin{gS + cur * Q3 * NT + tid, NT};
             float off_f, off_g;
             rest_offsets<3, St>(p, s, dh, gin, off_f, off_g);
-            const EncPtr<3, St> fo{Dp.fout, Dp.rfout, self, off_f, 0.f};
-            const EncPtr<3, St> go{Dp.gout, Dp.rgout, self, off_g, 0.f};
+            const EncPtr<3, St> fo{Dp.fout, Dp.rfout, self, off_f, 0.f, code_seed(p, self, 0)};
+            const EncPtr<3, St> go{Dp.gout, Dp.rgout, self, off_g, 0.f, code_seed(p, self, 1)};
 #if LBMP_FUSED_DHSMEM
 #pragma unroll
             for (int a = 0; a < Q3; ++a) dS[a * NT + tid] = dh[a];

@@ -115,8 +115,10 @@ __device__ __forceinline__ void fused2s_segment(const DevParams& p, const Pop<2,
             rest_offsets<2, St>(p, s, dh, gi, off_f, off_g);
             collide_outputs<2>(
                 p, s, DhArray{dh}, m, gi, nh[C2], nl[C2],
-                EncSoA<2, St>{fout.base + self, (unsigned short*)(fout.base + p.N) + self, p.N, off_f, 0.f},
-                EncSoA<2, St>{gout.base + self, (unsigned short*)(gout.base + p.N) + self, p.N, off_g, 0.f});
+                EncSoA<2, St>{fout.base + self, (unsigned short*)(fout.base + p.N) + self, p.N, off_f, 0.f,
+                              code_seed(p, self, 0)},
+                EncSoA<2, St>{gout.base + self, (unsigned short*)(gout.base + p.N) + self, p.N, off_g, 0.f,
+                              code_seed(p, self, 1)});
         }
         __syncthreads();
         const int t = sP;

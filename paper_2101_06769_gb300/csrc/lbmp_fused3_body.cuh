@@ -331,6 +331,7 @@ __global__ void batch_epilogue_kernel(BatchDomain* table, int ndom)
     if (d < ndom && table[d].steps_left > 0) {
         table[d].parity ^= 1;
         table[d].steps_left -= 1;
+        table[d].p.step += 1;  // seeds the stochastic rounding of the next step's codes
     }
 }
 

@@ -141,8 +141,10 @@ __global__ void __launch_bounds__(128) step_simple_kernel(DevParams p, Pop<D, St
         float off_f, off_g;
         rest_offsets<D, St>(p, s, dh, GFromArray{gr}, off_f, off_g);
         collide_outputs<D>(p, s, DhArray{dh}, m, GFromArray{gr}, nh[Q / 2], nl[Q / 2],
-                           EncSoA<D, St>{fout.base + i, (unsigned short*)(fout.base + p.N) + i, p.N, off_f, 0.f},
-                           EncSoA<D, St>{gout.base + i, (unsigned short*)(gout.base + p.N) + i, p.N, off_g, 0.f});
+                           EncSoA<D, St>{fout.base + i, (unsigned short*)(fout.base + p.N) + i, p.N, off_f, 0.f,
+                                         code_seed(p, i, 0)},
+                           EncSoA<D, St>{gout.base + i, (unsigned short*)(gout.base + p.N) + i, p.N, off_g, 0.f,
+                                         code_seed(p, i, 1)});
     } else {
         collide_outputs<D>(p, s, DhArray{dh}, m, GFromArray{gr}, nh[Q / 2], nl[Q / 2], SoAOut{fout.base + i, p.N},
                            SoAOut{gout.base + i, p.N});

@@ -2,27 +2,19 @@
 cell) against the FP64 oracle and against the FP32 path.
 
 Tolerances.  A stored code carries a deviation q of v_a/W_a from the cell's
-rest ratio with the relative precision of its format (half-ulp 2^-12 for
-FP16, 2^-9 for BF16), so every stored population is perturbed by about
-2^-12 (FP16) or 2^-9 (BF16) of its deviation from the rest-shaped part; the
-reference, totals and arithmetic stay FP32.  Measured errors after 100 steps
-(norm-wise, as in the FP32 parity tests) are at most 7.3e-4 on f' and 8.8e-5
-on g and phi for FP16 -- f' is the pressure-scale family whose deviations
-are largest relative to its maximum -- and 8x that for BF16 (three fewer
-mantissa bits).  The bounds below keep a factor ~2.5 of margin and the same
-ratio 8 between the formats.  Observable-level bars follow the storage
-requirement: Laplace pressure jump within 1 % of the oracle, relative mass
-drift within 1e-6 over the run, and Rayleigh-Taylor tip positions within a
-fraction of a cell of the FP32 run.
-
-One case sits outside those f' figures by construction: ragged2d_even is a
-nearly quiescent walled 2-D field, |f'| <= 5.2e-5 with no pressure level to
-speak of, so f' has no rest-shaped bulk for the shift to cancel and every
-stored f' value carries the format's precision relative to itself.  Its
-100-step f' error then grows toward the coherent bound n u (n = 100 steps,
-u the half-ulp: 2.4e-2 FP16, 0.195 BF16); measured 1.27e-3 (FP16) and
-2.94e-2 (BF16), identical for the fused kernel and the reference pair.  Its
-f' bounds keep the factor ~2 margin over those measurements.
+rest ratio with the relative precision of its format (ulp 2^-11 for FP16,
+2^-8 for BF16), rounded stochastically: each stored population is perturbed
+by up to one ulp of its deviation from the rest-shaped part, without bias;
+the reference, totals and arithmetic stay FP32.  Measured errors after 100
+steps (norm-wise, as in the FP32 parity tests) are at most 1.5e-3 on f' and
+1.0e-4 on g and phi for FP16 -- f' is the pressure-scale family whose
+deviations are largest relative to its maximum; the largest, ragged2d_even,
+is a nearly quiescent walled 2-D field whose f' has no rest-shaped bulk --
+and 1.1e-2 / 1.2e-3 for BF16.  The bounds below keep a factor of about two.
+Observable-level bars follow the storage requirement: Laplace pressure jump
+within 1 % of the oracle, relative mass drift within 1e-6 over the run, and
+Rayleigh-Taylor tip positions within a fraction of a cell of the FP32 run
+and of the oracle.
 """
 import numpy as np
 import pytest
@@ -36,9 +28,8 @@ from test_gpu_parity import CASES, rel_err
 pytestmark = pytest.mark.gpu
 
 STORAGES = {"fp16": FP16_SHIFTED, "bf16": BF16_SHIFTED}
-TOL_F = {"fp16": 2e-3, "bf16": 1.6e-2}     # f'
-TOL_G = {"fp16": 2e-4, "bf16": 1.6e-3}     # g and phi
-TOL_F_CASE = {("ragged2d_even", "fp16"): 3e-3, ("ragged2d_even", "bf16"): 6e-2}
+TOL_F = {"fp16": 3e-3, "bf16": 2.4e-2}     # f'
+TOL_G = {"fp16": 2.5e-4, "bf16": 2.5e-3}   # g and phi
 
 EVEN = dict(CASES)
 for k in [k for k, c in EVEN.items() if c["dims"][0] % 2]:
@@ -112,8 +103,7 @@ def test_step_parity_100_shifted(name, st):
     fo, go, po = o.get_state()
     fg, gg, pg = d.get_state()
     ef, eg, ep = rel_err(fg, fo), rel_err(gg, go), rel_err(pg, po)
-    tf = TOL_F_CASE.get((name, st), TOL_F[st])
-    assert ef <= tf and eg <= TOL_G[st] and ep <= TOL_G[st], (name, st, ef, eg, ep)
+    assert ef <= TOL_F[st] and eg <= TOL_G[st] and ep <= TOL_G[st], (name, st, ef, eg, ep)
 
 
 @pytest.mark.parametrize("st", sorted(STORAGES))
@@ -171,7 +161,7 @@ def test_laplace_jump_vs_oracle(st):
 def test_rt_tips_follow_fp32():
     """Reduced 3-D Rayleigh-Taylor over five time units T = L/U*: spike and
     bubble tips of the 16-bit runs stay within a fraction of a cell of the
-    FP32 run (measured: 0.003 cells FP16, 0.13 cells BF16), mass drift <= 1e-6."""
+    FP32 run (measured: 0.0025 cells FP16, 0.019 cells BF16), mass drift <= 1e-6."""
     c = EVEN["rt3d"]
     T = int(round(c["phys"]["L_ref"] / 0.04))
     tips = {}
@@ -236,8 +226,8 @@ def test_every_slot_written_shifted(name, kernel, st):
 # (tips in cells, kinetic energy relative), largest over four time units
 OBS_TOL = {
     ("rt3d", FP32): (0.01, 1e-3), ("rt2d", FP32): (0.01, 1e-3),
-    ("rt3d", FP16_SHIFTED): (0.01, 2e-3), ("rt2d", FP16_SHIFTED): (0.5, 2e-2),
-    ("rt3d", BF16_SHIFTED): (0.25, 0.12),
+    ("rt3d", FP16_SHIFTED): (0.01, 1e-3), ("rt2d", FP16_SHIFTED): (0.05, 2e-3),
+    ("rt3d", BF16_SHIFTED): (0.03, 2e-3), ("rt2d", BF16_SHIFTED): (0.15, 1e-2),
 }
 
 
@@ -247,13 +237,14 @@ def test_rt_observables_vs_oracle_over_four_time_units(name, st):
     over four time units T = L/U (3200 / 6400 steps), every T: spike and
     bubble tips, kinetic energy, mass drift.  Measured (largest over the four
     samples): FP32 tips 0.0005 (3-D) / 0.0019 (2-D) cells, kinetic energy
-    1.1e-4 / 1.2e-4, drift 3e-9; FP16 tips 0.0023 / 0.25 cells, kinetic
-    energy 7.9e-4 / 1.1e-2, drift 7e-8 / 5.3e-7; BF16 (3-D) tips 0.12 cells,
-    kinetic energy 5.8e-2, drift 2e-8.  The bounds keep a factor of about two
-    on the measurements.  BF16 on the 2-D run is not bounded here: its
-    8-bit codes damp the faster-growing 2-D instability (spike 7.2 cells
-    behind the oracle and kinetic energy -37 % at 4 T, mass drift 3.5e-7),
-    so FP16 is the 16-bit form for such runs."""
+    1.1e-4 / 1.2e-4, drift 3e-9; FP16 tips 0.0027 / 0.019 cells, kinetic
+    energy 1.7e-4 / 2.3e-4, drift 8e-8 / 6.1e-7; BF16 tips 0.019 / 0.074
+    cells, kinetic energy 8.7e-4 / 3.9e-3, drift 2e-8 / 3.4e-7.  The 16-bit
+    codes are rounded stochastically; with round-to-nearest codes the
+    per-step increments of the slowly growing instability below half an
+    ulp were lost, and the 2-D BF16 spike lagged the oracle by 7.2 cells
+    (FP16: 0.25) at 4 T with the kinetic energy 37 % low.  The bounds keep a
+    factor of two to three on the measurements."""
     c = EVEN[name]
     T = int(round(c["phys"]["L_ref"] / 0.04))
     o = O.Oracle(c["D"], c["dims"], c["periodic"], **c["phys"])
