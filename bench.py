@@ -36,6 +36,7 @@ WORKLOADS = _workloads()
 # once (phi is formed on chip and never stored by the fused kernels)
 BYTES_PER_CELL = {3: 2 * (27 + 27) * 4, 2: 2 * (9 + 9) * 4}  # FP32
 # shifted 16-bit storage: per population set one FP32 reference + (Q-1) codes
+HBM_NOMINAL_GBS = 7900.0  # HBM3e nominal bandwidth of the part (context beside the measured peak)
 BYTES_PER_CELL_16 = {3: 2 * 2 * (4 + 26 * 2), 2: 2 * 2 * (4 + 8 * 2)}
 # reduced phase-field lattice (D3Q7 / D2Q5): f' and g read and written once,
 # plus the stored previous phi u (D values) read and written once
@@ -577,7 +578,7 @@ def main():
     achieved = bytes_launch / (kern_ms * 1e-3) / 1e9
     traffic = traffic_per_launch(args.workload, form, cells) if (args.kernel == 0 and not args.grid) else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_kind": peak_kind, "traffic": traffic,
+            "peak_kind": peak_kind, "frac_nominal": achieved / HBM_NOMINAL_GBS, "traffic": traffic,
             "kernel": kernel_name(args, D),
             "bytes_per_cell": bpc}
 
