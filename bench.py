@@ -237,7 +237,7 @@ def kernel_name(args, D):
     if args.storage != "fp32":
         return ("step_fused3s_kernel<Store%s>" if D == 3 else "step_fused2s_kernel<Store%s>") % args.storage.upper()
     if args.phase == "reduced":
-        return "step_fused3_kernel (D3Q7 phase field)" if D == 3 else "phi_pass_kernel + step_simple_kernel"
+        return "step_fused3_kernel (D3Q7 phase field)" if D == 3 else "step_fused2_kernel (D2Q5 phase field)"
     if D == 2:
         return "step_fused2_kernel"
     return "step_fused3b_kernel" if args.kernel == 2 else "step_fused3_kernel"
@@ -311,7 +311,7 @@ def measure_forms(args, wl, stream, peak, pg):
         out["reduced_phase"] = {"mlups": mlups, "ms_per_step": ms, "bytes_per_cell": bpc, "achieved_gbs": gbs,
                                 "frac": gbs / peak, "mass_drift_rel": ob.mass_drift_rel, "steps": n,
                                 "kernel": "step_fused3_kernel (D3Q7 phase field)" if D == 3 else
-                                "step_simple_kernel (D2Q5 phase field)",
+                                "step_fused2_kernel (D2Q5 phase field)",
                                 "traffic": traffic_per_launch(args.workload, "reduced", d.N)}
         d.close()
     # batched form
@@ -565,7 +565,7 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms, mlups = aggregate(t_start.elapsed_time(t_end), cells, args.steps, pg)
     ms_per_step = total_ms / args.steps
-    launches_per_step = 2 if (args.kernel == 1 or (args.phase == "reduced" and D == 2)) else 1
+    launches_per_step = 2 if args.kernel == 1 else 1
 
     # roofline of the step kernel: algorithmic bytes per launch / event time
     peak, peak_kind = load_peaks()

@@ -94,8 +94,7 @@ enum {
      * Sec. 2.2, d/dt(phi u) the backward difference of a stored per-cell
      * phi u (the previous value equals the current one before the first step
      * after lbmp_init / lbmp_set_state).  The flow lattice is unchanged.
-     * FP32 storage only (LBMP_ERR_UNSUPPORTED otherwise); D3Q27 domains
-     * with it are batch members, D2Q9 ones are not. */
+     * FP32 storage only (LBMP_ERR_UNSUPPORTED otherwise). */
     LBMP_FLAG_PHASE_REDUCED = 1u << 3,
     /* Keep the w cs2 rho div(u) term of Xi (Sec. 2.3), which the default
      * reading drops (div u prescribed zero): div(u) is the isotropic
@@ -286,10 +285,9 @@ typedef struct lbmp_batch lbmp_batch;
 LBMP_API int lbmp_batch_create(size_t hbm_budget, void *cuda_stream, lbmp_batch **out);
 LBMP_API int lbmp_batch_destroy(lbmp_batch *b);
 /* Admit h for `steps` more steps (> 0).  Members may be D2Q9 or D3Q27
- * domains in any storage form, and D3Q27 domains with the reduced phase
- * lattice (each lattice, storage and phase-lattice kind runs its own
- * persistent kernel); D2Q9 domains with the reduced phase lattice and
- * domains with LBMP_FLAG_DIVU give LBMP_ERR_UNSUPPORTED.  LBMP_ERR_NOMEM
+ * domains in any storage form and with either phase lattice (each lattice,
+ * storage and phase-lattice kind runs its own persistent kernel); domains
+ * with LBMP_FLAG_DIVU give LBMP_ERR_UNSUPPORTED.  LBMP_ERR_NOMEM
  * when it would exceed the budget, LBMP_ERR_INVALID_ARG when h is already a
  * member or the batch is full (1024 members). */
 LBMP_API int lbmp_batch_add(lbmp_batch *b, lbmp_handle *h, long steps);

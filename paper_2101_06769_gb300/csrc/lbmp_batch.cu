@@ -8,7 +8,8 @@
 // once in a CUDA graph and the graph is replayed until the membership (or the
 // set of members with steps left) changes.  Members are grouped by kind --
 // FP32, FP16 and BF16 (shifted storage) D3Q27, FP32 D3Q27 with the reduced
-// phase lattice, then FP32, FP16 and BF16 D2Q9 --
+// phase lattice, then FP32, FP16 and BF16 D2Q9 and FP32 D2Q9 with the
+// reduced phase lattice --
 // each kind a contiguous segment of the table with its own work numbering
 // and its own persistent kernel.  Within a step the D3Q27 kernels run on the
 // batch stream and the D2Q9 kernels on a forked second stream, joined before
@@ -41,13 +42,15 @@ enum Kind {
     kF32x2 = 4,
     kF16x2 = 5,
     kBF16x2 = 6,
-    kKinds = 7
+    kF32x2R = 7,  // FP32 D2Q9 flow, D2Q5 phase field
+    kKinds = 8
 };
 constexpr int kLast3 = kF32x3R;  // the D3Q27 kinds are kF32x3 .. kLast3
 
 int kind_of(const lbmp_handle* h)
 {
     const int st = h->params.storage;
+    if (h->D == 2 && h->reduced) return kF32x2R;
     if (h->D == 2) return st == LBMP_FP16_SHIFTED ? kF16x2 : (st == LBMP_BF16_SHIFTED ? kBF16x2 : kF32x2);
     if (h->reduced) return kF32x3R;
     return st == LBMP_FP16_SHIFTED ? kF16x3 : (st == LBMP_BF16_SHIFTED ? kBF16x3 : kF32x3);
@@ -110,7 +113,7 @@ cudaError_t step_kernels(lbmp_batch* b)
     cudaError_t e = cudaSuccess;
     bool any3 = false;
     for (int k = kF32x3; k <= kLast3; ++k) any3 = any3 || b->ndom[k];
-    const bool any2 = b->ndom[kF32x2] || b->ndom[kF16x2] || b->ndom[kBF16x2];
+    const bool any2 = b->ndom[kF32x2] || b->ndom[kF16x2] || b->ndom[kBF16x2] || b->ndom[kF32x2R];
     const bool fork = any3 && any2;
     if (fork) {
         e = cudaEventRecord(b->fork, b->stream);
@@ -121,7 +124,10 @@ cudaError_t step_kernels(lbmp_batch* b)
             e = ops3_of(b, k).launch(b->d_table + b->dom0[k], b->ndom[k], b->nitems[k], b->device, b->stream);
     if (e == cudaSuccess && b->ndom[kF32x2])
         e = lbmp::launch_batch2(b->d_table + b->dom0[kF32x2], b->ndom[kF32x2], b->nitems[kF32x2], b->device,
-                                fork ? b->side : b->stream);
+                                fork ? b->side : b->stream, false);
+    if (e == cudaSuccess && b->ndom[kF32x2R])
+        e = lbmp::launch_batch2(b->d_table + b->dom0[kF32x2R], b->ndom[kF32x2R], b->nitems[kF32x2R], b->device,
+                                fork ? b->side : b->stream, true);
     for (int k = kF16x2; k <= kBF16x2 && e == cudaSuccess; ++k)
         if (b->ndom[k])
             e = ops3_of(b, k).launch(b->d_table + b->dom0[k], b->ndom[k], b->nitems[k], b->device,
@@ -159,7 +165,7 @@ cudaError_t rebuild(lbmp_batch* b, bool graphs = true)
     b->dom0[kind] = (int)b->h_table.size();
     const int D = kind >= kF32x2 ? 2 : 3;
     int item = 0;
-    const int TX = kind == kF32x2 ? lbmp::batch2_tile_x() : ops3_of(b, kind).tile_x;
+    const int TX = (kind == kF32x2 || kind == kF32x2R) ? lbmp::batch2_tile_x() : ops3_of(b, kind).tile_x;
     const int TY = D == 3 ? ops3_of(b, kind).tile_y : 1;
     const int chunk = b->chunk > 0 ? b->chunk : 16;
     for (const Member& m : b->members) {
@@ -194,7 +200,8 @@ cudaError_t rebuild(lbmp_batch* b, bool graphs = true)
     if (ndom > 0) {
         for (int k = kF32x3; k <= kLast3 && e == cudaSuccess; ++k)
             if (b->ndom[k]) e = ops3_of(b, k).prepare(b->device);
-        if (e == cudaSuccess && b->ndom[kF32x2]) e = lbmp::prepare_batch2(b->device);
+        if (e == cudaSuccess && b->ndom[kF32x2]) e = lbmp::prepare_batch2(b->device, false);
+        if (e == cudaSuccess && b->ndom[kF32x2R]) e = lbmp::prepare_batch2(b->device, true);
         for (int k = kF16x2; k <= kBF16x2 && e == cudaSuccess; ++k)
             if (b->ndom[k]) e = ops3_of(b, k).prepare(b->device);
         if (e == cudaSuccess)
@@ -278,9 +285,7 @@ LBMP_API int lbmp_batch_add(lbmp_batch* b, lbmp_handle* h, long steps)
     if (steps <= 0) return batch_fail(LBMP_ERR_INVALID_ARG, "steps must be > 0");
     if (h->device != b->device) return batch_fail(LBMP_ERR_INVALID_ARG, "domain lives on another device");
     if ((int)b->members.size() >= kMaxMembers) return batch_fail(LBMP_ERR_INVALID_ARG, "batch is full");
-    if ((h->reduced && h->D == 2) || h->divu)
-        return batch_fail(LBMP_ERR_UNSUPPORTED,
-                          "D2Q5 phase-lattice and divergence-term domains are not batch members");
+    if (h->divu) return batch_fail(LBMP_ERR_UNSUPPORTED, "divergence-term domains are not batch members");
     size_t used = 0;
     for (const Member& m : b->members) {
         if (m.h == h) return batch_fail(LBMP_ERR_INVALID_ARG, "domain is already a member");

@@ -7,7 +7,10 @@
 // (the two side cells by threads 0 and 1).  The step reads one population
 // set and writes the other, so the side reads never race with the
 // neighbouring segment's writes.  The per-cell arithmetic is the shared one
-// of lbmp_common.cuh, as in the reference pair.
+// of lbmp_common.cuh, as in the reference pair.  Templated on PR, the phase
+// field on the reduced lattice D2Q5 (first-order equilibrium and correction
+// term, Sec. 2.2): 5 staged g values, and the stored previous phi u of the
+// staged row copied with them.
 #include "lbmp_internal.h"
 
 namespace lbmp {
@@ -17,7 +20,8 @@ namespace {
 constexpr int TX2 = 128;
 constexpr int Q2 = 9;
 constexpr int RW = TX2 + 2;  // row of phi incl. one side cell each way
-constexpr size_t kSmem2 = sizeof(float) * (2 * Q2 * TX2 + Q2 * 2) + sizeof(float2) * 3 * RW;
+// g of two rows, side cells, and (reduced phase lattice) phi u of two rows
+constexpr size_t kSmem2 = sizeof(float) * (2 * Q2 * TX2 + Q2 * 2 + 2 * 2 * TX2) + sizeof(float2) * 3 * RW;
 
 struct DirPtrs2 {
     const float* fin[Q2];
@@ -74,6 +78,21 @@ __device__ __forceinline__ const float* pulled2(const float* const* base, int a,
     return base[a] + (R.ys[cy + 1] + C.xs[cx + 1]);
 }
 
+// the same for slot r of the phase lattice (PR: D2Q5 slots, opposite QG-1-r)
+template <bool PR>
+__device__ __forceinline__ const float* pulled2_g(const float* const* base, int r, const Col2& C, const Row2& R)
+{
+    if constexpr (!PR) {
+        return pulled2(base, r, C, R);
+    } else {
+        constexpr int QG = PhaseLat<2, true>::Q;
+        const int a = PhaseLat<2, true>::full(r);
+        const int cx = Lat<2>::cx(a), cy = Lat<2>::cy(a);
+        if ((cy == 1 && R.lo) || (cy == -1 && R.hi)) return base[QG - 1 - r] + (R.ys[1] + C.xs[1]);
+        return base[r] + (R.ys[cy + 1] + C.xs[cx + 1]);
+    }
+}
+
 __device__ __forceinline__ int row_src(const DevParams& p, int yy)
 {
     if (yy >= 0 && yy < p.ny) return yy;
@@ -81,45 +100,57 @@ __device__ __forceinline__ int row_src(const DevParams& p, int yy)
     return yy < 0 ? 0 : p.ny - 1;  // mirrored ghost (reading A17)
 }
 
-// stage row yy: own g into gbuf, side cells' g into sbuf, then phi into prow
+// stage row yy: own g into gbuf, side cells' g into sbuf, then phi into
+// prow; PR: also the own cells' stored phi u of that row into ubuf [2][TX2]
+template <bool PR>
 __device__ __forceinline__ void stage_row(const DevParams& p, const DirPtrs2& D, const Col2& own, const Col2& side,
                                           int tid, int yy, float* __restrict__ gbuf, float* __restrict__ sbuf,
-                                          float2* __restrict__ prow)
+                                          float2* __restrict__ prow, const float* __restrict__ phiu,
+                                          float* __restrict__ ubuf)
 {
+    constexpr int QG = PhaseLat<2, PR>::Q;
     Row2 R;
     set_row2(R, p, row_src(p, yy));
 #pragma unroll
-    for (int a = 0; a < Q2; ++a) cp_async4(gbuf + a * TX2 + tid, pulled2(D.gin, a, own, R));
+    for (int r = 0; r < QG; ++r) cp_async4(gbuf + r * TX2 + tid, pulled2_g<PR>(D.gin, r, own, R));
     if (tid < 2) {
 #pragma unroll
-        for (int a = 0; a < Q2; ++a) cp_async4(sbuf + a * 2 + tid, pulled2(D.gin, a, side, R));
+        for (int r = 0; r < QG; ++r) cp_async4(sbuf + r * 2 + tid, pulled2_g<PR>(D.gin, r, side, R));
+    }
+    if constexpr (PR) {
+        const int self = R.ys[1] + own.xs[1];
+        cp_async4(ubuf + tid, phiu + self);
+        cp_async4(ubuf + TX2 + tid, phiu + p.N + self);
     }
     cp_async_commit();
     cp_async_wait_all();
     float hi, lo;
     if (tid < 2) {
-        phi_sum<2>([&](int a) { return sbuf[a * 2 + tid]; }, hi, lo);
+        phi_sum_phase<2, PR>([&](int r) { return sbuf[r * 2 + tid]; }, hi, lo);
         prow[tid == 0 ? 0 : RW - 1] = make_float2(hi, lo);
     }
-    phi_sum<2>([&](int a) { return gbuf[a * TX2 + tid]; }, hi, lo);
+    phi_sum_phase<2, PR>([&](int r) { return gbuf[r * TX2 + tid]; }, hi, lo);
     prow[tid + 1] = make_float2(hi, lo);
 }
 
 // rows [y0, y1) of the segment starting at x0
+template <bool PR>
 __device__ __forceinline__ void fused2_segment(const DevParams& p, const DirPtrs2& D, float* smem, int x0, int y0,
-                                               int y1)
+                                               int y1, float* __restrict__ phiu)
 {
-    float* gS = smem;                               // [2][9][TX2]
-    float* sS = smem + 2 * Q2 * TX2;                // [9][2]
+    constexpr int QG = PhaseLat<2, PR>::Q;
+    float* gS = smem;                               // [2][QG][TX2]
+    float* sS = smem + 2 * Q2 * TX2;                // [QG][2]
     float2* phiS = (float2*)(sS + Q2 * 2);          // [3][RW]
+    float* uS = (float*)(phiS + 3 * RW);            // [2][2][TX2] phi u (PR)
     const int tid = threadIdx.x;
     Col2 own, side;
     set_col2(own, pmod(x0 + tid, p.nx), p.nx);
     set_col2(side, pmod(tid == 0 ? x0 - 1 : x0 + TX2, p.nx), p.nx);
     const bool valid = x0 + tid < p.nx;
     int sP = 0, sC = 1, sN = 2;
-    stage_row(p, D, own, side, tid, y0 - 1, gS + Q2 * TX2, sS, phiS + sP * RW);
-    stage_row(p, D, own, side, tid, y0, gS, sS, phiS + sC * RW);
+    stage_row<PR>(p, D, own, side, tid, y0 - 1, gS + QG * TX2, sS, phiS + sP * RW, phiu, uS + 2 * TX2);
+    stage_row<PR>(p, D, own, side, tid, y0, gS, sS, phiS + sC * RW, phiu, uS);
     for (int y = y0; y < y1; ++y) {
         const int cur = (y - y0) & 1;
         Row2 R;
@@ -127,7 +158,8 @@ __device__ __forceinline__ void fused2_segment(const DevParams& p, const DirPtrs
         float fr[Q2];
 #pragma unroll
         for (int a = 0; a < Q2; ++a) fr[a] = __ldg(pulled2(D.fin, a, own, R));
-        stage_row(p, D, own, side, tid, y + 1, gS + (cur ^ 1) * Q2 * TX2, sS, phiS + sN * RW);
+        stage_row<PR>(p, D, own, side, tid, y + 1, gS + (cur ^ 1) * QG * TX2, sS, phiS + sN * RW, phiu,
+                      uS + (cur ^ 1) * 2 * TX2);
         FlowMoments m;
         flow_moments<2>(m, fr);
         __syncthreads();
@@ -146,8 +178,13 @@ __device__ __forceinline__ void fused2_segment(const DevParams& p, const DirPtrs
             float dh[27];
             flow_collide<2>(p, nh[4], grad, lap, m, s, dh);
             const int self = R.ys[1] + own.xs[1];
-            collide_outputs<2>(p, s, DhArray{dh}, m, GFromStrided{gS + cur * Q2 * TX2 + tid, TX2}, nh[4], nl[4],
-                               PtrOut{D.fout, self}, PtrOut{D.gout, self});
+            if constexpr (PR)
+                collide_outputs<2, true>(p, s, DhArray{dh}, m, GFromStrided{gS + cur * QG * TX2 + tid, TX2}, nh[4],
+                                         nl[4], PtrOut{D.fout, self}, PtrOut{D.gout, self},
+                                         PhiUStaged<2>{p, phiu, self, uS + cur * 2 * TX2 + tid, TX2});
+            else
+                collide_outputs<2>(p, s, DhArray{dh}, m, GFromStrided{gS + cur * Q2 * TX2 + tid, TX2}, nh[4], nl[4],
+                                   PtrOut{D.fout, self}, PtrOut{D.gout, self});
         }
         __syncthreads();
         const int t = sP;
@@ -159,18 +196,21 @@ __device__ __forceinline__ void fused2_segment(const DevParams& p, const DirPtrs
 
 struct Fused2Args {
     int tiles_x, chunk, nitems;
+    float* phiu;  // reduced phase lattice: stored previous phi u; else null
 };
 
+template <bool PR>
 __global__ void __launch_bounds__(TX2) step_fused2_kernel(DevParams p, Fused2Args A, DirPtrs2 D)
 {
     extern __shared__ float smem[];
     for (int item = blockIdx.x; item < A.nitems; item += gridDim.x) {
         const int tile = item % A.tiles_x;
         const int y0 = (item / A.tiles_x) * A.chunk;
-        fused2_segment(p, D, smem, tile * TX2, y0, min(y0 + A.chunk, p.ny));
+        fused2_segment<PR>(p, D, smem, tile * TX2, y0, min(y0 + A.chunk, p.ny), A.phiu);
     }
 }
 
+template <bool PR>
 __global__ void __launch_bounds__(TX2) step_batch2_kernel(const BatchDomain* __restrict__ table, int ndom,
                                                           int nitems)
 {
@@ -178,6 +218,7 @@ __global__ void __launch_bounds__(TX2) step_batch2_kernel(const BatchDomain* __r
     __shared__ DevParams sp;
     __shared__ DirPtrs2 sd;
     __shared__ int s_dom, s_tx, s_chunk, s_begin, s_active;
+    __shared__ float* s_phiu;
     int cur = -1;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         __syncthreads();
@@ -202,15 +243,17 @@ __global__ void __launch_bounds__(TX2) step_batch2_kernel(const BatchDomain* __r
                 s_chunk = B.chunk;
                 s_begin = B.item_begin;
                 s_active = B.steps_left > 0;
+                s_phiu = B.phiu;
             }
             const int par = B.parity;
+            constexpr int QG = PhaseLat<2, PR>::Q;
             for (int k = threadIdx.x; k < 4 * Q2; k += blockDim.x) {
                 const int set = k / Q2, a = k % Q2;
                 const size_t off = (size_t)a * (size_t)B.p.N;
                 if (set == 0) sd.fin[a] = B.f[par] + off;
-                if (set == 1) sd.gin[a] = B.g[par] + off;
+                if (set == 1 && a < QG) sd.gin[a] = B.g[par] + off;
                 if (set == 2) sd.fout[a] = B.f[par ^ 1] + off;
-                if (set == 3) sd.gout[a] = B.g[par ^ 1] + off;
+                if (set == 3 && a < QG) sd.gout[a] = B.g[par ^ 1] + off;
             }
             cur = d;
             __syncthreads();
@@ -219,11 +262,13 @@ __global__ void __launch_bounds__(TX2) step_batch2_kernel(const BatchDomain* __r
         const int local = item - s_begin;
         const int tile = local % s_tx;
         const int y0 = (local / s_tx) * s_chunk;
-        fused2_segment(sp, sd, smem, tile * TX2, y0, min(y0 + s_chunk, sp.ny));
+        fused2_segment<PR>(sp, sd, smem, tile * TX2, y0, min(y0 + s_chunk, sp.ny), s_phiu);
     }
 }
 
-int g_f2_dev = -1, g_f2_per_sm = 0, g_f2_sms = 0, g_b2_dev = -1, g_b2_cap = 0;
+// launch configuration per phase lattice [PR]
+int g_f2_dev[2] = {-1, -1}, g_f2_per_sm[2] = {0, 0}, g_f2_sms[2] = {0, 0}, g_b2_dev[2] = {-1, -1},
+    g_b2_cap[2] = {0, 0};
 
 cudaError_t setup_kernel(const void* fn, int device, int& dev_cached, int& per_sm_out, int& sms_out)
 {
@@ -247,43 +292,56 @@ int batch2_tile_x() { return TX2; }
 
 cudaError_t launch_step_fused2(lbmp_handle* h)
 {
-    cudaError_t e = setup_kernel((const void*)step_fused2_kernel, h->device, g_f2_dev, g_f2_per_sm, g_f2_sms);
+    const int k = h->reduced ? 1 : 0;
+    const void* fn = h->reduced ? (const void*)step_fused2_kernel<true> : (const void*)step_fused2_kernel<false>;
+    cudaError_t e = setup_kernel(fn, h->device, g_f2_dev[k], g_f2_per_sm[k], g_f2_sms[k]);
     if (e != cudaSuccess) return e;
     DirPtrs2 D;
     const int s = h->parity, d = 1 - h->parity;
     for (int a = 0; a < Q2; ++a) {
         const size_t off = (size_t)a * (size_t)h->N;
         D.fin[a] = h->f[s] + off;
-        D.gin[a] = h->g[s] + off;
         D.fout[a] = h->f[d] + off;
-        D.gout[a] = h->g[d] + off;
+        D.gin[a] = a < h->Qg ? h->g[s] + off : nullptr;
+        D.gout[a] = a < h->Qg ? h->g[d] + off : nullptr;
     }
     Fused2Args A;
     A.tiles_x = (h->grid.nx + TX2 - 1) / TX2;
-    const LaunchShape L = launch_shape(h, A.tiles_x, h->grid.ny, g_f2_per_sm, g_f2_sms);
+    const LaunchShape L = launch_shape(h, A.tiles_x, h->grid.ny, g_f2_per_sm[k], g_f2_sms[k]);
     A.chunk = L.chunk;
     A.nitems = L.nitems;
-    step_fused2_kernel<<<L.grid, TX2, kSmem2, h->stream>>>(h->dp, A, D);
+    A.phiu = h->phiu;
+    if (h->reduced)
+        step_fused2_kernel<true><<<L.grid, TX2, kSmem2, h->stream>>>(h->dp, A, D);
+    else
+        step_fused2_kernel<false><<<L.grid, TX2, kSmem2, h->stream>>>(h->dp, A, D);
     return cudaGetLastError();
 }
 
-cudaError_t prepare_batch2(int device)
+cudaError_t prepare_batch2(int device, bool reduced)
 {
-    int per_sm = 0, sms = 0, dev = g_b2_dev;
-    cudaError_t e = setup_kernel((const void*)step_batch2_kernel, device, dev, per_sm, sms);
-    if (e == cudaSuccess && g_b2_dev != device) {
-        g_b2_cap = per_sm * sms;
-        g_b2_dev = device;
+    const int k = reduced ? 1 : 0;
+    const void* fn = reduced ? (const void*)step_batch2_kernel<true> : (const void*)step_batch2_kernel<false>;
+    int per_sm = 0, sms = 0, dev = g_b2_dev[k];
+    cudaError_t e = setup_kernel(fn, device, dev, per_sm, sms);
+    if (e == cudaSuccess && g_b2_dev[k] != device) {
+        g_b2_cap[k] = per_sm * sms;
+        g_b2_dev[k] = device;
     }
     return e;
 }
 
-cudaError_t launch_batch2(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream)
+cudaError_t launch_batch2(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream,
+                          bool reduced)
 {
-    if (g_b2_dev != device) return cudaErrorNotReady;  // prepare_batch2 first
+    const int k = reduced ? 1 : 0;
+    if (g_b2_dev[k] != device) return cudaErrorNotReady;  // prepare_batch2 first
     if (nitems <= 0) return cudaSuccess;
-    const int grid = nitems < g_b2_cap ? nitems : g_b2_cap;
-    step_batch2_kernel<<<grid, TX2, kSmem2, stream>>>(table, ndom, nitems);
+    const int grid = nitems < g_b2_cap[k] ? nitems : g_b2_cap[k];
+    if (reduced)
+        step_batch2_kernel<true><<<grid, TX2, kSmem2, stream>>>(table, ndom, nitems);
+    else
+        step_batch2_kernel<false><<<grid, TX2, kSmem2, stream>>>(table, ndom, nitems);
     return cudaGetLastError();
 }
 

@@ -320,10 +320,10 @@ LaunchCfg g_cfg;
 }  // namespace
 
 #if LBMP_FUSED3_WITH_COMMON
-// every domain has a fused kernel (FP32 and shifted 16-bit, D3Q27 and D2Q9;
-// the reduced phase lattice in 3-D) but the reduced phase lattice in 2-D and
-// the divergence-term variant, which run the reference pair
-bool fused_supported(const lbmp_handle* h) { return (!h->reduced || h->D == 3) && !h->divu; }
+// every domain has a fused kernel (FP32 and shifted 16-bit, D3Q27 and D2Q9,
+// full and reduced phase lattice) but the divergence-term variant, which
+// runs the reference pair
+bool fused_supported(const lbmp_handle* h) { return !h->divu; }
 
 __global__ void batch_epilogue_kernel(BatchDomain* table, int ndom)
 {

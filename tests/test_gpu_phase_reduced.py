@@ -126,21 +126,14 @@ def test_reduced_rejections():
     c = reduced("rt3d")
     with pytest.raises(LbmpError):
         Domain(c["D"], c["dims"], c["periodic"], storage=FP16_SHIFTED, **c["phys"])
-    c = reduced("rt2d")  # D2Q5 domains run the reference pair and have no batch kernel
-    d = Domain(c["D"], c["dims"], c["periodic"], **c["phys"])
-    d.init(c["case"], c["args"], seed=c["seed"])
-    b = Batch()
-    with pytest.raises(LbmpError):
-        b.add(d, 10)
-    b.close()
 
 
 def test_batch_with_reduced_members_is_bitwise_stepping_alone():
-    """D3Q27 domains with the D3Q7 phase field are batch members (their own
-    persistent kernel kind), beside full-lattice members; each member's state
+    """Domains with the D3Q7 / D2Q5 phase field are batch members (their own
+    persistent kernel kinds), beside full-lattice members; each member's state
     and stored phi u equal stepping it alone."""
     members = [(reduced("rt3d"), 23), (reduced("ragged3d"), 17), (dict(CASES["rt3d"]), 19),
-               (reduced("splash3d"), 9)]
+               (reduced("splash3d"), 9), (reduced("rt2d"), 21), (reduced("ragged2d"), 14), (dict(CASES["rt2d"]), 11)]
     alone, doms = [], []
     b = Batch()
     for c, n in members:
