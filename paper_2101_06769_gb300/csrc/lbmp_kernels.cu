@@ -460,7 +460,9 @@ __global__ void set_state_f32_kernel(DevParams p, float* f, float* g, const doub
 }
 
 // Shifted encoding of one writer cell from the canonical values v[a] of the
-// slots it owns (FP64 arithmetic; R from the exact total, see Pop).
+// slots it owns (FP64 arithmetic; R from the exact total, see Pop).  Codes
+// round to nearest here: this rounds a set state once, where the step's
+// stochastic rounding guards against a bias repeated every step.
 template <int D, class St>
 __device__ void encode_cell(const Pop<D, St>& set, long long j, const double* v)
 {
