@@ -111,8 +111,19 @@ void fill_devparams(lbmp_handle* h)
     q.test_extra_tx = 0;
 }
 
+void drop_step_graphs(lbmp_handle* h)
+{
+    for (int k = 0; k < 2; ++k)
+        if (h->step_graph[k]) {
+            cudaGraphExecDestroy(h->step_graph[k]);
+            h->step_graph[k] = nullptr;
+        }
+    h->graph_warm = false;
+}
+
 void free_handle(lbmp_handle* h)
 {
+    drop_step_graphs(h);
     for (int k = 0; k < 2; ++k) {
         if (h->f[k]) cudaFree(h->f[k]);
         if (h->g[k]) cudaFree(h->g[k]);
@@ -164,6 +175,69 @@ cudaError_t launch_step(lbmp_handle* h)
     return launch_step_fused3(h);
 }
 }  // namespace lbmp
+
+namespace {
+
+// Runs of kStepGraph steps are replayed from a CUDA graph captured once per
+// starting parity: for a small domain the host launch cost exceeds the
+// kernel's own time.  kStepGraph is even, so a replay returns to the parity
+// it started from.  Only for FP32 storage (the shifted forms seed their
+// stochastic rounding with the step index, which a replay cannot advance),
+// on a stream of the caller's (the legacy default stream cannot be
+// captured) that is not itself being captured.
+constexpr int kStepGraph = 16;
+
+bool step_graph_usable(lbmp_handle* h)
+{
+    if (h->graph_off || h->params.storage != LBMP_FP32 || !h->stream) return false;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(h->stream, &st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return st == cudaStreamCaptureStatusNone;
+}
+
+// drop the graphs when a launch option they were captured with has changed
+void check_graph_key(lbmp_handle* h)
+{
+    const long long key[6] = {h->kernel, h->opt_chunk, h->opt_ctas, h->opt_tile, (long long)h->dp.wait_ns,
+                              (long long)h->dp.test_extra_tx};
+    if (memcmp(key, h->graph_key, sizeof key) != 0) {
+        drop_step_graphs(h);
+        memcpy(h->graph_key, key, sizeof key);
+    }
+}
+
+// the graph of kStepGraph steps from the current parity (built on first use),
+// or null when capture is not possible
+cudaGraphExec_t step_graph(lbmp_handle* h)
+{
+    const int p0 = h->parity;
+    if (h->step_graph[p0]) return h->step_graph[p0];
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int k = 0; k < kStepGraph && e == cudaSuccess; ++k) {
+            e = lbmp::launch_step(h);
+            h->parity ^= 1;
+        }
+        h->parity = p0;
+        const cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->step_graph[p0], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->step_graph[p0] = nullptr;
+        h->graph_off = true;  // plain launches from now on
+        return nullptr;
+    }
+    return h->step_graph[p0];
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -343,12 +417,27 @@ int lbmp_step(lbmp_handle* h, long n)
     int rc = check_handle(h);
     if (rc) return rc;
     if (n < 0) return fail(LBMP_ERR_INVALID_ARG, "negative step count");
-    for (long k = 0; k < n; ++k) {
+    const bool graphs = n >= kStepGraph && step_graph_usable(h);
+    if (graphs) check_graph_key(h);
+    long k = 0;
+    while (k < n) {
+        if (graphs && h->graph_warm && n - k >= kStepGraph) {
+            cudaGraphExec_t g = step_graph(h);
+            if (g) {
+                cudaError_t e = cudaGraphLaunch(g, h->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "step graph");
+                h->step += kStepGraph;
+                k += kStepGraph;
+                continue;
+            }
+        }
         h->dp.step = (unsigned)h->step;
         cudaError_t e = lbmp::launch_step(h);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel");
         h->parity ^= 1;
         h->step += 1;
+        h->graph_warm = true;
+        ++k;
     }
     return LBMP_OK;
 }

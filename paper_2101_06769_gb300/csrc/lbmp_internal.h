@@ -33,6 +33,12 @@ struct lbmp_handle {
     int opt_ctas;      // LBMP_OPT_CTAS_PER_SM: resident CTAs per SM of the grid, 0 = occupancy maximum
     int opt_tile;      // LBMP_OPT_TILE: tile shape of the FP32 D3Q27 fused kernel (0 32x4, 1 16x8, 2 8x16)
     int probe[3];
+    // step graphs (lbmp_step): kStepGraph steps captured from each starting
+    // parity, for the launch options in graph_key; warm once a plain step
+    // ran with those options (the kernels' one-time set-up is not captured)
+    cudaGraphExec_t step_graph[2];
+    long long graph_key[6];
+    bool graph_warm, graph_off;
     // observables scratch (partial sums per block) and result slot
     double* red;
     int red_blocks;

@@ -274,3 +274,29 @@ def test_checkpoint_resume_is_bitwise(name):
     e.step(n)
     for got in (b.get_state(), e.get_state()):
         assert all(np.array_equal(x, y) for x, y in zip(got, want))
+
+
+@pytest.mark.parametrize("name,flags", [("rt3d", 0), ("rt2d", 0), ("ragged3d", 8), ("ragged2d", 8), ("drop2d", 16)])
+def test_step_graphs_are_bitwise_plain_steps(name, flags):
+    """lbmp_step replays runs of 16 steps from a captured CUDA graph on a
+    caller's stream (FP32 storage); the result equals plain launches bitwise,
+    also after a launch option changes between calls (the graphs are
+    recaptured).  flags 8: reduced phase lattice, 16: divergence term."""
+    import torch
+    from paper_2101_06769_gb300.lbmp import OPT_CHUNK
+    c = CASES[name]
+    phys = dict(c["phys"])
+    phys["flags"] = int(phys.get("flags", 0)) | flags
+    s = torch.cuda.Stream()
+    a = Domain(c["D"], c["dims"], c["periodic"], stream=s.cuda_stream, **phys)
+    b = Domain(c["D"], c["dims"], c["periodic"], **phys)  # legacy default stream: plain launches only
+    for d in (a, b):
+        d.init(c["case"], c["args"], seed=c["seed"])
+    a.step(5)
+    a.step(64)
+    a.set_option(OPT_CHUNK, 4)
+    a.step(37)
+    for _ in range(106):
+        b.step(1)
+    a.sync()
+    assert all(np.array_equal(x, y) for x, y in zip(a.get_state(), b.get_state()))
