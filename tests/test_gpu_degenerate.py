@@ -20,10 +20,10 @@ PHYS = dict(rho_ratio=20.0, nu_ratio=2.0, nu_h=0.05, mobility=0.02, width=4.0, s
 @pytest.mark.parametrize("phi0", [0.0, 1.0])
 @pytest.mark.parametrize("D", [2, 3])
 def test_single_phase_rest_state_stays(D, phi0, storage):
-    """A single phase at rest with a uniform pressure: every term of the
-    update vanishes (no gradient of phi, the hydrostatic body force of a
-    bulk phase is balanced by nothing -- so gravity is off here), the state
-    is a fixed point up to the FP32 rounding of the collision."""
+    """A single phase at rest with a uniform pressure and no gravity (a
+    uniform pressure does not balance a body force): no gradient of phi, no
+    force, so the state is a fixed point up to the FP32 rounding of the
+    collision."""
     dims = (16, 12, 10) if D == 3 else (16, 12, 1)
     per = (1, 1, 0) if D == 3 else (1, 0, 1)
     phys = dict(PHYS, g_accel=0.0)
