@@ -242,7 +242,7 @@ LBMP_API int lbmp_set_option(lbmp_handle *h, int option, long value);
 /* Launch-shape autotuner of the fused step kernel (no counterpart in the
  * paper; serving-side tuning).  Times each candidate (tile shape in {32 x 4,
  * 16 x 8, 8 x 16} for the FP32 D3Q27 kernel, planes per work item -- cells
- * per thread per work item -- in {automatic, 4, 8, 16, 32, 64, 128} up to
+ * per thread per work item -- in {automatic, 1, 2, 4, 8, 16, 32, 64, 128} up to
  * the marching extent, CTAs per SM in {maximum, 1, 2}) over `reps` launches
  * (>= 1) after one warm-up launch, with CUDA events on the handle's stream,
  * and keeps the fastest as the handle's options.  Trial launches read the

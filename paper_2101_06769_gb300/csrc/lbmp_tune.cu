@@ -20,9 +20,9 @@ LBMP_API int lbmp_autotune(lbmp_handle* h, int reps, lbmp_tune_entry* table, int
     if (max_entries < 0) return lbmp::set_error(LBMP_ERR_INVALID_ARG, "max_entries must be >= 0");
     if (h->kernel == 1 || !lbmp::fused_supported(h)) return LBMP_OK;
     const int nmarch = h->D == 3 ? h->grid.nz : h->grid.ny;
-    int chunks[8], nc = 0;
+    int chunks[10], nc = 0;
     chunks[nc++] = 0;
-    for (int c = 4; c <= 128; c *= 2)
+    for (int c = 1; c <= 128; c *= 2)  // 1 and 2 for small domains: more work items than SMs
         if (c <= nmarch) chunks[nc++] = c;
     const int ctas[3] = {0, 1, 2};
     // tile shapes exist for the FP32 D3Q27 cp.async kernel only
