@@ -21,7 +21,7 @@ constexpr int TX2 = 128;
 constexpr int Q2 = 9;
 constexpr int RW = TX2 + 2;  // row of phi incl. one side cell each way
 // g of two rows, side cells, and (reduced phase lattice) phi u of two rows
-constexpr size_t kSmem2 = sizeof(float) * (2 * Q2 * TX2 + Q2 * 2 + 2 * 2 * TX2) + sizeof(float2) * 3 * RW;
+constexpr size_t kSmem2 = sizeof(float) * (2 * Q2 * TX2 + Q2 * 2 + 2 * 2 * TX2) + sizeof(float2) * 4 * RW;
 
 struct DirPtrs2 {
     const float* fin[Q2];
@@ -133,7 +133,13 @@ __device__ __forceinline__ void stage_row(const DevParams& p, const DirPtrs2& D,
     prow[tid + 1] = make_float2(hi, lo);
 }
 
-// rows [y0, y1) of the segment starting at x0
+// rows [y0, y1) of the segment starting at x0.  One barrier per row: every
+// shared value but phi is written and read by the same thread, and phi of
+// row yy sits in slot (yy - y0 + 1) & 3 of four, so the row staged in an
+// iteration is never one that a slower thread still reads from the previous
+// one (a thread is at most one iteration ahead: it must pass that
+// iteration's barrier first).  Ends with a barrier, so the caller may reuse
+// shared memory afterwards.
 template <bool PR>
 __device__ __forceinline__ void fused2_segment(const DevParams& p, const DirPtrs2& D, float* smem, int x0, int y0,
                                                int y1, float* __restrict__ phiu)
@@ -141,18 +147,18 @@ __device__ __forceinline__ void fused2_segment(const DevParams& p, const DirPtrs
     constexpr int QG = PhaseLat<2, PR>::Q;
     float* gS = smem;                               // [2][QG][TX2]
     float* sS = smem + 2 * Q2 * TX2;                // [QG][2]
-    float2* phiS = (float2*)(sS + Q2 * 2);          // [3][RW]
-    float* uS = (float*)(phiS + 3 * RW);            // [2][2][TX2] phi u (PR)
+    float2* phiS = (float2*)(sS + Q2 * 2);          // [4][RW]
+    float* uS = (float*)(phiS + 4 * RW);            // [2][2][TX2] phi u (PR)
     const int tid = threadIdx.x;
     Col2 own, side;
     set_col2(own, pmod(x0 + tid, p.nx), p.nx);
     set_col2(side, pmod(tid == 0 ? x0 - 1 : x0 + TX2, p.nx), p.nx);
     const bool valid = x0 + tid < p.nx;
-    int sP = 0, sC = 1, sN = 2;
-    stage_row<PR>(p, D, own, side, tid, y0 - 1, gS + QG * TX2, sS, phiS + sP * RW, phiu, uS + 2 * TX2);
-    stage_row<PR>(p, D, own, side, tid, y0, gS, sS, phiS + sC * RW, phiu, uS);
+    stage_row<PR>(p, D, own, side, tid, y0 - 1, gS + QG * TX2, sS, phiS, phiu, uS + 2 * TX2);
+    stage_row<PR>(p, D, own, side, tid, y0, gS, sS, phiS + RW, phiu, uS);
     for (int y = y0; y < y1; ++y) {
         const int cur = (y - y0) & 1;
+        const int sP = (y - y0) & 3, sC = (y - y0 + 1) & 3, sN = (y - y0 + 2) & 3;
         Row2 R;
         set_row2(R, p, y);
         float fr[Q2];
@@ -186,12 +192,8 @@ __device__ __forceinline__ void fused2_segment(const DevParams& p, const DirPtrs
                 collide_outputs<2>(p, s, DhArray{dh}, m, GFromStrided{gS + cur * Q2 * TX2 + tid, TX2}, nh[4], nl[4],
                                    PtrOut{D.fout, self}, PtrOut{D.gout, self});
         }
-        __syncthreads();
-        const int t = sP;
-        sP = sC;
-        sC = sN;
-        sN = t;
     }
+    __syncthreads();
 }
 
 struct Fused2Args {
@@ -200,7 +202,7 @@ struct Fused2Args {
 };
 
 template <bool PR>
-__global__ void __launch_bounds__(TX2) step_fused2_kernel(DevParams p, Fused2Args A, DirPtrs2 D)
+__global__ void __launch_bounds__(TX2, 7) step_fused2_kernel(DevParams p, Fused2Args A, DirPtrs2 D)
 {
     extern __shared__ float smem[];
     for (int item = blockIdx.x; item < A.nitems; item += gridDim.x) {
