@@ -22,7 +22,7 @@ constexpr int TX2 = 128;
 constexpr int Q2 = 9;
 constexpr int C2 = 4;
 constexpr int RW = TX2 + 2;  // row of phi incl. one side cell each way
-constexpr size_t kSmem2s = sizeof(float) * (2 * Q2 * TX2) + sizeof(float2) * 3 * RW;
+constexpr size_t kSmem2s = sizeof(float) * (2 * Q2 * TX2) + sizeof(float2) * 4 * RW;
 
 __device__ __forceinline__ int pmod(int v, int n)
 {
@@ -67,23 +67,28 @@ __device__ __forceinline__ void stage_row16(const DevParams& p, const Pop<2, St>
     prow[tid + 1] = decode_row_cell<St>(p, g, x_own, row, true, gbuf + tid, TX2);
 }
 
-// rows [y0, y1) of the segment starting at x0
+// rows [y0, y1) of the segment starting at x0.  One barrier per row: the
+// decoded g is private to its thread, and phi of row yy sits in slot
+// (yy - y0 + 1) & 3 of four, so the row staged in an iteration is never one
+// that a slower thread still reads from the previous one (a thread is at
+// most one iteration ahead: it must pass that iteration's barrier first).
+// Ends with a barrier, so the caller may reuse shared memory afterwards.
 template <class St>
 __device__ __forceinline__ void fused2s_segment(const DevParams& p, const Pop<2, St>& fin, const Pop<2, St>& gin,
                                                 const Pop<2, St>& fout, const Pop<2, St>& gout, float* smem, int x0,
                                                 int y0, int y1)
 {
     float* gS = smem;                       // [2][9][TX2] decoded g of the staged rows
-    float2* phiS = (float2*)(gS + 2 * Q2 * TX2);  // [3][RW]
+    float2* phiS = (float2*)(gS + 2 * Q2 * TX2);  // [4][RW]
     const int tid = threadIdx.x;
     const int x_own = pmod(x0 + tid, p.nx);
     const int x_side = pmod(tid == 0 ? x0 - 1 : x0 + TX2, p.nx);
     const bool valid = x0 + tid < p.nx;
-    int sP = 0, sC = 1, sN = 2;
-    stage_row16<St>(p, gin, tid, x_own, x_side, y0 - 1, gS + Q2 * TX2, phiS + sP * RW);
-    stage_row16<St>(p, gin, tid, x_own, x_side, y0, gS, phiS + sC * RW);
+    stage_row16<St>(p, gin, tid, x_own, x_side, y0 - 1, gS + Q2 * TX2, phiS);
+    stage_row16<St>(p, gin, tid, x_own, x_side, y0, gS, phiS + RW);
     for (int y = y0; y < y1; ++y) {
         const int cur = (y - y0) & 1;
+        const int sP = (y - y0) & 3, sC = (y - y0 + 1) & 3, sN = (y - y0 + 2) & 3;
         const long long self = (long long)y * p.nx + x_own;
         float fr[Q2];
 #pragma unroll
@@ -120,12 +125,8 @@ __device__ __forceinline__ void fused2s_segment(const DevParams& p, const Pop<2,
                 EncSoA<2, St>{gout.base + self, (unsigned short*)(gout.base + p.N) + self, p.N, off_g, 0.f,
                               code_seed(p, self, 1)});
         }
-        __syncthreads();
-        const int t = sP;
-        sP = sC;
-        sC = sN;
-        sN = t;
     }
+    __syncthreads();
 }
 
 struct Fused2sArgs {
