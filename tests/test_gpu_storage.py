@@ -129,6 +129,26 @@ def test_fused_and_reference_agree_bitwise_shifted(name, st):
     assert np.array_equal(raw[0], raw[1])
 
 
+@pytest.mark.parametrize("chunk", [1, 2, 3, 7])
+@pytest.mark.parametrize("name", ["drop2d", "rt2d"])
+def test_fused2s_segment_boundaries_bitwise(name, chunk):
+    """The 16-bit D2Q9 kernel with segments of 1, 2, 3 and 7 rows: every
+    segment stages its first rows and the writers' reference rows around
+    them anew (periodic images on the fully periodic drop, the mirrored
+    ghost row on segments that start or end at a wall), and must still equal
+    the reference pair bitwise."""
+    from paper_2101_06769_gb300.lbmp import OPT_CHUNK
+    c = EVEN[name]
+    a, b = domain(c, FP16_SHIFTED), domain(c, FP16_SHIFTED)
+    for dm, k in ((a, 0), (b, 1)):
+        dm.init(c["case"], c["args"], seed=c["seed"])
+        dm.set_kernel(k)
+    a.set_option(OPT_CHUNK, chunk)
+    a.step(9)
+    b.step(9)
+    assert all(np.array_equal(x, y) for x, y in zip(a.get_state(), b.get_state()))
+
+
 @pytest.mark.parametrize("st", sorted(STORAGES))
 def test_mass_drift_steady_drop(st):
     """A converged static drop repeats the same roundings every step, so any
