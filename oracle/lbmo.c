@@ -11,7 +11,7 @@
  * so that a reader can check each step against the paper by eye.  It shares
  * no code with the CUDA library.
  *
- * Readings of the paper taken here (each documented in the design doc):
+ * Readings of the paper taken here, where it is silent, garbled or ambiguous:
  *   A1  mu_phi = 2 beta phi (phi-1)(2phi-1) - kappa lap(phi)       (Sec. 2.1)
  *   A2  force on the fluid = +F_s + F_b, F_s = mu_phi grad(phi)    (Sec. 2.3)
  *   A3  +S_bar on the right-hand side of the g update                (Sec. 2.2)
