@@ -261,7 +261,8 @@ int lbmp_create(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* 
     if (N > (1LL << 31) - 1) return fail(LBMP_ERR_INVALID_ARG, "more than 2^31-1 cells");
     if (params->storage != LBMP_FP32 && params->storage != LBMP_FP16_SHIFTED && params->storage != LBMP_BF16_SHIFTED)
         return fail(LBMP_ERR_INVALID_ARG, "unknown storage form");
-    // shifted codes are staged as 32-bit words holding two neighbouring cells
+    // the D3Q27 16-bit kernel stages codes as 32-bit words holding two
+    // neighbouring cells; the D2Q9 one loads 2-byte codes but keeps the same rule
     if (params->storage != LBMP_FP32 && (grid->nx & 1))
         return fail(LBMP_ERR_INVALID_ARG, "16-bit storage needs an even nx");
     if (params->flags & ~31u) return fail(LBMP_ERR_INVALID_ARG, "unknown flag bits");
