@@ -109,7 +109,7 @@ enum {
 };
 
 typedef struct {
-    int nx, ny, nz;  /* nz = 1 for D2Q9 */
+    int nx, ny, nz;  /* nz = 1 for D2Q9; nx even with FP16/BF16 storage; at most 2^31-1 cells */
     int periodic[3]; /* 1 = periodic; 0 = half-way bounce-back walls (vertical axis only) */
 } lbmp_grid;
 
@@ -169,7 +169,13 @@ LBMP_API int lbmp_get_derived(const lbmp_handle *h, lbmp_derived *out);
 LBMP_API int lbmp_init(lbmp_handle *h, int case_id, const double *case_args, int nargs,
               unsigned long long seed);
 
-/* Advance n time steps (Sec. 2.2/2.3), asynchronously on the handle's stream. */
+/* Advance n time steps (Sec. 2.2/2.3), asynchronously on the handle's stream.
+ * With FP32 storage, n >= 16 and a stream other than the legacy default one
+ * that is not itself being captured, runs of 16 steps replay a CUDA graph
+ * captured once per starting parity after the first plain step (bitwise the
+ * same as plain launches; recaptured when a launch option changes).  FP16/BF16 storage launches step by step: its stochastic
+ * rounding of the codes is seeded with the step index.  Errors: INVALID_ARG
+ * for n < 0. */
 LBMP_API int lbmp_step(lbmp_handle *h, long n);
 
 /* Wait for the handle's stream; reports a device-side error status:
