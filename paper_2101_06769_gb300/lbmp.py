@@ -218,6 +218,12 @@ class Domain:
         _check(load().lbmp_get_state(self._h, f.ctypes.data, g.ctypes.data, phi.ctypes.data))
         return f, g, phi
 
+    def get_phi(self):
+        """phi alone in the exchange format (lbmp_get_state with f and g NULL)"""
+        phi = np.empty(self.shape[1:])
+        _check(load().lbmp_get_state(self._h, None, None, phi.ctypes.data))
+        return phi
+
     def set_state(self, f, g):
         f = np.ascontiguousarray(f, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
