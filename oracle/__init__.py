@@ -52,7 +52,9 @@ _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # LBMO_LIBRARY: a separately built copy (the mutation test builds
+        # oracles with a planted mistake to show that the pins catch it)
+        path = os.environ.get("LBMO_LIBRARY") or _build.build()
         L = C.CDLL(path)
         L.lbmo_create.restype = C.c_void_p
         L.lbmo_create.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(Phys)]

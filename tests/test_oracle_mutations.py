@@ -1,0 +1,97 @@
+"""Pins against planted mistakes: each mutation below changes one sign,
+factor, weight, index or stored value of the oracle (a copy of lbmo.c built
+into a temporary library), and the pin named beside it must then fail.  An
+unmutated build passes the same pins.  The mutated oracles never leave the
+test: they are loaded by child processes through LBMO_LIBRARY."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "lbmo.c")
+
+# name: (first occurrence in lbmo.c, its replacement, pin that must fail)
+MUTATIONS = {
+    # collision of the flow populations (Sec. 2.3) and the closure
+    "velocity_force_half": ("c->u[i] = J[i] / (c->rho * CS2) + c->F[i] / (2.0 * c->rho);",
+                            "c->u[i] = J[i] / (c->rho * CS2) + c->F[i] / c->rho;",
+                            "test_oracle_collision.py::test_moment_identities"),
+    "xi_drops_force": ("Xi[a] = CS2 * (G - L->w[a]) * cmu_grho + cmu_F * G;",
+                       "Xi[a] = CS2 * (G - L->w[a]) * cmu_grho;",
+                       "test_oracle_collision.py::test_moment_identities"),
+    "omega_offset": ("1.0 / (c->nu / CS2 + 0.5);", "1.0 / (c->nu / CS2 + 0.25);",
+                     "test_oracle_collision.py::test_moment_identities"),
+    "mu_laplacian_sign": ("(2.0 * phi - 1.0) - d->kappa * lap;", "(2.0 * phi - 1.0) + d->kappa * lap;",
+                          "test_oracle_collision.py::test_moment_identities"),
+    "body_force_sign": ("c->F[s->vert] -= (c->rho", "c->F[s->vert] += (c->rho",
+                        "test_oracle_collision.py::test_moment_identities"),
+    "trace_equilibrium": ("T -= ob * (T - 3.0 * CS2);", "T -= ob * (T - 3.0);",
+                          "test_oracle_collision.py::test_unit_rates_give_product_equilibrium"),
+    "shear_split_index": ("K[KI(0, 0, 2)] = (T + d1 - 2.0 * d2) / 3.0;", "K[KI(0, 0, 2)] = (T - 2.0 * d1 + d2) / 3.0;",
+                          "test_oracle_collision.py::test_shear_rate_on_second_order_only"),
+    "cumulant4_factor": ("K[KI(2, 2, 0)] = k[KI(2, 2, 0)] - (k200 * k020 + 2.0 * k110 * k110);",
+                         "K[KI(2, 2, 0)] = k[KI(2, 2, 0)] - (k200 * k020 + 1.0 * k110 * k110);",
+                         "test_oracle_cumulants.py::test_forward_cumulants_match_partition_formula"),
+    "cumulant6_cubic_factor": ("double cub = 16.0 * k110 * k101 * k011", "double cub = 8.0 * k110 * k101 * k011",
+                               "test_oracle_cumulants.py::test_forward_cumulants_match_partition_formula"),
+    # phase field (Sec. 2.2)
+    "sharpening_sign": ("+ d->lambda_phi * Lg->w[a] * cn * X + corr;", "- d->lambda_phi * Lg->w[a] * cn * X + corr;",
+                        "test_oracle_collision.py::test_phase_field_collision_moments"),
+    "tau_phi_offset": ("o->tau_phi = o->M / cs2g + 0.5;", "o->tau_phi = o->M / cs2g + 1.0;",
+                       "test_oracle_lattice.py::test_derived_closure"),
+    # reduced phase lattice (Sec. 2.2 alternative, readings P1-P3)
+    "reduced_equilibrium_sign": ("geq = Lg->w[a] * phi * (1.0 + cu / Lg->cs2);",
+                                 "geq = Lg->w[a] * phi * (1.0 - cu / Lg->cs2);",
+                                 "test_oracle_phase_reduced.py::test_reduced_collision_moments"),
+    "correction_factor": ("corr = d->lambda_phi * Lg->w[a] * cd / Lg->cs2;", "corr = Lg->w[a] * cd / Lg->cs2;",
+                          "test_oracle_phase_reduced.py::test_reduced_collision_moments"),
+    "face_weight": ("L->w[L->Q] = moving ? 1.0 / 8.0 : 1.0 / 4.0;", "L->w[L->Q] = moving ? 1.0 / 6.0 : 0.0;",
+                    "test_oracle_phase_reduced.py::test_reduced_lattice"),
+    "phase_lattice_cs2": ("const double cs2g = ((p->flags & LBMO_FLAG_PHASE_REDUCED) && D == 3) ? 0.25 : CS2;",
+                          "const double cs2g = CS2;",
+                          "test_oracle_phase_reduced.py::test_reduced_relaxation_time"),
+    "stored_phi_u": ("for (int k = 0; k < 3; ++k) s->phiu_prev[(size_t)k * N + i] = diag[14 + k];",
+                     "for (int k = 0; k < 3; ++k) s->phiu_prev[(size_t)k * N + i] = 0.0;",
+                     "test_oracle_phase_reduced.py::test_reduced_interface_galilean_invariance"),
+    # divergence term (reading V1)
+    "wall_ghost_sign": ("if ((v < 0 || v >= s->n[k]) && !s->per[k]) sign = -1;",
+                        "if ((v < 0 || v >= s->n[k]) && !s->per[k]) sign = 1;",
+                        "test_oracle_divu.py::test_divergence_wall_ghost_closed_form"),
+    "divergence_factor": ("Xi[a] += L->w[a] * CS2 * c.rho * divu;", "Xi[a] += 0.5 * L->w[a] * CS2 * c.rho * divu;",
+                          "test_oracle_divu.py::test_divergence_term_moments"),
+    "previous_velocity_reset": ("s->u_prev[(size_t)k * N + i] = c.u[k];", "s->u_prev[(size_t)k * N + i] = 0.0;",
+                                "test_oracle_divu.py::test_divergence_step_matches_cellwise"),
+}
+
+
+def _build(source, out):
+    subprocess.run(["gcc", "-std=c11", "-O2", "-fopenmp", "-fPIC", "-shared", "-I", os.path.join(ROOT, "oracle"),
+                    "-o", out, source, "-lm"], check=True)
+
+
+def _pin_passes(lib, pin):
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join("tests", pin), "-q", "-x",
+                        "-p", "no:cacheprovider"], cwd=ROOT, env=dict(os.environ, LBMO_LIBRARY=lib),
+                       capture_output=True, text=True, timeout=600)
+    return r.returncode == 0
+
+
+def test_unmutated_copy_passes_the_pins(tmp_path):
+    lib = str(tmp_path / "liblbmo_ref.so")
+    _build(SRC, lib)
+    for pin in sorted({m[2] for m in MUTATIONS.values()}):
+        assert _pin_passes(lib, pin), pin
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new, pin = MUTATIONS[name]
+    text = open(SRC).read()
+    assert old in text, f"{name}: anchor not found in lbmo.c"
+    src = tmp_path / "lbmo.c"
+    src.write_text(text.replace(old, new, 1))
+    lib = str(tmp_path / "liblbmo_mut.so")
+    _build(str(src), lib)
+    assert not _pin_passes(lib, pin), f"{name} went unnoticed by {pin}"
