@@ -33,7 +33,13 @@
 extern "C" {
 #endif
 
-/* initial-condition cases (reading A18 of the design notes) */
+/* initial-condition cases.  The paper does not give its initial states; both
+ * implementations take phi = (1 + tanh(2 d / W)) / 2 with d the signed
+ * distance into the heavy fluid (RT: d = z - h(x, y), heavy on top;
+ * drop and sheet: the larger of the drop's and the sheet's d), u = 0 except
+ * the falling drop (u = -U0 in its phi-weighted region), p_h = 0 or the
+ * optional hydrostatic / Laplace start, f' = f'_eq(p_h, rho, u) and
+ * g = g_eq(phi, u), plus optional seeded velocity noise. */
 enum {
     LBMO_CASE_RT = 0,          /* args: h0, amplitude, noise [, hydrostatic] */
     LBMO_CASE_DROP_STATIC = 1, /* args: R, p_init(0/1), noise                */

@@ -55,6 +55,34 @@ MUTATIONS = {
     "stored_phi_u": ("for (int k = 0; k < 3; ++k) s->phiu_prev[(size_t)k * N + i] = diag[14 + k];",
                      "for (int k = 0; k < 3; ++k) s->phiu_prev[(size_t)k * N + i] = 0.0;",
                      "test_oracle_phase_reduced.py::test_reduced_interface_galilean_invariance"),
+    # observables and initial states
+    "kinetic_energy_half": ("ke_c[i] = 0.5 * m.rho * uu;", "ke_c[i] = m.rho * uu;",
+                            "test_oracle_observables.py::test_kinetic_energy_closed_forms"),
+    "kinetic_energy_density": ("ke_c[i] = 0.5 * m.rho * uu;", "ke_c[i] = 0.5 * uu;",
+                               "test_oracle_observables.py::test_kinetic_energy_closed_forms"),
+    "max_speed_squared": ("um_c[i] = sqrt(uu);", "um_c[i] = uu;",
+                          "test_oracle_observables.py::test_max_speed_closed_forms"),
+    "spike_tip_weight": ("o->tip_spike = k - (pk - 0.5) / (pk - pm);", "o->tip_spike = k - (pk - 0.5) / (pk + pm);",
+                         "test_oracle_observables.py::test_tip_interpolation_exact_on_linear_columns"),
+    "bubble_tip_index": ("o->tip_bubble = k + (0.5 - pk) / (pp - pk);",
+                         "o->tip_bubble = k + 1 + (0.5 - pk) / (pp - pk);",
+                         "test_oracle_observables.py::test_tip_interpolation_exact_on_linear_columns"),
+    "drop_centre_offset": ("double zc = sheet + 0.5 * Dd + 2.0 * d->W;", "double zc = sheet + 0.5 * Dd + d->W;",
+                           "test_oracle_observables.py::test_drop_sheet_start_geometry"),
+    "drop_radius": ("double d_drop = 0.5 * Dd - sqrt(r2);", "double d_drop = Dd - sqrt(r2);",
+                    "test_oracle_observables.py::test_drop_sheet_start_geometry"),
+    "drop_sheet_union": ("phi = tanh_profile(fmax(d_drop, d_sheet), d->W);",
+                         "phi = tanh_profile(fmin(d_drop, d_sheet), d->W);",
+                         "test_oracle_observables.py::test_drop_sheet_start_geometry"),
+    "hydrostatic_factor": ("p = -d->g_accel * (d->rho_h - d->rho_l) * 0.25 * d->W * lncosh;",
+                           "p = -d->g_accel * (d->rho_h - d->rho_l) * 0.5 * d->W * lncosh;",
+                           "test_oracle_observables.py::test_rt_hydrostatic_start"),
+    "hydrostatic_sign": ("p = -d->g_accel * (d->rho_h - d->rho_l) * 0.25 * d->W * lncosh;",
+                         "p = d->g_accel * (d->rho_h - d->rho_l) * 0.25 * d->W * lncosh;",
+                         "test_oracle_observables.py::test_rt_hydrostatic_start"),
+    "rt_perturbation_y": ("if (D == 3) h += A[1] * cos(2.0 * PI * y / s->n[1]);",
+                          "if (D == 3) h += A[1] * sin(2.0 * PI * y / s->n[1]);",
+                          "test_oracle_observables.py::test_rt_start_interface_and_tips"),
     # divergence term (reading V1)
     "wall_ghost_sign": ("if ((v < 0 || v >= s->n[k]) && !s->per[k]) sign = -1;",
                         "if ((v < 0 || v >= s->n[k]) && !s->per[k]) sign = 1;",
