@@ -8,9 +8,11 @@ reserve), adds it to one lbmp batch, advances the batch a round of steps at a
 time (one persistent kernel per lattice type per step, replayed as a CUDA
 graph), and retires requests as their steps run out: their observables are
 read back, their memory freed, and the freed memory admits waiting requests
-before the next round.  A request whose state becomes non-finite is evicted
-as failed; the others continue.  Work of requests that arrive while others
-are running overlaps on the device.
+before the next round.  After every `health_every` rounds the observables of
+every running request are read; a request whose state has become
+non-finite or unstable (library health word set) is evicted as failed at
+once, its memory freed, and the others continue.  Work of requests that
+arrive while others are running overlaps on the device.
 
 Every arithmetic step runs in the CUDA library; this module only schedules.
 """
@@ -116,8 +118,9 @@ class Server:
     running requests, state_budget), one batch, rounds of `round_steps` steps."""
 
     def __init__(self, stream=None, hbm_reserve=2 << 30, round_steps=64, free_hbm=None, domain_factory=None,
-                 batch=None, state_budget=None):
+                 batch=None, state_budget=None, health_every=1):
         self.stream = stream
+        self.health_every = health_every  # rounds between health checks of the running requests (0: never)
         self.reserve = hbm_reserve
         self.state_budget = state_budget
         self.round_steps = round_steps
@@ -156,12 +159,28 @@ class Server:
             del self.running[r.rid]
             d.close()
 
+    def _evict_unhealthy(self, now):
+        """Evict every running request whose health word is set (non-finite
+        state or a speed beyond the stable range) before it uses more of
+        the batch's kernel time."""
+        for rid, (r, d) in list(self.running.items()):
+            ob = d.observables()
+            if ob.health == 0:
+                continue
+            self.batch.remove(d)
+            r.obs = ob.as_dict()
+            r.status = "failed"
+            r.done = now
+            del self.running[rid]
+            d.close()
+
     def run(self, requests, clock=time.perf_counter, max_wall=None):
         """Serve the requests; returns a summary dict."""
         pending = sorted(requests, key=lambda r: r.arrival)
         t0 = clock()
         k = 0
         cell_updates = 0
+        rounds = 0
         while k < len(pending) or self.running:
             now = clock() - t0
             if max_wall is not None and now > max_wall:
@@ -194,6 +213,9 @@ class Server:
             for rid, l0 in before.items():
                 cell_updates += (l0 - after.get(rid, 0)) * self.running[rid][0].cells
             self._retire(clock() - t0)
+            rounds += 1
+            if self.health_every and rounds % self.health_every == 0:
+                self._evict_unhealthy(clock() - t0)
         wall = clock() - t0
         done = [r for r in pending if r.status == "done"]
         lat = np.array([r.latency() for r in done]) if done else np.array([float("nan")])

@@ -123,6 +123,22 @@ def test_failed_request_is_evicted_and_others_continue():
     assert reqs[3].status == "failed"
 
 
+def test_unhealthy_request_is_evicted_before_its_steps_run_out():
+    """The health of every running request is read after each round: a
+    request that blows up is removed at once (its memory freed, its batch
+    time given back), not when its step count runs out."""
+    reqs = [r for r in small_stream(12, seed=4) if r.steps > 3 * 32]
+    bad = reqs[0]
+    FakeDomain.poison = {bad.seed}
+    try:
+        out, batch = run(reqs, budget=1 << 40)
+    finally:
+        FakeDomain.poison = set()
+    assert bad.status == "failed" and out["failed"] == 1 and out["done"] == len(reqs) - 1
+    assert bad.obs["step"] == 32  # evicted after its first round of 32 steps
+    assert FakeDomain.live_bytes == 0
+
+
 def test_stream_distribution():
     reqs = serve.request_stream(256, seed=7)
     kinds = {r.kind for r in reqs}
