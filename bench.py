@@ -179,18 +179,35 @@ def _oracle_rate(wl, depth, steps):
     return cells * steps / dt / 1e6, dims, dt
 
 
-def cpu_baseline(wl, budget_s=15.0):
-    """The FP64 oracle as it stands, on all host cores, on a bounded sample of
-    the workload: a horizontal slab of the domain (full x and y extent) with
-    the workload's parameters, stepped for about budget_s seconds."""
+def cpu_baseline(wl, budget_s=12.0, max_state_gb=32.0):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of
+    the workload: the full grid (when its FP64 state fits max_state_gb, else
+    a horizontal slab of full x and y extent) with the workload's parameters,
+    stepped on all cores for about budget_s seconds (at least one step), and
+    one step on one thread beside it."""
     import oracle as O
     cores = O.get_threads()
-    depth = min(wl["dims"][2], 64) if wl["D"] == 3 else 1
+    nx, ny, nz = wl["dims"]
+    q = 27 if wl["D"] == 3 else 9
+    per_plane_gb = 2 * 2 * q * 8 * nx * ny / 1e9  # two population sets of f' and g, FP64
+    depth = nz if wl["D"] == 3 else 1
+    if wl["D"] == 3 and depth * per_plane_gb > max_state_gb:
+        depth = max(2, int(max_state_gb / per_plane_gb))
+    what = "full grid" if depth == nz or wl["D"] == 2 else f"{nx}x{ny}x{depth} slab"
     rate, dims, dt = _oracle_rate(wl, depth, 1)
-    steps = max(1, int(budget_s * rate * 1e6 / (dims[0] * dims[1] * dims[2])))
-    rate, dims, dt = _oracle_rate(wl, depth, steps)
+    steps = max(1, int(budget_s / max(dt, 1e-9)))
+    if steps > 1:
+        rate, dims, dt = _oracle_rate(wl, depth, steps)
+    O.set_threads(1)
+    try:
+        rate1, _, dt1 = _oracle_rate(wl, depth, 1)
+    finally:
+        O.set_threads(cores)
     return {"value": rate, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{dims[0]}x{dims[1]}x{dims[2]} slab of the workload, {steps} steps, FP64, {dt:.1f} s"}
+            "sample": f"{what} of the workload ({dims[0]}x{dims[1]}x{dims[2]}), {steps} steps on {cores} threads, "
+                      f"FP64, {dt:.1f} s",
+            "threads_1": {"value": rate1, "unit": "MLUPS", "cores": 1,
+                          "sample": f"{what} of the workload, 1 step on 1 thread, FP64, {dt1:.1f} s"}}
 
 
 def run_reference(args, wl):
