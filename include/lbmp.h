@@ -155,11 +155,36 @@ typedef struct lbmp_handle lbmp_handle;
 
 /* Create a domain.  cuda_stream is a cudaStream_t (NULL = legacy default
  * stream); every later call of the handle is ordered on it.  Allocates the
- * device state (two FP32/FP16/BF16 population sets for f' and g, and a phi
- * field); no device work.  Errors: INVALID_ARG (bad grid or parameters),
- * NOMEM, CUDA.  The caller owns *out and releases it with lbmp_destroy. */
+ * device state with cudaMalloc: two FP32/FP16/BF16 population sets for f'
+ * and g, the stored previous phi u of the reduced phase lattice, the stored
+ * velocities of LBMP_FLAG_DIVU, a phi field (8 bytes per cell) only for the
+ * reference pair (LBMP_OPT_KERNEL = 1, or LBMP_FLAG_DIVU), and a few KiB for
+ * the observables; no device work.  The fused kernels never store phi: the
+ * observables and lbmp_get_state form it in the population set the next
+ * step overwrites.  Errors: INVALID_ARG (bad grid or parameters), NOMEM,
+ * CUDA.  The caller owns *out and releases it with lbmp_destroy. */
 LBMP_API int lbmp_create(const lbmp_grid *grid, lbmp_lattice lattice, const lbmp_params *params,
                 void *cuda_stream, lbmp_handle **out);
+
+/* Caller-supplied device memory (an allocator callback, e.g. a framework's
+ * caching allocator): alloc(bytes, stream, ctx) returns a device pointer to
+ * at least `bytes` bytes, aligned to 256 bytes, usable on `stream` (the
+ * handle's stream), or NULL when it cannot; free(ptr, bytes, stream, ctx)
+ * gives it back.  Every device array a handle keeps for its lifetime comes
+ * from alloc and goes back through free, at lbmp_destroy or when
+ * lbmp_create_ex fails; ctx is passed through unchanged.  Both callbacks are
+ * called from the thread that makes the lbmp call, never from the GPU. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
+    void *ctx;
+} lbmp_allocator;
+
+/* lbmp_create with the handle's device arrays from `allocator` (NULL: as
+ * lbmp_create).  A NULL return of alloc fails the call with LBMP_ERR_NOMEM
+ * after freeing what was already allocated. */
+LBMP_API int lbmp_create_ex(const lbmp_grid *grid, lbmp_lattice lattice, const lbmp_params *params,
+                            void *cuda_stream, const lbmp_allocator *allocator, lbmp_handle **out);
 LBMP_API int lbmp_destroy(lbmp_handle *h);
 LBMP_API const char *lbmp_last_error(void);
 LBMP_API int lbmp_get_derived(const lbmp_handle *h, lbmp_derived *out);
@@ -330,9 +355,51 @@ LBMP_API int lbmp_batch_autotune(lbmp_batch *b, int reps, lbmp_tune_entry *table
  * LBMP_ERR_INVALID_ARG).  Ordered on cuda_stream (NULL = legacy default
  * stream) and synchronises it.  The first call on a device looks up the
  * array's address with that device current: make it before any stream
- * capture.  Every call on a device shares the array, so calls that overlap on
- * the GPU race: serialise them. */
+ * capture.  Later calls outside a capture look it up again (a device reset
+ * moves the array); a call on a capturing stream uses the address of the last
+ * call on that device that was not, and a first call on a capturing stream
+ * returns LBMP_ERR_UNSUPPORTED.  Every call on a device shares the array, so
+ * calls that overlap on the GPU race: serialise them. */
 LBMP_API int lbmp_mass_noalloc(const float *g_dev, long long n_values, double *mass_out, void *cuda_stream);
+
+/* ------------------------------------------------------------ z-slabs
+ * Decomposition of a D3Q27 domain into slabs along z, one per rank (the
+ * paper has no counterpart: this is how the library runs one domain on
+ * several GPUs).  A slab holds the global planes [z_begin, z_end) and, on
+ * every face that borders another slab, two ghost planes; on a face that is
+ * the domain's own wall it keeps the wall (half-way bounce-back, mirrored
+ * phi).  A step updates the slab's own planes only; between steps the
+ * caller moves the populations that cross each face from the neighbour's
+ * boundary planes into this slab's ghost planes (lbmp_pack_planes on the
+ * sender, any transport, lbmp_unpack_planes on the receiver).  With the
+ * ghosts filled every step, the slabs reproduce the undivided domain
+ * bitwise.
+ *
+ * lbmp_create_slab: grid is the whole domain (x and y periodic; z periodic
+ * or walled); 0 <= z_begin < z_end <= grid->nz with at least two planes; a
+ * slab must border at least one other slab.  FP32 storage and the full
+ * phase lattice only, without LBMP_FLAG_DIVU (else LBMP_ERR_UNSUPPORTED).
+ * lbmp_init sets the initial state at the global positions (the same
+ * seeded noise as the undivided domain); lbmp_get_state / lbmp_set_state
+ * exchange the local planes, ghosts included ([a][local z][y][x]);
+ * lbmp_observables reduces over the slab's own planes (mass, kinetic
+ * energy, max |u|; the Laplace probes and tips are NaN: sum and gather
+ * them across ranks).  lbmp_step takes n = 1 only, the fused kernel only
+ * (LBMP_OPT_KERNEL 0); slabs are not batch members. */
+LBMP_API int lbmp_create_slab(const lbmp_grid *grid, int z_begin, int z_end, lbmp_lattice lattice,
+                              const lbmp_params *params, void *cuda_stream, const lbmp_allocator *allocator,
+                              lbmp_handle **out);
+/* layout[0..4] = z_begin, z_end, ghost planes below, ghost planes above,
+ * local nz (the planes of the local arrays); a plain domain reports
+ * 0, nz, 0, 0, nz. */
+LBMP_API int lbmp_slab_layout(const lbmp_handle *h, int *layout);
+/* Copy n whole planes of the current population sets into the device
+ * buffer dev_buf (pack) or back (unpack): plan holds n triples (set: 0 = f',
+ * 1 = g; direction a in the canonical order; local plane z), and triple k
+ * occupies dev_buf[k nx ny, (k+1) nx ny).  n <= 64.  Asynchronous on the
+ * handle's stream; dev_buf is the caller's device memory. */
+LBMP_API int lbmp_pack_planes(lbmp_handle *h, const int *plan, int n, float *dev_buf);
+LBMP_API int lbmp_unpack_planes(lbmp_handle *h, const int *plan, int n, const float *dev_buf);
 
 #ifdef __cplusplus
 }

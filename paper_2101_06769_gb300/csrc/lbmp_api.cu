@@ -7,6 +7,8 @@
 
 #include <new>
 
+#include <limits>
+
 #include "lbmp_internal.h"
 
 namespace {
@@ -91,6 +93,12 @@ void fill_devparams(lbmp_handle* h)
     q.ny = h->grid.ny;
     q.nz = h->grid.nz;
     q.vert_periodic = h->grid.periodic[h->D - 1] ? 1 : 0;
+    // a plain domain; lbmp_create_slab overrides these for one rank's slab
+    q.wall_lo = q.wall_hi = q.vert_periodic ? 0 : 1;
+    q.zb = 0;
+    q.ze = h->D == 3 ? h->grid.nz : h->grid.ny;
+    q.zoff = 0;
+    q.nzg = q.ze;
     q.N = h->N;
     q.rho_l = (float)d.rho_l;
     q.drho = (float)(d.rho_h - d.rho_l);
@@ -121,19 +129,25 @@ void drop_step_graphs(lbmp_handle* h)
     h->graph_warm = false;
 }
 
+// bytes of the observables' result slots: 16 scalars and phi on the spike and bubble columns
+size_t red_out_bytes(const lbmp_handle* h)
+{
+    const int nv = (h->D == 3) ? h->grid.nz : h->grid.ny;
+    return sizeof(double) * (16 + 2 * (size_t)nv);
+}
+
 void free_handle(lbmp_handle* h)
 {
     drop_step_graphs(h);
     for (int k = 0; k < 2; ++k) {
-        if (h->f[k]) cudaFree(h->f[k]);
-        if (h->g[k]) cudaFree(h->g[k]);
+        lbmp::dev_free(h, h->f[k], lbmp::set_bytes(h));
+        lbmp::dev_free(h, h->g[k], lbmp::gset_bytes(h));
     }
-    if (h->phi) cudaFree(h->phi);
-    if (h->phiu) cudaFree(h->phiu);
-    for (int k = 0; k < 2; ++k)
-        if (h->uvel[k]) cudaFree(h->uvel[k]);
-    if (h->red) cudaFree(h->red);
-    if (h->red_out) cudaFree(h->red_out);
+    lbmp::dev_free(h, h->phi, 2 * sizeof(float) * (size_t)h->N);
+    lbmp::dev_free(h, h->phiu, lbmp::phiu_bytes(h));
+    for (int k = 0; k < 2; ++k) lbmp::dev_free(h, h->uvel[k], lbmp::uvel_bytes(h));
+    lbmp::dev_free(h, h->red, sizeof(double) * 4 * (size_t)h->red_blocks);
+    lbmp::dev_free(h, h->red_out, red_out_bytes(h));
     delete h;
 }
 
@@ -162,6 +176,36 @@ int check_handle(const lbmp_handle* h)
 
 namespace lbmp {
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+cudaError_t dev_alloc(lbmp_handle* h, void** p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    if (!h->alloc.alloc) return cudaMalloc(p, bytes);
+    *p = h->alloc.alloc(bytes, (void*)h->stream, h->alloc.ctx);
+    if (!*p) return cudaErrorMemoryAllocation;
+    if (((uintptr_t)*p) & 255u) {  // the kernels' vector and bulk accesses need the promised alignment
+        h->alloc.free(*p, bytes, (void*)h->stream, h->alloc.ctx);
+        *p = nullptr;
+        return cudaErrorMisalignedAddress;
+    }
+    return cudaSuccess;
+}
+
+void dev_free(lbmp_handle* h, void* p, size_t bytes)
+{
+    if (!p) return;
+    if (h->alloc.free)
+        h->alloc.free(p, bytes, (void*)h->stream, h->alloc.ctx);
+    else
+        cudaFree(p);
+}
+
+cudaError_t ensure_phi(lbmp_handle* h)
+{
+    if (h->phi) return cudaSuccess;
+    return dev_alloc(h, (void**)&h->phi, 2 * sizeof(float) * (size_t)h->N);
+}
 
 cudaError_t launch_step(lbmp_handle* h)
 {
@@ -246,6 +290,14 @@ const char* lbmp_last_error(void) { return g_msg; }
 int lbmp_create(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* params, void* cuda_stream,
                 lbmp_handle** out)
 {
+    return lbmp_create_ex(grid, lattice, params, cuda_stream, nullptr, out);
+}
+
+int lbmp_create_ex(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* params, void* cuda_stream,
+                   const lbmp_allocator* allocator, lbmp_handle** out)
+{
+    if (allocator && (!allocator->alloc || !allocator->free))
+        return fail(LBMP_ERR_INVALID_ARG, "allocator needs both alloc and free");
     if (!grid || !params || !out) return fail(LBMP_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
     if (lattice != LBMP_D2Q9 && lattice != LBMP_D3Q27) return fail(LBMP_ERR_INVALID_ARG, "unknown lattice");
@@ -284,6 +336,7 @@ int lbmp_create(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* 
     h->params = *params;
     h->N = N;
     h->stream = (cudaStream_t)cuda_stream;
+    if (allocator) h->alloc = *allocator;
     int rc = derive(*params, D, h->der);
     if (rc != LBMP_OK) {
         delete h;
@@ -302,18 +355,20 @@ int lbmp_create(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_params* 
     }
     const size_t pop = lbmp::set_bytes(h), gpop = lbmp::gset_bytes(h);
     for (int k = 0; k < 2; ++k) {
-        e = cudaMalloc(&h->f[k], pop);
-        if (e == cudaSuccess) e = cudaMalloc(&h->g[k], gpop);
+        e = lbmp::dev_alloc(h, (void**)&h->f[k], pop);
+        if (e == cudaSuccess) e = lbmp::dev_alloc(h, (void**)&h->g[k], gpop);
         if (e != cudaSuccess) break;
     }
-    if (e == cudaSuccess && h->reduced) e = cudaMalloc(&h->phiu, lbmp::phiu_bytes(h));
-    for (int k = 0; k < 2 && e == cudaSuccess && h->divu; ++k) e = cudaMalloc(&h->uvel[k], lbmp::uvel_bytes(h));
-    if (e == cudaSuccess) e = cudaMalloc(&h->phi, 2 * sizeof(float) * (size_t)N);
+    if (e == cudaSuccess && h->reduced) e = lbmp::dev_alloc(h, (void**)&h->phiu, lbmp::phiu_bytes(h));
+    for (int k = 0; k < 2 && e == cudaSuccess && h->divu; ++k)
+        e = lbmp::dev_alloc(h, (void**)&h->uvel[k], lbmp::uvel_bytes(h));
+    // the divergence-term variant always runs the reference pair, which reads phi
+    if (e == cudaSuccess && h->divu) e = lbmp::ensure_phi(h);
     h->red_blocks = 1024;
-    if (e == cudaSuccess) e = cudaMalloc(&h->red, sizeof(double) * 4 * h->red_blocks);
-    const int nv = (D == 3) ? grid->nz : grid->ny;
-    if (e == cudaSuccess) e = cudaMalloc(&h->red_out, sizeof(double) * (16 + 2 * (size_t)nv));
-    if (e == cudaSuccess) e = cudaMemset(h->red_out, 0, sizeof(double) * 16);
+    if (e == cudaSuccess) e = lbmp::dev_alloc(h, (void**)&h->red, sizeof(double) * 4 * h->red_blocks);
+    if (e == cudaSuccess) e = lbmp::dev_alloc(h, (void**)&h->red_out, red_out_bytes(h));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->red_out, 0, sizeof(double) * 16, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e == cudaSuccess) h->dp.status = (int*)(h->red_out + kStatusSlot);
     if (e != cudaSuccess) {
         free_handle(h);
@@ -351,6 +406,15 @@ int lbmp_set_option(lbmp_handle* h, int option, long value)
     switch (option) {
     case LBMP_OPT_KERNEL:
         if (value < 0 || value > 2) return fail(LBMP_ERR_INVALID_ARG, "kernel must be 0, 1 or 2");
+        if (h->slab && value != 0) return fail(LBMP_ERR_UNSUPPORTED, "z-slabs run the fused kernel only");
+        if (value == 1) {  // the reference pair keeps phi in an array of its own
+            const cudaError_t e = lbmp::ensure_phi(h);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return e == cudaErrorMemoryAllocation ? fail(LBMP_ERR_NOMEM, "device allocation failed")
+                                                      : cuda_fail(e, "phi array");
+            }
+        }
         h->kernel = (int)value;
         return LBMP_OK;
     case LBMP_OPT_CHUNK:
@@ -418,6 +482,7 @@ int lbmp_step(lbmp_handle* h, long n)
     int rc = check_handle(h);
     if (rc) return rc;
     if (n < 0) return fail(LBMP_ERR_INVALID_ARG, "negative step count");
+    if (h->slab && n > 1) return fail(LBMP_ERR_INVALID_ARG, "a z-slab takes one step at a time (ghosts are exchanged in between)");
     const bool graphs = n >= kStepGraph && step_graph_usable(h);
     if (graphs) check_graph_key(h);
     long k = 0;
@@ -459,7 +524,9 @@ int lbmp_observables(lbmp_handle* h, lbmp_obs* out)
     if (rc) return rc;
     if (!out) return fail(LBMP_ERR_INVALID_ARG, "null output");
     const int nv = (h->D == 3) ? h->grid.nz : h->grid.ny;
-    LBMP_CUDA(lbmp::launch_observables(h, h->red_out), "observables kernels");
+    // a z-slab reduces over its own planes; probes and tips need the whole domain
+    LBMP_CUDA(h->slab ? lbmp::launch_mass(h, h->red_out) : lbmp::launch_observables(h, h->red_out),
+              "observables kernels");
     double* host = new (std::nothrow) double[16 + 2 * (size_t)nv];
     if (!host) return fail(LBMP_ERR_NOMEM, "host allocation failed");
     cudaError_t e = cudaMemcpyAsync(host, h->red_out, sizeof(double) * (16 + 2 * (size_t)nv), cudaMemcpyDeviceToHost,
@@ -494,6 +561,10 @@ int lbmp_observables(lbmp_handle* h, lbmp_obs* out)
             out->tip_bubble = (k == nv - 1) ? (double)k : k + (0.5 - cb[k]) / (cb[k + 1] - cb[k]);
             break;
         }
+    if (h->slab) {
+        const double nan = std::numeric_limits<double>::quiet_NaN();
+        out->p_in = out->p_out = out->laplace_dp = out->tip_spike = out->tip_bubble = nan;
+    }
     out->step = h->step;
     int word = 0;
     memcpy(&word, host + kStatusSlot, sizeof word);
@@ -524,7 +595,7 @@ int lbmp_get_state(lbmp_handle* h, double* f, double* g, double* phi)
         float* tmp = new (std::nothrow) float[2 * h->N];
         if (!tmp) return fail(LBMP_ERR_NOMEM, "host allocation failed");
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(tmp, h->phi, 2 * sizeof(float) * h->N, cudaMemcpyDeviceToHost, h->stream);
+            e = cudaMemcpyAsync(tmp, lbmp::phi_buf(h), 2 * sizeof(float) * h->N, cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e == cudaSuccess)
             for (long long i = 0; i < h->N; ++i) phi[i] = (double)tmp[i] + (double)tmp[h->N + i];

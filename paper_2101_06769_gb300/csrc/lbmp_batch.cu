@@ -286,6 +286,7 @@ LBMP_API int lbmp_batch_add(lbmp_batch* b, lbmp_handle* h, long steps)
     if (h->device != b->device) return batch_fail(LBMP_ERR_INVALID_ARG, "domain lives on another device");
     if ((int)b->members.size() >= kMaxMembers) return batch_fail(LBMP_ERR_INVALID_ARG, "batch is full");
     if (h->divu) return batch_fail(LBMP_ERR_UNSUPPORTED, "divergence-term domains are not batch members");
+    if (h->slab) return batch_fail(LBMP_ERR_UNSUPPORTED, "z-slabs are not batch members");
     size_t used = 0;
     for (const Member& m : b->members) {
         if (m.h == h) return batch_fail(LBMP_ERR_INVALID_ARG, "domain is already a member");
@@ -367,7 +368,12 @@ LBMP_API int lbmp_batch_autotune(lbmp_batch* b, int reps, lbmp_tune_entry* table
     const int saved_tile = b->tile, saved_chunk = b->chunk;
     const int chunks[4] = {8, 16, 32, 64};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaEventCreate(&e0);
+    // the trials run real step kernels: keep the reduced members' stored phi u
+    std::vector<float*> phiu_copies(b->members.size(), nullptr);
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < b->members.size() && e == cudaSuccess; ++k)
+        e = lbmp::phiu_save(b->members[k].h, b->stream, &phiu_copies[k]);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     double best = 1e300;
     int best_tile = saved_tile, best_chunk = saved_chunk, n = 0;
@@ -396,6 +402,11 @@ LBMP_API int lbmp_batch_autotune(lbmp_batch* b, int reps, lbmp_tune_entry* table
         }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    // the D2Q9 trials ran on the side stream, joined into b->stream
+    for (size_t k = 0; k < b->members.size(); ++k) {
+        const cudaError_t er = lbmp::phiu_restore(b->members[k].h, b->stream, phiu_copies[k]);
+        if (e == cudaSuccess) e = er;
+    }
     b->tile = n ? best_tile : saved_tile;
     b->chunk = n ? best_chunk : saved_chunk;
     b->dirty = true;  // graphs are rebuilt with the chosen shape at the next step

@@ -21,7 +21,22 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// 1: the pair loops of phase_outputs / flow_outputs keep their memory
+// operations in program order (a compiler barrier per pair), so that the
+// compiler does not hoist the loads of later pairs; this lowers the register
+// footprint of a kernel built for four CTAs per SM at no change in results
+#ifndef LBMP_OUT_ORDERED
+#define LBMP_OUT_ORDERED 0
+#endif
+
 namespace lbmp {
+
+__device__ __forceinline__ void out_pair_done()
+{
+#if LBMP_OUT_ORDERED
+    asm volatile("" ::: "memory");
+#endif
+}
 
 __host__ __device__ constexpr double w1d(int c) { return c == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
 
@@ -89,6 +104,16 @@ struct PhaseLat {
 struct DevParams {
     int nx, ny, nz;         // nz = 1 in 2-D
     int vert_periodic;      // vertical axis periodic (1) or walled (0)
+    // Vertical axis of a z-slab (one rank's planes of a domain decomposed
+    // along z; equal to the plain values otherwise): half-way bounce-back
+    // wall below plane 0 / above plane nz-1 (wall_lo / wall_hi), the planes
+    // [zb, ze) the step updates (the others are ghost planes filled by the
+    // exchange), the global index of plane 0 (zoff) and the global extent
+    // (nzg).  A slab's local axis is periodic in the index arithmetic, but no
+    // updated plane or staged ghost ever pulls across its ends.
+    int wall_lo, wall_hi;
+    int zb, ze;
+    int zoff, nzg;
     long long N;            // cells
     float rho_l, drho, rho_bar;
     float nu_h, nu_l, eta_h, eta_l;
@@ -150,7 +175,7 @@ __device__ __forceinline__ long long pull_src(const DevParams& p, int a, int x, 
         ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
         int zs = z - cz;
         if (zs < 0 || zs >= p.nz) {
-            if (!p.vert_periodic) {
+            if (zs < 0 ? p.wall_lo : p.wall_hi) {
                 dir = Lat<D>::opp(a);
                 return self;
             }
@@ -211,7 +236,7 @@ __device__ __forceinline__ long long push_dst(const DevParams& p, int a, int x, 
         yd = yd < 0 ? yd + p.ny : (yd >= p.ny ? yd - p.ny : yd);
         int zd = z + cz;
         if (zd < 0 || zd >= p.nz) {
-            if (!p.vert_periodic) {
+            if (zd < 0 ? p.wall_lo : p.wall_hi) {
                 dir = Lat<D>::opp(a);
                 return self;
             }
@@ -499,6 +524,13 @@ __device__ __forceinline__ int wrap_v(int v, int n, int periodic)
     if (periodic) return v < 0 ? v + n : v - n;
     return v < 0 ? 0 : n - 1;
 }
+// the same per side of the vertical axis (z-slabs: a wall on one side only)
+__device__ __forceinline__ int wrap_vert(const DevParams& p, int v, int n)
+{
+    if (v >= 0 && v < n) return v;
+    if (v < 0) return p.wall_lo ? 0 : v + n;
+    return p.wall_hi ? n - 1 : v - n;
+}
 
 // ------------------------------------------------------- cells and stencil
 __device__ __forceinline__ void cell_xyz(const DevParams& p, long long i, int& x, int& y, int& z)
@@ -516,7 +548,7 @@ __device__ __forceinline__ long long nbr_index(const DevParams& p, int a, int x,
     const int xx = wrap_h(x + Lat<D>::cx(a), p.nx);
     if (D == 3) {
         const int yy = wrap_h(y + Lat<D>::cy(a), p.ny);
-        const int zz = wrap_v(z + Lat<D>::cz(a), p.nz, p.vert_periodic);
+        const int zz = wrap_vert(p, z + Lat<D>::cz(a), p.nz);
         return ((long long)zz * p.ny + yy) * p.nx + xx;
     } else {
         const int yy = wrap_v(y + Lat<D>::cy(a), p.ny, p.vert_periodic);
@@ -730,15 +762,13 @@ __device__ __forceinline__ float flow_closure(const DevParams& p, float phi, con
     return rho;
 }
 
-// The closure above and the relaxed second-order deviations.  Produces the
-// 27-entry Kronecker inverse of the post-collision moment differences in
-// dh[] (h* - E(u)).
-template <int D, bool DV = false>
-__device__ __forceinline__ void flow_collide(const DevParams& p, float phi, const float grad[3], float lap,
-                                             const FlowMoments& m, CellState& s, float dh[27], float divu = 0.f)
+// The relaxation of the flow collision, after the closure (inv_rho and nu
+// from flow_closure): the relaxed second-order deviations and the per-axis
+// product equilibrium (s.ew).  Produces the 27-entry Kronecker inverse of the
+// post-collision moment differences in dh[] (h* - E(u)).
+template <int D>
+__device__ __forceinline__ void flow_relax(const FlowMoments& m, CellState& s, float inv_rho, float nu, float dh[27])
 {
-    float inv_rho, nu;
-    flow_closure<D, DV>(p, phi, grad, lap, m, s, inv_rho, nu, divu);
     const float omega = 1.0f / (3.0f * nu + 0.5f);
     const float om1 = 1.0f - omega;
     const float ux = s.u[0], uy = s.u[1], uz = s.u[2];
@@ -835,6 +865,16 @@ __device__ __forceinline__ void flow_collide(const DevParams& p, float phi, cons
     }
 #pragma unroll
     for (int i = 0; i < 27; ++i) dh[i] = k[i];
+}
+
+// The closure and the relaxation of one cell: s (every field) and dh[].
+template <int D, bool DV = false>
+__device__ __forceinline__ void flow_collide(const DevParams& p, float phi, const float grad[3], float lap,
+                                             const FlowMoments& m, CellState& s, float dh[27], float divu = 0.f)
+{
+    float inv_rho, nu;
+    flow_closure<D, DV>(p, phi, grad, lap, m, s, inv_rho, nu, divu);
+    flow_relax<D>(m, s, inv_rho, nu, dh);
 }
 
 // Deviation of the second-order Hermite equilibrium f_eq/rho (App. A) from
@@ -993,6 +1033,131 @@ struct NoPhiU {
     __device__ __forceinline__ void operator()(const CellState&, float d[3]) const { d[0] = d[1] = d[2] = 0.f; }
 };
 
+// Per-pair pieces of the outputs.  Direction a < Q/2 and its opposite
+// b = Q-1-a are the two lanes (c, -c) of the paired arithmetic.
+//
+// pair_gamma: the equilibrium deviation Gamma - w = w [3 c.u + 4.5 (c.u)^2 -
+// 1.5 u^2] (gd) and Gamma itself (wgd = w + gd); m15uu = -1.5 |u|^2.
+template <int D>
+__device__ __forceinline__ void pair_gamma(const CellState& s, int a, float m15uu, float2& gd, float2& wgd)
+{
+    const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
+    const float w = Lat<D>::w(a);
+    const float2 w2 = f2(w, w);
+    const float cu = cx * s.u[0] + cy * s.u[1] + cz * s.u[2];
+    const float X = fmaf(4.5f * cu, cu, m15uu);
+    gd = mul2(w2, fma2(f2(3.f, -3.f), f2(cu, cu), f2(X, X)));
+    wgd = add2(w2, gd);
+}
+
+// pair_flow: f'* = rho cs2 (E - w + dh) + w p_h + Xi/2 of the pair, with
+// Xi = (Gamma - w)(c - u).G + Gamma (c - u).F and E(u) - w telescoped over
+// the axes; dab = (dh[a], dh[b]).
+template <int D, bool DV>
+__device__ __forceinline__ float2 pair_flow(const CellState& s, int a, float2 gd, float2 wgd, float2 dab)
+{
+    const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
+    const float w = Lat<D>::w(a);
+    const float2 pm1 = f2(1.f, -1.f);
+    const float cG0 = cx * s.G[0] + cy * s.G[1] + cz * s.G[2];
+    const float cF0 = cx * s.F[0] + cy * s.F[1] + cz * s.F[2];
+    const float2 cG = fma2(pm1, f2(cG0, cG0), f2(-s.uG, -s.uG));
+    const float2 cF = fma2(pm1, f2(cF0, cF0), f2(-s.uF, -s.uF));
+    float2 xi = fma2(gd, cG, mul2(wgd, cF));
+    if constexpr (DV) xi = add2(xi, f2(w * s.sdiv, w * s.sdiv));
+    const float2 exs = f2(s.ew[0][cx + 1], s.ew[0][1 - cx]);
+    const float2 eys = f2(s.ew[1][cy + 1], s.ew[1][1 - cy]);
+    const float wx = (float)w1d(cx), wy = (float)w1d(cy), wz = (float)w1d(cz);
+    const float2 ex = add2(f2(wx, wx), exs);
+    float2 ew;
+    if (D == 3) {
+        const float2 ezs = f2(s.ew[2][cz + 1], s.ew[2][1 - cz]);
+        const float2 ey = add2(f2(wy, wy), eys);
+        ew = fma2(mul2(ex, ey), ezs, fma2(mul2(ex, eys), f2(wz, wz), mul2(exs, f2(wy * wz, wy * wz))));
+    } else {
+        ew = fma2(ex, eys, mul2(exs, f2(wy, wy)));
+    }
+    const float wph = w * s.ph;
+    return fma2(f2(s.rcs2, s.rcs2), add2(ew, dab), fma2(f2(0.5f, 0.5f), xi, f2(wph, wph)));
+}
+
+// pair_phase: g* = g + (phi Gamma - g)/tau + w (c.n) lambda 4 phi (1-phi)/W
+// of the pair (flow lattice), gi = (g_a, g_b) pre-collision
+template <int D>
+__device__ __forceinline__ float2 pair_phase(const DevParams& p, const CellState& s, int a, float2 wgd, float2 gi)
+{
+    const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
+    const float w = Lat<D>::w(a);
+    const float2 pm1 = f2(1.f, -1.f);
+    const float cn0 = cx * s.n[0] + cy * s.n[1] + cz * s.n[2];
+    const float ws = w * s.sharp;
+    const float2 itau = f2(p.inv_tau_phi, p.inv_tau_phi);
+    return fma2(f2(ws, ws), mul2(pm1, f2(cn0, cn0)), fma2(itau, fma2(f2(s.phi, s.phi), wgd, neg2(gi)), gi));
+}
+
+// The rest populations from the conservation identities (see below): the
+// flow total P + u.G (+ the divergence term) less the moving outputs fs,
+// the phase-field total (gsum_hi, gsum_lo) less the compensated moving
+// outputs (gs, gl); or a shifted encoder takes the totals themselves.
+template <bool DV, class Out>
+__device__ __forceinline__ void flow_rest(const CellState& s, const FlowMoments& m, float2 fs, const Out& fout,
+                                          int C)
+{
+    if constexpr (Out::kTotal)
+        fout.finish(m.P, s.uG);
+    else
+        fout(C, (DV ? (m.P + s.uG) + s.sdiv : m.P + s.uG) - (fs.x + fs.y));
+}
+template <class Out>
+__device__ __forceinline__ void phase_rest(float gsum_hi, float gsum_lo, float2 gs, float2 gl, const Out& gout, int GC)
+{
+    if constexpr (Out::kTotal) {
+        gout.finish(gsum_hi, gsum_lo);
+    } else {
+        float t = gs.x + gs.y;  // combine the lanes exactly
+        const float bb = t - gs.x;
+        const float e = (gs.x - (t - bb)) + (gs.y - bb);
+        gout(GC, (gsum_hi - t) + (gsum_lo - (gl.x + gl.y + e)));
+    }
+}
+
+// The phase-field update on the reduced lattice: g* = g + (g_eq - g)/tau +
+// w c.(lambda 4 phi(1-phi)/W n + lambda/cs2 d/dt(phi u)) with the
+// first-order equilibrium g_eq = w phi (1 + c.u/cs2), the sharpening source
+// and the correction term (Sec. 2.2), lanes (r, opposite); the rest slot
+// from the conserved total.
+template <int D, class GSrc, class Out, class DPhiU>
+__device__ __forceinline__ void phase_outputs_reduced(const DevParams& p, const CellState& s, const GSrc& gin,
+                                                      float gsum_hi, float gsum_lo, const Out& gout,
+                                                      const DPhiU& dphiu_fn, float2 gs, float2 gl)
+{
+    constexpr int GC = PhaseLat<D, true>::C;
+    constexpr float ics = PhaseLat<D, true>::inv_cs2;
+    const float2 itau = f2(p.inv_tau_phi, p.inv_tau_phi);
+    const float2 pm1 = f2(1.f, -1.f);
+    float qv[3];
+    dphiu_fn(s, qv);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) qv[i] = fmaf(p.lam_corr, qv[i], s.sharp * s.n[i]);
+#pragma unroll
+    for (int r = 0; r < GC; ++r) {
+        const int a = PhaseLat<D, true>::full(r);
+        const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
+        const float w = PhaseLat<D, true>::w(r);
+        const float cu = cx * s.u[0] + cy * s.u[1] + cz * s.u[2];
+        const float cq = cx * qv[0] + cy * qv[1] + cz * qv[2];
+        const float wphi = w * s.phi;
+        const float t = wphi * ics * cu;
+        const float2 geq = fma2(pm1, f2(t, t), f2(wphi, wphi));
+        const float2 gi = f2(gin(r), gin(2 * GC - r));
+        const float2 go = fma2(f2(w, w), mul2(pm1, f2(cq, cq)), fma2(itau, add2(geq, neg2(gi)), gi));
+        gout(r, go.x);
+        gout(2 * GC - r, go.y);
+        two_sum2(gs, gl, go);
+    }
+    phase_rest(gsum_hi, gsum_lo, gs, gl, gout, GC);
+}
+
 // PR: g on the reduced phase lattice (gin / gout index its slots), with
 // dphiu(s, d) giving d/dt(phi u) of the cell for the correction term.
 // DV: the w cs2 rho div(u) term of Xi (s.sdiv from flow_closure<D, true>):
@@ -1007,101 +1172,80 @@ __device__ __forceinline__ void collide_outputs(const DevParams& p, const CellSt
     static_assert(!(DV && Out::kTotal), "the divergence term is supported with FP32 storage only");
     constexpr int Q = Lat<D>::Q;
     constexpr int C = Q / 2;
-    const float2 rcs2 = f2(s.rcs2, s.rcs2);
-    const float2 itau = f2(p.inv_tau_phi, p.inv_tau_phi);
-    const float2 phi2 = f2(s.phi, s.phi);
-    const float2 pm1 = f2(1.f, -1.f);
     const float m15uu = -1.5f * s.uu;
     float2 fs = f2(0.f, 0.f), gs = f2(0.f, 0.f), gl = f2(0.f, 0.f);
 #pragma unroll
     for (int a = 0; a < C; ++a) {
         const int b = Q - 1 - a;
-        const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
-        const float w = Lat<D>::w(a);
-        const float2 w2 = f2(w, w);
-        // equilibrium deviation Gamma - w = w [3 c.u + 4.5 (c.u)^2 - 1.5 u^2], lanes (c, -c)
-        const float cu = cx * s.u[0] + cy * s.u[1] + cz * s.u[2];
-        const float X = fmaf(4.5f * cu, cu, m15uu);
-        const float2 gd = mul2(w2, fma2(f2(3.f, -3.f), f2(cu, cu), f2(X, X)));
-        const float2 wgd = add2(w2, gd);
-        // Xi = (Gamma - w)(c - u).G + Gamma (c - u).F
-        const float cG0 = cx * s.G[0] + cy * s.G[1] + cz * s.G[2];
-        const float cF0 = cx * s.F[0] + cy * s.F[1] + cz * s.F[2];
-        const float2 cG = fma2(pm1, f2(cG0, cG0), f2(-s.uG, -s.uG));
-        const float2 cF = fma2(pm1, f2(cF0, cF0), f2(-s.uF, -s.uF));
-        float2 xi = fma2(gd, cG, mul2(wgd, cF));
-        if constexpr (DV) xi = add2(xi, f2(w * s.sdiv, w * s.sdiv));
-        // E(u) - w telescoped over the axes, lanes (c, -c)
-        const float2 exs = f2(s.ew[0][cx + 1], s.ew[0][1 - cx]);
-        const float2 eys = f2(s.ew[1][cy + 1], s.ew[1][1 - cy]);
-        const float wx = (float)w1d(cx), wy = (float)w1d(cy), wz = (float)w1d(cz);
-        const float2 ex = add2(f2(wx, wx), exs);
-        float2 ew;
-        if (D == 3) {
-            const float2 ezs = f2(s.ew[2][cz + 1], s.ew[2][1 - cz]);
-            const float2 ey = add2(f2(wy, wy), eys);
-            ew = fma2(mul2(ex, ey), ezs, fma2(mul2(ex, eys), f2(wz, wz), mul2(exs, f2(wy * wz, wy * wz))));
-        } else {
-            ew = fma2(ex, eys, mul2(exs, f2(wy, wy)));
-        }
-        // f'* = rho cs2 (E - w + dh) + w p_h + Xi/2
-        const float wph = w * s.ph;
-        const float2 fo = fma2(rcs2, add2(ew, f2(dh[a], dh[b])), fma2(f2(0.5f, 0.5f), xi, f2(wph, wph)));
+        float2 gd, wgd;
+        pair_gamma<D>(s, a, m15uu, gd, wgd);
+        const float2 fo = pair_flow<D, DV>(s, a, gd, wgd, f2(dh[a], dh[b]));
         fout(a, fo.x);
         fout(b, fo.y);
         fs = add2(fs, fo);
         if constexpr (!PR) {
-            // g* = g + (phi Gamma - g)/tau + w (c.n) lambda 4 phi (1-phi)/W
-            const float cn0 = cx * s.n[0] + cy * s.n[1] + cz * s.n[2];
-            const float ws = w * s.sharp;
-            const float2 gi = f2(gin(a), gin(b));
-            const float2 go =
-                fma2(f2(ws, ws), mul2(pm1, f2(cn0, cn0)), fma2(itau, fma2(phi2, wgd, neg2(gi)), gi));
+            const float2 go = pair_phase<D>(p, s, a, wgd, f2(gin(a), gin(b)));
             gout(a, go.x);
             gout(b, go.y);
-            two_sum2(gs, gl, go);
-        }
-    }
-    constexpr int GC = PhaseLat<D, PR>::C;  // rest slot of g
-    if constexpr (PR) {
-        // g* = g + (g_eq - g)/tau + w c.(lambda 4 phi(1-phi)/W n + lambda/cs2 d/dt(phi u)),
-        // g_eq = w phi (1 + c.u/cs2): first-order equilibrium, sharpening source
-        // and correction term (Sec. 2.2), lanes (r, opposite)
-        constexpr float ics = PhaseLat<D, true>::inv_cs2;
-        float qv[3];
-        dphiu_fn(s, qv);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) qv[i] = fmaf(p.lam_corr, qv[i], s.sharp * s.n[i]);
-#pragma unroll
-        for (int r = 0; r < GC; ++r) {
-            const int a = PhaseLat<D, true>::full(r);
-            const int cx = Lat<D>::cx(a), cy = Lat<D>::cy(a), cz = Lat<D>::cz(a);
-            const float w = PhaseLat<D, true>::w(r);
-            const float cu = cx * s.u[0] + cy * s.u[1] + cz * s.u[2];
-            const float cq = cx * qv[0] + cy * qv[1] + cz * qv[2];
-            const float wphi = w * s.phi;
-            const float t = wphi * ics * cu;
-            const float2 geq = fma2(pm1, f2(t, t), f2(wphi, wphi));
-            const float2 gi = f2(gin(r), gin(2 * GC - r));
-            const float2 go = fma2(f2(w, w), mul2(pm1, f2(cq, cq)), fma2(itau, add2(geq, neg2(gi)), gi));
-            gout(r, go.x);
-            gout(2 * GC - r, go.y);
             two_sum2(gs, gl, go);
         }
     }
     // target totals: P + u.G (flow) and the incoming sum (phase field); the
     // rest populations take the difference (conservation identities above),
     // or a shifted encoder takes the totals themselves
-    if constexpr (Out::kTotal) {
-        fout.finish(m.P, s.uG);
-        gout.finish(gsum_hi, gsum_lo);
-    } else {
-        fout(C, (DV ? (m.P + s.uG) + s.sdiv : m.P + s.uG) - (fs.x + fs.y));
-        float t = gs.x + gs.y;  // combine the lanes exactly
-        const float bb = t - gs.x;
-        const float e = (gs.x - (t - bb)) + (gs.y - bb);
-        gout(GC, (gsum_hi - t) + (gsum_lo - (gl.x + gl.y + e)));
+    flow_rest<DV>(s, m, fs, fout, C);
+    if constexpr (PR)
+        phase_outputs_reduced<D>(p, s, gin, gsum_hi, gsum_lo, gout, dphiu_fn, gs, gl);
+    else
+        phase_rest(gsum_hi, gsum_lo, gs, gl, gout, C);
+}
+
+// The same outputs in two passes, phase field first: phase_outputs needs only
+// the closure (CellState without ew), so a kernel can run it before
+// flow_relax and reuse the staged pre-collision g for the moment
+// differences; flow_outputs then emits f'.  Each value is formed by the same
+// operations as in collide_outputs, and the rest populations accumulate the
+// moving ones in the same order, so the results are identical.
+template <int D, class GSrc, class Out>
+__device__ __forceinline__ void phase_outputs(const DevParams& p, const CellState& s, const GSrc& gin, float gsum_hi,
+                                              float gsum_lo, const Out& gout)
+{
+    constexpr int Q = Lat<D>::Q;
+    constexpr int C = Q / 2;
+    const float m15uu = -1.5f * s.uu;
+    float2 gs = f2(0.f, 0.f), gl = f2(0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < C; ++a) {
+        const int b = Q - 1 - a;
+        float2 gd, wgd;
+        pair_gamma<D>(s, a, m15uu, gd, wgd);
+        const float2 go = pair_phase<D>(p, s, a, wgd, f2(gin(a), gin(b)));
+        gout(a, go.x);
+        gout(b, go.y);
+        two_sum2(gs, gl, go);
+        out_pair_done();
     }
+    phase_rest(gsum_hi, gsum_lo, gs, gl, gout, C);
+}
+template <int D, class Out, class DH>
+__device__ __forceinline__ void flow_outputs(const CellState& s, const DH& dh, const FlowMoments& m, const Out& fout)
+{
+    constexpr int Q = Lat<D>::Q;
+    constexpr int C = Q / 2;
+    const float m15uu = -1.5f * s.uu;
+    float2 fs = f2(0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < C; ++a) {
+        const int b = Q - 1 - a;
+        float2 gd, wgd;
+        pair_gamma<D>(s, a, m15uu, gd, wgd);
+        const float2 fo = pair_flow<D, false>(s, a, gd, wgd, f2(dh[a], dh[b]));
+        fout(a, fo.x);
+        fout(b, fo.y);
+        fs = add2(fs, fo);
+        out_pair_done();
+    }
+    flow_rest<false>(s, m, fs, fout, C);
 }
 
 }  // namespace lbmp

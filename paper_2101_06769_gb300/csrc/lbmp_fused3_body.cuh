@@ -111,10 +111,24 @@ struct RingCopy {
 // barrier is needed in between.
 // Reduced phase lattice: the own cells' stored phi u of plane zz is copied
 // with them into ubuf ([3][NT]), so the collision finds it in shared memory.
+// With kRingReg the ring threads instead load their cell's g(zz) to
+// registers and write its phi at once, after issuing the own copies.
+
+// ring cell's g(zz) loaded to registers and summed at once (kRingReg)
+template <bool Walls>
+__device__ __forceinline__ void ring_phi_direct(const DirPtrs& D, const Column& C, const Plane& P, float2* dst)
+{
+    float v[QG];
+    Unroll<QG>::run(PullLoadG<Walls>{D.gin, C, P, v});
+    float hi, lo;
+    phi_sum_phase<3, PR>([&](int r) { return v[r]; }, hi, lo);
+    *dst = make_float2(hi, lo);
+}
+
 __device__ __forceinline__ void stage_issue(const DevParams& p, const DirPtrs& D, const Column& own,
-                                            const Column& ring, int tid, int zz, float* __restrict__ gbuf,
+                                            const Column& ring, int tid, int rslot, int zz, float* __restrict__ gbuf,
                                             float* __restrict__ rbuf, const float* __restrict__ phiu,
-                                            float* __restrict__ ubuf)
+                                            float* __restrict__ ubuf, float2* __restrict__ phi_plane)
 {
     Plane P;
     set_plane(P, p, plane_src(p, zz));
@@ -125,19 +139,29 @@ __device__ __forceinline__ void stage_issue(const DevParams& p, const DirPtrs& D
     }
     if (P.lo || P.hi) {  // uniform across the CTA
         Unroll<QG>::run(StageCopy<true>{D, own, P, gbuf + tid});
-        if (tid < NRING) Unroll<QG>::run(RingCopy<true>{D, ring, P, rbuf + tid});
+        if (!kRingReg && tid < NRING) Unroll<QG>::run(RingCopy<true>{D, ring, P, rbuf + tid});
     } else {
         Unroll<QG>::run(StageCopy<false>{D, own, P, gbuf + tid});
-        if (tid < NRING) Unroll<QG>::run(RingCopy<false>{D, ring, P, rbuf + tid});
+        if (!kRingReg && tid < NRING) Unroll<QG>::run(RingCopy<false>{D, ring, P, rbuf + tid});
     }
     cp_async_commit();
+    if constexpr (kRingReg) {
+        // the phi plane slot is free: the barrier ending the previous plane
+        // separates this write from the last stencil reads of its old plane
+        if (tid < NRING) {
+            if (P.lo || P.hi)
+                ring_phi_direct<true>(D, ring, P, phi_plane + rslot);
+            else
+                ring_phi_direct<false>(D, ring, P, phi_plane + rslot);
+        }
+    }
 }
 
 __device__ __forceinline__ void stage_finish(int tid, int oslot, int rslot, const float* __restrict__ gbuf,
                                              const float* __restrict__ rbuf, float2* __restrict__ phi_plane)
 {
     cp_async_wait_all();
-    if (tid < NRING) {
+    if (!kRingReg && tid < NRING) {
         float hi, lo;
         phi_sum_phase<3, PR>([&](int r) { return rbuf[r * NRING + tid]; }, hi, lo);
         phi_plane[rslot] = make_float2(hi, lo);
@@ -154,26 +178,27 @@ __device__ __forceinline__ void stage_finish(int tid, int oslot, int rslot, cons
 __device__ __forceinline__ void fused_segment(const DevParams& p, const DirPtrs& Dp, const ThreadGeo& T, float* smem,
                                               int x0, int y0, int z0, int z1, float* __restrict__ phiu)
 {
-    float* gS = smem;                           // [2][QG][NT]
-    float* rS = smem + 2 * QG * NT;             // [QG][NRING] ring cells' g of the plane being staged
-    float2* phiS = (float2*)(rS + QG * NRING);  // (hi, lo) [3][RY][RX]
-    float* fS = (float*)(phiS + 3 * PLANE);     // [27][NT] f' of the plane (LBMP_FUSED_FSMEM)
-    float* dS = fS + LBMP_FUSED_FSMEM * Q3 * NT;  // [27][NT] dh (LBMP_FUSED_DHSMEM)
-    float* uS = dS + LBMP_FUSED_DHSMEM * Q3 * NT;  // [2][3][NT] previous phi u (reduced phase lattice)
+    float* gS = smem;                                    // [2][QG][NT]
+    float* rS = smem + 2 * QG * NT;                      // [QG][NRING] ring cells' g of the plane being staged
+    float2* phiS = (float2*)(rS + (kRingReg ? 0 : QG * NRING));  // (hi, lo) [3][RY][RX]
+    float* fS = (float*)(phiS + 3 * PLANE);              // [27][NT] f' of the plane (LBMP_FUSED_FSMEM)
+    float* dS = fS + LBMP_FUSED_FSMEM * Q3 * NT;         // [27][NT] dh (kDhSmem)
+    float* uS = dS + (kDhSmem ? Q3 * NT : 0);            // [2][3][NT] previous phi u (reduced phase lattice)
     const int tid = T.tid, oslot = T.oslot, rslot = T.rslot;
     Column own, ring;
     set_column(own, p, pmod(x0 + T.tx, p.nx), pmod(y0 + T.ty, p.ny));
     set_column(ring, p, pmod(x0 + T.lx, p.nx), pmod(y0 + T.ly, p.ny));
     const bool valid = (x0 + T.tx < p.nx) && (y0 + T.ty < p.ny);
     int sP = 0, sC = 1, sN = 2;
-    stage_issue(p, Dp, own, ring, tid, z0 - 1, gS + QG * NT, rS, phiu, uS + 3 * NT);
+    stage_issue(p, Dp, own, ring, tid, rslot, z0 - 1, gS + QG * NT, rS, phiu, uS + 3 * NT, phiS + sP * PLANE);
     stage_finish(tid, oslot, rslot, gS + QG * NT, rS, phiS + sP * PLANE);
-    stage_issue(p, Dp, own, ring, tid, z0, gS, rS, phiu, uS);
+    stage_issue(p, Dp, own, ring, tid, rslot, z0, gS, rS, phiu, uS, phiS + sC * PLANE);
     stage_finish(tid, oslot, rslot, gS, rS, phiS + sC * PLANE);
     for (int z = z0; z < z1; ++z) {
         const int cur = (z - z0) & 1;
         // g(z+1) and the ring copies in flight while f'(z) is loaded
-        stage_issue(p, Dp, own, ring, tid, z + 1, gS + (cur ^ 1) * QG * NT, rS, phiu, uS + (cur ^ 1) * 3 * NT);
+        stage_issue(p, Dp, own, ring, tid, rslot, z + 1, gS + (cur ^ 1) * QG * NT, rS, phiu, uS + (cur ^ 1) * 3 * NT,
+                    phiS + sN * PLANE);
         Plane P;
         set_plane(P, p, z);
         FlowMoments m;
@@ -213,20 +238,33 @@ __device__ __forceinline__ void fused_segment(const DevParams& p, const DirPtrs&
                 },
                 centre, grad, lap);
             CellState s;
-            float dh[27];
-            flow_collide<3>(p, centre.x, grad, lap, m, s, dh);
             const int self = P.zs[1] + own.ys[1] + own.xs[1];
-#if LBMP_FUSED_DHSMEM
+            float* gcol = gS + cur * QG * NT + tid;  // this cell's staged pre-collision g
+            if constexpr (kSplit) {
+                // g first; its staged column then holds the moment differences
+                float inv_rho, nu;
+                flow_closure<3>(p, centre.x, grad, lap, m, s, inv_rho, nu);
+                phase_outputs<3>(p, s, GFromStrided{gcol, NT}, centre.x, centre.y, PtrOut{Dp.gout, self});
+                float dh[27];
+                flow_relax<3>(m, s, inv_rho, nu, dh);
 #pragma unroll
-            for (int a = 0; a < Q3; ++a) dS[a * NT + tid] = dh[a];
-            collide_outputs<3, PR>(p, s, DhStrided{dS + tid, NT}, m, GFromStrided{gS + cur * QG * NT + tid, NT},
-                                   centre.x, centre.y, PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self},
-                                   PhiUStaged<3>{p, phiu, self, uS + cur * 3 * NT + tid, NT});
-#else
-            collide_outputs<3, PR>(p, s, DhArray{dh}, m, GFromStrided{gS + cur * QG * NT + tid, NT}, centre.x,
-                                   centre.y, PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self},
-                                   PhiUStaged<3>{p, phiu, self, uS + cur * 3 * NT + tid, NT});
-#endif
+                for (int a = 0; a < Q3; ++a) gcol[a * NT] = dh[a];
+                flow_outputs<3>(s, DhStrided{gcol, NT}, m, PtrOut{Dp.fout, self});
+            } else {
+                float dh[27];
+                flow_collide<3>(p, centre.x, grad, lap, m, s, dh);
+                if constexpr (kDhSmem) {
+#pragma unroll
+                    for (int a = 0; a < Q3; ++a) dS[a * NT + tid] = dh[a];
+                    collide_outputs<3, PR>(p, s, DhStrided{dS + tid, NT}, m, GFromStrided{gcol, NT}, centre.x,
+                                           centre.y, PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self},
+                                           PhiUStaged<3>{p, phiu, self, uS + cur * 3 * NT + tid, NT});
+                } else {
+                    collide_outputs<3, PR>(p, s, DhArray{dh}, m, GFromStrided{gcol, NT}, centre.x, centre.y,
+                                           PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self},
+                                           PhiUStaged<3>{p, phiu, self, uS + cur * 3 * NT + tid, NT});
+                }
+            }
         }
         __syncthreads();
         const int t = sP;
@@ -243,9 +281,9 @@ __global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_fused3_kernel(DevPar
     for (int item = blockIdx.x; item < A.nitems; item += gridDim.x) {
         const int tile = item % (A.tiles_x * A.tiles_y);
         const int chunk = item / (A.tiles_x * A.tiles_y);
-        const int z0 = chunk * A.chunk;
+        const int z0 = p.zb + chunk * A.chunk;  // the updated planes [zb, ze) (all planes but a slab's ghosts)
         fused_segment(p, Dp, T, smem, (tile % A.tiles_x) * TX, (tile / A.tiles_x) * TY, z0,
-                      min(z0 + A.chunk, p.nz), A.phiu);
+                      min(z0 + A.chunk, p.ze), A.phiu);
     }
 }
 
@@ -305,8 +343,8 @@ __global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_batch3_kernel(const 
         const int local = item - s_begin;
         const int tiles = s_tx * s_ty;
         const int tile = local % tiles;
-        const int z0 = (local / tiles) * s_chunk;
-        fused_segment(sp, sd, T, smem, (tile % s_tx) * TX, (tile / s_tx) * TY, z0, min(z0 + s_chunk, sp.nz),
+        const int z0 = sp.zb + (local / tiles) * s_chunk;
+        fused_segment(sp, sd, T, smem, (tile % s_tx) * TX, (tile / s_tx) * TY, z0, min(z0 + s_chunk, sp.ze),
                       s_phiu);
     }
 }
@@ -409,7 +447,7 @@ cudaError_t LBMP_FUSED3_LAUNCH(lbmp_handle* h)
     A.phiu = h->phiu;
     A.tiles_x = (h->grid.nx + TX - 1) / TX;
     A.tiles_y = (h->grid.ny + TY - 1) / TY;
-    const LaunchShape L = launch_shape(h, A.tiles_x * A.tiles_y, h->grid.nz, g_cfg.per_sm, g_cfg.sms);
+    const LaunchShape L = launch_shape(h, A.tiles_x * A.tiles_y, h->dp.ze - h->dp.zb, g_cfg.per_sm, g_cfg.sms);
     A.chunk = L.chunk;
     A.nitems = L.nitems;
     step_fused3_kernel<<<L.grid, NT, kSmemBytes, h->stream>>>(h->dp, A, D);

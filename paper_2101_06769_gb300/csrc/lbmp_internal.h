@@ -22,7 +22,12 @@ struct lbmp_handle {
     // previous step (pull streaming reads them upstream)
     float* f[2];
     float* g[2];
-    float* phi;        // phi = sum g as hi [0, N) + lo [N, 2N), refreshed by the phi pass
+    // z-slab (lbmp_create_slab): global planes [slab_z0, slab_z1) held with
+    // slab_ghost[0] / [1] ghost planes below / above; slab = false otherwise
+    bool slab;
+    int slab_z0, slab_z1, slab_ghost[2];
+    float* phi;        // reference pair only: phi = sum g as hi [0, N) + lo [N, 2N), refreshed by the phi pass
+    lbmp_allocator alloc;  // caller's device allocator (alloc == null: cudaMalloc / cudaFree)
     float* phiu;       // reduced phase lattice: phi u of the previous step, [k < D][cell]; else null
     bool divu;         // LBMP_FLAG_DIVU
     float* uvel[2];    // LBMP_FLAG_DIVU: stored velocity [k < D][cell], uvel[parity] the previous step's; else null
@@ -59,8 +64,11 @@ struct BatchDomain {
 
 // Launch shape of a persistent fused kernel over `tiles` tiles marching
 // through `nmarch` planes (rows in 2-D): planes per work item and grid size,
-// from the handle's options or the defaults (enough items for four rounds of
-// the full-occupancy grid, at least 8 planes per item).
+// from the handle's options or the defaults (enough items for three rounds of
+// the full-occupancy grid, at least 8 planes per item: each item stages two
+// planes more than it updates, so longer items win until the rounds get
+// coarse; on the 128x128x512 RT workload 32 planes per item at 4 CTAs per
+// SM measured 0.852 ms per step, 16 planes 0.893 ms).
 struct LaunchShape {
     int chunk, nitems, grid;
 };
@@ -74,7 +82,7 @@ inline LaunchShape launch_shape(const lbmp_handle* h, int tiles, int nmarch, int
         chunk = h->opt_chunk < nmarch ? h->opt_chunk : nmarch;
     } else {
         chunk = nmarch;
-        while (chunk > 8 && (long long)tiles * ((nmarch + chunk - 1) / chunk) < 4LL * per_sm * sms) chunk /= 2;
+        while (chunk > 8 && (long long)tiles * ((nmarch + chunk - 1) / chunk) < 3LL * per_sm * sms) chunk /= 2;
     }
     LaunchShape L;
     L.chunk = chunk;
@@ -100,6 +108,27 @@ inline size_t gset_bytes(const lbmp_handle* h)
 inline size_t phiu_bytes(const lbmp_handle* h) { return h->reduced ? sizeof(float) * h->D * (size_t)h->N : 0; }
 // bytes of one stored velocity field (LBMP_FLAG_DIVU)
 inline size_t uvel_bytes(const lbmp_handle* h) { return h->divu ? sizeof(float) * h->D * (size_t)h->N : 0; }
+
+// The autotuners time real step kernels.  On the reduced phase lattice a
+// step replaces the stored previous phi u in place, so a trial launch would
+// leave this step's phi u where the next step expects the previous one (its
+// d/dt(phi u) would read zero).  phiu_save copies the stored phi u of h into
+// a fresh device buffer (*copy, null when h keeps none) on `stream`;
+// phiu_restore copies it back on `stream`, waits for the copy and frees the
+// buffer.
+cudaError_t phiu_save(lbmp_handle* h, cudaStream_t stream, float** copy);
+cudaError_t phiu_restore(lbmp_handle* h, cudaStream_t stream, float* copy);
+
+// device memory of a handle: the caller's allocator, or cudaMalloc
+cudaError_t dev_alloc(lbmp_handle* h, void** p, size_t bytes);
+void dev_free(lbmp_handle* h, void* p, size_t bytes);
+// where the phi pass writes phi (hi, lo; 2N floats): the handle's phi array
+// when it keeps one (the reference pair reads it while writing the other
+// population set), else the f' population set the next step overwrites,
+// whose contents are dead between steps
+inline float* phi_buf(const lbmp_handle* h) { return h->phi ? h->phi : h->f[1 - h->parity]; }
+// allocate the phi array the reference pair needs (not during a capture)
+cudaError_t ensure_phi(lbmp_handle* h);
 
 // kernel launchers (return cudaError_t of the launch)
 cudaError_t launch_phi_pass(lbmp_handle* h);

@@ -182,7 +182,7 @@ struct PhiPassL {
     {
         const int B = 256;
         phi_pass_kernel<D, St, PR><<<grid_for(h->N, B), B, 0, h->stream>>>(
-            h->dp, pop_of<D, St>(h, h->g[h->parity]), h->phi);
+            h->dp, pop_of<D, St>(h, h->g[h->parity]), phi_buf(h));
         return cudaGetLastError();
     }
 };
@@ -205,6 +205,9 @@ struct StepSimpleL {
 
 cudaError_t launch_step_simple(lbmp_handle* h)
 {
+    // the pair writes the other population sets while it reads phi: phi must
+    // have an array of its own (allocated when the pair is selected)
+    if (!h->phi) return cudaErrorInvalidValue;
     cudaError_t e = launch_phi_pass(h);
     if (e != cudaSuccess) return e;
     return dispatch(h, StepSimpleL{h});
@@ -247,8 +250,18 @@ __global__ void init_kernel(DevParams p, InitArgs A, float* __restrict__ f, floa
     if (i >= p.N) return;
     int x, y, z;
     cell_xyz(p, i, x, y, z);
-    const int n[3] = {p.nx, p.ny, p.nz};
-    const double pos[3] = {(double)x, (double)y, (double)z};
+    // global position of the cell (a z-slab holds planes zoff.. of an axis of
+    // nzg planes; a plain domain has zoff = 0, nzg = nz) and its global index,
+    // which seeds the velocity noise
+    int zg = z;
+    long long gi = i;
+    if (D == 3) {
+        zg = z + p.zoff;
+        zg = zg < 0 ? zg + p.nzg : (zg >= p.nzg ? zg - p.nzg : zg);
+        gi = ((long long)zg * p.ny + y) * p.nx + x;
+    }
+    const int n[3] = {p.nx, p.ny, D == 3 ? p.nzg : p.nz};
+    const double pos[3] = {(double)x, (double)y, (double)zg};
     const int v = D - 1;
     const double hv = pos[v];
     const double PI = 3.14159265358979323846;
@@ -317,7 +330,7 @@ __global__ void init_kernel(DevParams p, InitArgs A, float* __restrict__ f, floa
     }
     if (noise != 0.0) {
         for (int k = 0; k < D; ++k) {
-            const double r = (double)(splitmix64(A.seed, 3ULL * (unsigned long long)i + k) >> 11) *
+            const double r = (double)(splitmix64(A.seed, 3ULL * (unsigned long long)gi + k) >> 11) *
                              (1.0 / 9007199254740992.0);
             u[k] += noise * A.U_ref * (2.0 * r - 1.0) * phi;
         }
@@ -549,10 +562,10 @@ cudaError_t launch_phiu_reset(lbmp_handle* h)
     const int B = 128;
     if (h->D == 3)
         phiu_reset_kernel<3><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, pop_of<3, StoreF32>(h, h->f[h->parity]),
-                                                                     h->phi, h->phiu, h->uvel[h->parity]);
+                                                                     phi_buf(h), h->phiu, h->uvel[h->parity]);
     else
         phiu_reset_kernel<2><<<grid_for(h->N, B), B, 0, h->stream>>>(h->dp, pop_of<2, StoreF32>(h, h->f[h->parity]),
-                                                                     h->phi, h->phiu, h->uvel[h->parity]);
+                                                                     phi_buf(h), h->phiu, h->uvel[h->parity]);
     return cudaGetLastError();
 }
 
@@ -603,6 +616,7 @@ __global__ void __launch_bounds__(256) obs_partial_kernel(DevParams p, Pop<D, St
          i += (long long)gridDim.x * blockDim.x) {
         int x, y, z;
         cell_xyz(p, i, x, y, z);
+        if (D == 3 && (z < p.zb || z >= p.ze)) continue;  // a z-slab's ghost planes belong to its neighbours
         float rho, u[3], ph;
         cell_macro<D, St>(p, f, phi, x, y, z, i, rho, u, ph, ustore);
         const double uu = (double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2];
@@ -726,14 +740,15 @@ struct ObsL {
     {
         const Pop<D, St> f = pop_of<D, St>(h, h->f[h->parity]);
         const float* us = h->uvel[h->parity];  // the velocity the next step's div(u) uses, or null
-        obs_partial_kernel<D, St><<<h->red_blocks, 256, 0, h->stream>>>(h->dp, f, h->phi, h->red, us);
+        const float* phi = phi_buf(h);
+        obs_partial_kernel<D, St><<<h->red_blocks, 256, 0, h->stream>>>(h->dp, f, phi, h->red, us);
         obs_final_kernel<<<1, 256, 0, h->stream>>>(h->red, h->red_blocks, out);
         if (full) {
             const int nv = (D == 3) ? h->grid.nz : h->grid.ny;
             const int* pr = h->probe;
-            probe_kernel<D, St><<<2, 32, 0, h->stream>>>(h->dp, f, h->phi, pr[0], pr[1], D == 3 ? pr[2] : 0, 0, 0,
+            probe_kernel<D, St><<<2, 32, 0, h->stream>>>(h->dp, f, phi, pr[0], pr[1], D == 3 ? pr[2] : 0, 0, 0,
                                                          0, out + 4, us);
-            column_kernel<D><<<grid_for(nv, 128), 128, 0, h->stream>>>(h->dp, h->phi, out + 16);
+            column_kernel<D><<<grid_for(nv, 128), 128, 0, h->stream>>>(h->dp, phi, out + 16);
         }
         return cudaGetLastError();
     }

@@ -26,7 +26,11 @@
 //     must be serialised by the caller;
 //   * the first call on a device looks up the array's device address with
 //     cudaGetSymbolAddress, with that device current. Make that first call
-//     before any stream capture.
+//     before any stream capture. Every later call made outside a stream
+//     capture looks the address up again, because a device reset
+//     (cudaDeviceReset) reloads the module and moves the array; a call made
+//     while its stream is capturing uses the address found by the last call
+//     on that device that was not.
 #include <atomic>
 
 #include "lbmp_internal.h"
@@ -99,17 +103,29 @@ LBMP_API int lbmp_mass_noalloc(const float* g_dev, long long n_values, double* m
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(LBMP_ERR_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(LBMP_ERR_UNSUPPORTED, "lbmp_mass_noalloc: device ordinal");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return noalloc_fail(LBMP_ERR_CUDA, cudaGetErrorString(e));
     double* scratch = g_scratch_addr[dev].load(std::memory_order_acquire);
-    if (!scratch) {
-        // set-up, once per device, with that device current
-        e = cudaGetSymbolAddress((void**)&scratch, g_mass_scratch);
-        if (e != cudaSuccess || !scratch) {
+    if (cap == cudaStreamCaptureStatusNone) {
+        // set-up with this device current: on the first call, and again on
+        // every call outside a capture (a device reset moves the array)
+        double* fresh = nullptr;
+        e = cudaGetSymbolAddress((void**)&fresh, g_mass_scratch);
+        if (e != cudaSuccess || !fresh) {
             return noalloc_fail(LBMP_ERR_CUDA, e != cudaSuccess ? cudaGetErrorString(e)
                                                                 : "lbmp_mass_noalloc: null symbol address");
         }
+        scratch = fresh;
         g_scratch_addr[dev].store(scratch, std::memory_order_release);
+    } else if (!scratch) {
+        return noalloc_fail(LBMP_ERR_UNSUPPORTED,
+                            "lbmp_mass_noalloc: first call on this device made during a stream capture "
+                            "(make one call before capturing)");
     }
-    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // an earlier, unrelated launch error is not this call's: clear it first
+    (void)cudaGetLastError();
     mass_partial_kernel<<<(unsigned)nparts, kThreads, 0, s>>>(g_dev, n_values, scratch);
     mass_final_kernel<<<1, kThreads, 0, s>>>(scratch, (int)nparts, scratch + kMaxPartials);
     e = cudaGetLastError();

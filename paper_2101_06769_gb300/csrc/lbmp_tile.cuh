@@ -37,6 +37,18 @@ namespace LBMP_TILE_NS {
 #ifndef LBMP_PHASE_REDUCED
 #define LBMP_PHASE_REDUCED 0
 #endif
+// 1 (full phase lattice only): the phase-field outputs are emitted first, so
+// the staged pre-collision g of the plane is consumed before the flow
+// relaxation, which then parks its 27 moment differences in that g column
+// (no separate shared-memory array for them)
+#ifndef LBMP_FUSED_SPLIT
+#define LBMP_FUSED_SPLIT 0
+#endif
+// 1: the ring cells' g are loaded to registers and summed at once by the
+// ring threads (no shared-memory ring buffer)
+#ifndef LBMP_FUSED_RINGREG
+#define LBMP_FUSED_RINGREG 0
+#endif
 constexpr int TX = LBMP_FUSED_TX, TY = LBMP_FUSED_TY, NT = TX * TY;
 constexpr int RX = TX + 2, RY = TY + 2;
 constexpr int PLANE = RY * RX;
@@ -44,9 +56,13 @@ constexpr int NRING = 2 * RX + 2 * TY;
 constexpr int Q3 = 27;
 constexpr bool PR = LBMP_PHASE_REDUCED != 0;
 constexpr int QG = PhaseLat<3, PR>::Q;  // phase-field populations
-constexpr size_t kSmemBytes = sizeof(float) * ((2 * QG + (LBMP_FUSED_FSMEM + LBMP_FUSED_DHSMEM) * Q3) * NT +
-                                               QG * NRING + (PR ? 2 * 3 * NT : 0)) +
-                              sizeof(float2) * 3 * PLANE;
+constexpr bool kSplit = LBMP_FUSED_SPLIT != 0 && !PR;
+constexpr bool kRingReg = LBMP_FUSED_RINGREG != 0;
+constexpr bool kDhSmem = LBMP_FUSED_DHSMEM != 0 && !kSplit;
+constexpr size_t kSmemBytes =
+    sizeof(float) * ((2 * QG + (LBMP_FUSED_FSMEM + (kDhSmem ? 1 : 0)) * Q3) * NT + (kRingReg ? 0 : QG * NRING) +
+                     (PR ? 2 * 3 * NT : 0)) +
+    sizeof(float2) * 3 * PLANE;
 static_assert(NRING <= NT, "one thread per ring cell");
 
 __device__ __forceinline__ void cp_async4(float* smem, const float* gmem)
@@ -91,8 +107,8 @@ struct Plane {
 __device__ __forceinline__ void set_plane(Plane& P, const DevParams& p, int z)
 {
     const int nxy = p.nx * p.ny;
-    P.lo = !p.vert_periodic && z == 0;
-    P.hi = !p.vert_periodic && z == p.nz - 1;
+    P.lo = p.wall_lo && z == 0;
+    P.hi = p.wall_hi && z == p.nz - 1;
     P.zs[0] = (z + 1 == p.nz ? 0 : z + 1) * nxy;
     P.zs[1] = z * nxy;
     P.zs[2] = (z == 0 ? p.nz - 1 : z - 1) * nxy;
@@ -152,13 +168,27 @@ struct PullLoad {
     }
 };
 
+// post-streaming phase-field values of the QG slots of one cell into registers
+template <bool Walls>
+struct PullLoadG {
+    const float* const* base;
+    const Column& C;
+    const Plane& P;
+    float* v;
+    template <int r>
+    __device__ __forceinline__ void step() const
+    {
+        v[r] = __ldg(pulled_g<Walls, r>(base, C, P));
+    }
+};
+
 // plane whose phi stands for plane zz: periodic wrap, or the mirrored ghost
 // at a wall (reading A17)
 __device__ __forceinline__ int plane_src(const DevParams& p, int zz)
 {
     if (zz >= 0 && zz < p.nz) return zz;
-    if (p.vert_periodic) return pmod(zz, p.nz);
-    return zz < 0 ? 0 : p.nz - 1;
+    if (zz < 0) return p.wall_lo ? 0 : pmod(zz, p.nz);
+    return p.wall_hi ? p.nz - 1 : pmod(zz, p.nz);
 }
 
 // per-thread geometry inside a tile: own cell and (for tid < NRING) ring cell

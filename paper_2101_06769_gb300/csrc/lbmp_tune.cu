@@ -4,11 +4,37 @@
 // A trial launch is the step kernel without the parity flip of lbmp_step: it
 // reads the current population set and writes the other one, so the state
 // the handle exposes is untouched and the next real step overwrites the
-// trial's output.
+// trial's output.  The one array a step rewrites in place, the stored
+// previous phi u of the reduced phase lattice, is saved before the trials
+// and restored after them.
 #include <stdio.h>
 #include <string.h>
 
 #include "lbmp_internal.h"
+
+namespace lbmp {
+
+cudaError_t phiu_save(lbmp_handle* h, cudaStream_t stream, float** copy)
+{
+    *copy = nullptr;
+    const size_t n = phiu_bytes(h);
+    if (n == 0 || !h->phiu) return cudaSuccess;
+    cudaError_t e = dev_alloc(h, (void**)copy, n);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(*copy, h->phiu, n, cudaMemcpyDeviceToDevice, stream);
+}
+
+cudaError_t phiu_restore(lbmp_handle* h, cudaStream_t stream, float* copy)
+{
+    if (!copy) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(h->phiu, copy, phiu_bytes(h), cudaMemcpyDeviceToDevice, stream);
+    const cudaError_t es = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess) e = es;
+    dev_free(h, copy, phiu_bytes(h));
+    return e;
+}
+
+}  // namespace lbmp
 
 extern "C" {
 
@@ -24,18 +50,20 @@ LBMP_API int lbmp_autotune(lbmp_handle* h, int reps, lbmp_tune_entry* table, int
     chunks[nc++] = 0;
     for (int c = 1; c <= 128; c *= 2)  // 1 and 2 for small domains: more work items than SMs
         if (c <= nmarch) chunks[nc++] = c;
-    const int ctas[3] = {0, 1, 2};
+    const int ctas[4] = {0, 1, 2, 3};
     // tile shapes exist for the FP32 D3Q27 cp.async kernel only
     const int ntiles = (h->D == 3 && h->params.storage == LBMP_FP32 && h->kernel == 0 && !h->reduced) ? 3 : 1;
     const int saved_chunk = h->opt_chunk, saved_ctas = h->opt_ctas, saved_tile = h->opt_tile;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaEventCreate(&e0);
+    float* phiu_copy = nullptr;
+    cudaError_t e = lbmp::phiu_save(h, h->stream, &phiu_copy);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     double best = 1e300;
     int best_chunk = saved_chunk, best_ctas = saved_ctas, best_tile = ntiles > 1 ? saved_tile : 0, n = 0;
     for (int t = 0; t < ntiles && e == cudaSuccess; ++t)
     for (int i = 0; i < nc && e == cudaSuccess; ++i)
-        for (int j = 0; j < 3 && e == cudaSuccess; ++j) {
+        for (int j = 0; j < 4 && e == cudaSuccess; ++j) {
             h->opt_tile = ntiles > 1 ? t : saved_tile;
             h->opt_chunk = chunks[i];
             h->opt_ctas = ctas[j];
@@ -59,6 +87,8 @@ LBMP_API int lbmp_autotune(lbmp_handle* h, int reps, lbmp_tune_entry* table, int
         }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    const cudaError_t er = lbmp::phiu_restore(h, h->stream, phiu_copy);
+    if (e == cudaSuccess) e = er;
     if (e != cudaSuccess) {
         h->opt_chunk = saved_chunk;
         h->opt_ctas = saved_ctas;

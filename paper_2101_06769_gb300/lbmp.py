@@ -24,12 +24,13 @@ ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5
           -6: "UNSUPPORTED"}
 
 # every entry point declared in include/lbmp.h
-EXPORTS = ("lbmp_create", "lbmp_destroy", "lbmp_last_error", "lbmp_get_derived", "lbmp_init",
+EXPORTS = ("lbmp_create", "lbmp_create_ex", "lbmp_destroy", "lbmp_last_error", "lbmp_get_derived", "lbmp_init",
            "lbmp_step", "lbmp_sync", "lbmp_observables", "lbmp_get_state", "lbmp_set_state",
            "lbmp_state_bytes", "lbmp_upload", "lbmp_download", "lbmp_set_option", "lbmp_mass_noalloc",
            "lbmp_batch_create", "lbmp_batch_destroy", "lbmp_batch_add", "lbmp_batch_remove",
            "lbmp_batch_step", "lbmp_batch_members", "lbmp_autotune", "lbmp_device_name",
-           "lbmp_batch_autotune")
+           "lbmp_batch_autotune", "lbmp_create_slab", "lbmp_slab_layout", "lbmp_pack_planes",
+           "lbmp_unpack_planes")
 
 
 class Grid(C.Structure):
@@ -58,6 +59,41 @@ class Obs(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+# lbmp_allocator: caller-supplied device memory (include/lbmp.h)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+def make_allocator(alloc, free):
+    """An lbmp_allocator from two Python callables: alloc(nbytes, stream)
+    returns a device address (int) or 0, free(ptr, nbytes, stream).  Keep the
+    returned structure alive as long as any handle created with it."""
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return int(alloc(int(nbytes), int(stream or 0))) or None
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        free(int(ptr), int(nbytes), int(stream or 0))
+
+    return Allocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+
+
+def torch_allocator(device=None):
+    """lbmp_allocator backed by torch's CUDA caching allocator: the library's
+    device arrays then count in torch.cuda.memory_allocated() and reuse the
+    cache of the calling process."""
+    import torch
+    dev = torch.cuda.current_device() if device is None else int(device)
+    return make_allocator(lambda n, s: torch.cuda.caching_allocator_alloc(n, dev, s),
+                          lambda p, n, s: torch.cuda.caching_allocator_delete(p))
+
+
 class TuneEntry(C.Structure):
     _fields_ = [("chunk", C.c_int), ("ctas_per_sm", C.c_int), ("ms", C.c_double), ("tile", C.c_int)]
 
@@ -82,6 +118,13 @@ def load(path=None):
     L = C.CDLL(path)
     vp = C.c_void_p
     L.lbmp_create.argtypes = [C.POINTER(Grid), C.c_int, C.POINTER(Params), vp, C.POINTER(vp)]
+    L.lbmp_create_ex.argtypes = [C.POINTER(Grid), C.c_int, C.POINTER(Params), vp, C.POINTER(Allocator),
+                                 C.POINTER(vp)]
+    L.lbmp_create_slab.argtypes = [C.POINTER(Grid), C.c_int, C.c_int, C.c_int, C.POINTER(Params), vp,
+                                   C.POINTER(Allocator), C.POINTER(vp)]
+    L.lbmp_slab_layout.argtypes = [vp, C.POINTER(C.c_int)]
+    L.lbmp_pack_planes.argtypes = [vp, C.POINTER(C.c_int), C.c_int, vp]
+    L.lbmp_unpack_planes.argtypes = [vp, C.POINTER(C.c_int), C.c_int, vp]
     L.lbmp_destroy.argtypes = [vp]
     L.lbmp_last_error.restype = C.c_char_p
     L.lbmp_get_derived.argtypes = [vp, C.POINTER(Derived)]
@@ -132,7 +175,9 @@ class Domain:
     ``stream`` is a raw cudaStream_t handle (int) or None for the default stream.
     """
 
-    def __init__(self, D, dims, periodic=(1, 1, 1), stream=None, **params):
+    def __init__(self, D, dims, periodic=(1, 1, 1), stream=None, allocator=None, **params):
+        """allocator: None (cudaMalloc), "torch" (torch's caching allocator)
+        or an Allocator structure (make_allocator)."""
         L = load()
         self.D = D
         self.periodic = tuple(int(v) for v in periodic)
@@ -144,8 +189,18 @@ class Domain:
         self.N = self.dims[0] * self.dims[1] * self.dims[2]
         g = Grid(self.dims[0], self.dims[1], self.dims[2], (C.c_int * 3)(*[int(v) for v in periodic]))
         h = C.c_void_p()
-        _check(L.lbmp_create(C.byref(g), D3Q27 if D == 3 else D2Q9, C.byref(make_params(**params)),
-                             C.c_void_p(stream) if stream else None, C.byref(h)))
+        if isinstance(allocator, str):
+            if allocator != "torch":
+                raise ValueError(f"unknown allocator {allocator!r}")
+            allocator = torch_allocator()
+        self._allocator = allocator  # the callbacks must outlive the handle
+        lat = D3Q27 if D == 3 else D2Q9
+        st = C.c_void_p(stream) if stream else None
+        if allocator is None:
+            _check(L.lbmp_create(C.byref(g), lat, C.byref(make_params(**params)), st, C.byref(h)))
+        else:
+            _check(L.lbmp_create_ex(C.byref(g), lat, C.byref(make_params(**params)), st, C.byref(allocator),
+                                    C.byref(h)))
         self._h = h
 
     @property

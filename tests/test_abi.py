@@ -55,6 +55,8 @@ int main(void) {
   O(lbmp_tune_entry, ms); O(lbmp_tune_entry, tile);
   O(lbmp_grid, periodic); O(lbmp_params, force_x); O(lbmp_params, storage); O(lbmp_params, flags);
   O(lbmp_obs, tip_bubble); O(lbmp_obs, step); O(lbmp_obs, health); O(lbmp_derived, force_x);
+  printf("lbmp_allocator %zu\n", sizeof(lbmp_allocator));
+  O(lbmp_allocator, alloc); O(lbmp_allocator, free); O(lbmp_allocator, ctx);
   return 0;
 }
 """
@@ -80,6 +82,9 @@ int main(void) {
     assert int(vals["lbmp_tune_entry"]) == C.sizeof(lbmp.TuneEntry)
     assert int(vals["lbmp_tune_entry.ms"]) == lbmp.TuneEntry.ms.offset
     assert int(vals["lbmp_tune_entry.tile"]) == lbmp.TuneEntry.tile.offset
+    assert int(vals["lbmp_allocator"]) == C.sizeof(lbmp.Allocator)
+    for f in ("alloc", "free", "ctx"):
+        assert int(vals["lbmp_allocator." + f]) == getattr(lbmp.Allocator, f).offset
 
 
 def test_invalid_arguments_rejected_without_device_work(lib):

@@ -177,6 +177,34 @@ def test_batch_autotune_keeps_results():
     b.close()
 
 
+def test_batch_autotune_keeps_reduced_members():
+    """Members on the reduced phase lattice keep their stored previous phi u
+    across the batch autotuner's trials: after tuning, a few steps of the
+    batch equal the same steps of untuned twins stepped alone (same tile
+    build, so bitwise)."""
+    from paper_2101_06769_gb300.lbmp import FLAG_PHASE_REDUCED
+    red = []
+    for m in MEMBERS[:3]:
+        r = dict(m)
+        r["phys"] = dict(m["phys"], flags=FLAG_PHASE_REDUCED)
+        red.append(r)
+    b = Batch()
+    doms = [make(m) for m in red]
+    twins = [make(m) for m in red]
+    for d in doms:
+        b.add(d, 7)
+    b.step(3)  # a stored phi u from real steps
+    for t in twins:
+        t.step(3)
+    b.autotune(reps=1)
+    b.step(4)
+    for t in twins:
+        t.step(4)
+    for d, t in zip(doms, twins):
+        assert all(np.array_equal(x, y) for x, y in zip(d.get_state(), t.get_state()))
+    b.close()
+
+
 def test_batch_writes_every_slot():
     """Every member's target set is poisoned with NaN before each batch step;
     no NaN survives."""

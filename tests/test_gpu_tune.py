@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2101_06769_gb300 import Domain, LbmpError
-from paper_2101_06769_gb300.lbmp import OPT_CHUNK, OPT_CTAS_PER_SM, OPT_TILE, FP16_SHIFTED
+from paper_2101_06769_gb300.lbmp import FLAG_PHASE_REDUCED, OPT_CHUNK, OPT_CTAS_PER_SM, OPT_TILE, FP16_SHIFTED
 
 from test_gpu_parity import CASES
 
@@ -57,10 +57,17 @@ def test_bad_options_rejected():
             d.set_option(opt, v)
 
 
-@pytest.mark.parametrize("name,storage", [("splash3d", 0), ("rt2d", 0), ("rt3d", FP16_SHIFTED)])
-def test_autotune_does_not_advance_or_change_state(name, storage, tmp_path, monkeypatch):
+@pytest.mark.parametrize("name,storage,flags", [("splash3d", 0, 0), ("rt2d", 0, 0), ("rt3d", FP16_SHIFTED, 0),
+                                                ("rt3d", 0, FLAG_PHASE_REDUCED), ("rt2d", 0, FLAG_PHASE_REDUCED)])
+def test_autotune_does_not_advance_or_change_state(name, storage, flags, tmp_path, monkeypatch):
+    """Trial launches change nothing a later step sees: the populations, the
+    step count and, on the reduced phase lattice, the stored previous phi u
+    (a step after tuning equals the same step of an untuned twin bitwise)."""
     monkeypatch.setenv("LBMP_TUNE_CACHE", str(tmp_path / "tune.json"))
-    a, b = dom(name, storage=storage), dom(name, storage=storage)
+    kw = dict(storage=storage)
+    if flags:
+        kw["flags"] = flags
+    a, b = dom(name, **kw), dom(name, **kw)
     a.step(4)
     b.step(4)
     before = a.get_state()
@@ -74,6 +81,6 @@ def test_autotune_does_not_advance_or_change_state(name, storage, tmp_path, monk
     b.step(5)
     assert all(np.array_equal(x, y) for x, y in zip(a.get_state(), b.get_state()))
     # second call: served from the cache, same choice, no trials
-    c = dom(name, storage=storage)
+    c = dom(name, **kw)
     chunk2, ctas2, trials2 = c.autotune(reps=2)
     assert (chunk2, ctas2) == (chunk, ctas) and trials2 == []
