@@ -195,6 +195,21 @@ __device__ __forceinline__ long long pull_src(const DevParams& p, int a, int x, 
     }
 }
 
+// A z-slab's ghost cell whose pull source lies across a local end without a
+// wall has no slot in this slab (the neighbour's planes hold it): writers of
+// the state skip it instead of wrapping onto the opposite end, where the
+// wrapped index belongs to another cell (a wall plane's bounce-back slot,
+// for one).  Always true for a plain domain (zb = 0, ze = nz).
+template <int D>
+__device__ __forceinline__ bool has_pull_slot(const DevParams& p, int a, int z)
+{
+    if (D != 3) return true;
+    const int zs = z - Lat<D>::cz(a);
+    if (zs < 0) return p.wall_lo || p.zb == 0;
+    if (zs >= p.nz) return p.wall_hi || p.ze == p.nz;
+    return true;
+}
+
 template <int D>
 __device__ __forceinline__ long long pull_index(const DevParams& p, int a, int x, int y, int z, long long self)
 {

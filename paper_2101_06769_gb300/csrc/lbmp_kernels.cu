@@ -348,7 +348,7 @@ __global__ void init_kernel(DevParams p, InitArgs A, float* __restrict__ f, floa
         if (cf) {
             cf[(long long)a * p.N + i] = fe;
             cg[(long long)a * p.N + i] = ge;
-        } else {
+        } else if (has_pull_slot<D>(p, a, z)) {
             const long long slot = pull_index<D>(p, a, x, y, z, i);
             f[slot] = (float)fe;
             if (!PR) g[slot] = (float)ge;
@@ -362,6 +362,7 @@ __global__ void init_kernel(DevParams p, InitArgs A, float* __restrict__ f, floa
             const int a = PhaseLat<D, true>::full(r);
             const double w = (r == C) ? (D == 3 ? 0.25 : 1.0 / 3.0) : (D == 3 ? 0.125 : 1.0 / 6.0);
             const double cu = Lat<D>::cx(a) * u[0] + Lat<D>::cy(a) * u[1] + Lat<D>::cz(a) * u[2];
+            if (!has_pull_slot<D>(p, a, z)) continue;
             int slot;
             const long long c = pull_src_g<D, true>(p, r, x, y, z, i, slot);
             g[(long long)slot * p.N + c] = (float)(w * phi * (1.0 + cu * (D == 3 ? 4.0 : 3.0)));
@@ -463,9 +464,10 @@ __global__ void set_state_f32_kernel(DevParams p, float* f, float* g, const doub
     cell_xyz(p, i, x, y, z);
 #pragma unroll
     for (int a = 0; a < Lat<D>::Q; ++a)
-        f[pull_index<D>(p, a, x, y, z, i)] = (float)cf[(long long)a * p.N + i];
+        if (has_pull_slot<D>(p, a, z)) f[pull_index<D>(p, a, x, y, z, i)] = (float)cf[(long long)a * p.N + i];
 #pragma unroll
     for (int r = 0; r < PhaseLat<D, PR>::Q; ++r) {
+        if (!has_pull_slot<D>(p, PhaseLat<D, PR>::full(r), z)) continue;
         int slot;
         const long long c = pull_src_g<D, PR>(p, r, x, y, z, i, slot);
         g[(long long)slot * p.N + c] = (float)cg[(long long)r * p.N + i];
