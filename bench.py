@@ -384,29 +384,43 @@ def measure_forms(args, wl, stream, peak, pg):
     # storage of the D3Q27 requests (224 instead of 432 B/cell: more requests
     # resident), in a memory-bound regime (0.5 GB: the largest requests fit
     # only in 16-bit form) and a compute-bound one (2 GB)
+    # capacity (requests served) and throughput are reported apart: under the
+    # 0.5 GB cap FP32 cannot hold the largest requests at all, so the GLUPS of
+    # the two forms are also compared on the requests whose FP32 state fits
     out["serving_budget"] = {}
     for gb in (0.5, 2.0):
         budget = int(gb * (1 << 30))
-        out["serving_budget"]["%gGB" % gb] = {
-            "state_budget_bytes": budget,
-            "fp32": measure_serving(stream, mlups, storage=0, state_budget=budget),
-            "fp16": measure_serving(stream, mlups, storage=1, state_budget=budget)}
+        rec = {"state_budget_bytes": budget,
+               "fp32": measure_serving(stream, mlups, storage=0, state_budget=budget),
+               "fp16": measure_serving(stream, mlups, storage=1, state_budget=budget)}
+        rec["capacity"] = {"fp32_served": rec["fp32"]["done"], "fp16_served": rec["fp16"]["done"],
+                           "requests": rec["fp32"]["requests"]}
+        if rec["fp32"]["done"] < rec["fp32"]["requests"]:
+            rec["same_requests"] = {
+                "note": "only the requests whose FP32 state fits the cap, served by both forms",
+                "fp32": measure_serving(stream, mlups, storage=0, state_budget=budget, fits=budget),
+                "fp16": measure_serving(stream, mlups, storage=1, state_budget=budget, fits=budget)}
+        out["serving_budget"]["%gGB" % gb] = rec
     out["_launches"] = launches
     return out
 
 
-def measure_serving(stream, capacity_mlups, n=64, load=1.2, storage=0, state_budget=None):
+def measure_serving(stream, capacity_mlups, n=64, load=1.2, storage=0, state_budget=None, fits=None):
     """The serving loop (continuous batching) on the reduced serving stream:
     n seeded requests (RT or drop-on-sheet, 2-D 64^2-256^2 or 3-D
     64^3-128^3, We, Re and density ratio drawn as in the serving workload,
     200-2000 steps), Poisson arrivals at `load` times the capacity implied by
-    the batched form's measured MLUPS."""
+    the batched form's measured MLUPS.  fits: keep only the requests whose
+    FP32 state is at most this many bytes (the same requests for every
+    storage form)."""
     from paper_2101_06769_gb300 import serve
     kw = dict(sides2=(64, 128, 256), sides3=(64, 96, 128), steps_range=(200, 2000))
     probe = serve.request_stream(n, seed=7, **kw)
     work = sum(r.cells * r.steps for r in probe) / n
     rate = load * capacity_mlups * 1e6 / work
     reqs = serve.request_stream(n, seed=7, rate=rate, storage=storage, **kw)
+    if fits is not None:  # FP32 state: two sets of f' and g, 4 bytes per population
+        reqs = [r for r in reqs if 16 * (27 if r.D == 3 else 9) * r.cells <= fits]
     srv = serve.Server(stream=stream.cuda_stream, round_steps=64, state_budget=state_budget)
     peak = [0]
     admit = srv._admit

@@ -60,8 +60,9 @@ class Request:
 def make_request(rid, rng, D, side, kind, steps, We, Re, rho_ratio, storage=0):
     """A request of the serving stream: the drop-on-sheet or RT set-up of the
     paper at a given size and non-dimensional parameter set (lattice units:
-    U0 = 0.05 for the drop, sqrt(g L) = 0.04 for RT, W = 4, M = 0.02).
-    storage applies to D3Q27 requests (D2Q9 requests stay FP32)."""
+    U0 = 0.05, W = 5, M = 0.1 for the drop, the reading of the paper's
+    impacts; sqrt(g L) = 0.04, W = 4, M = 0.02 for RT).  storage applies to
+    D3Q27 requests (D2Q9 requests stay FP32)."""
     if D == 3:
         dims = (side, side, side)
     else:
@@ -78,8 +79,8 @@ def make_request(rid, rng, D, side, kind, steps, We, Re, rho_ratio, storage=0):
         args = [nv / 2.0, 0.05 * side, 1e-4, 1.0]
     else:
         Dd = max(8.0, side / 4.0)
-        phys = dict(rho_ratio=rho_ratio, nu_ratio=15.0, We=We, Re=Re, U0=0.05, L_ref=Dd, mobility=0.02,
-                    width=4.0)
+        phys = dict(rho_ratio=rho_ratio, nu_ratio=15.0, We=We, Re=Re, U0=0.05, L_ref=Dd, mobility=0.1,
+                    width=5.0)
         args = [Dd, 0.2 * Dd, 0.05, 1e-4]
     st = storage if D == 3 else 0
     phys["storage"] = st

@@ -95,24 +95,34 @@ def spread(case, times, slice3d=False):
     return out
 
 
+# t/T at which r_K is compared with the paper's line, and the lower bound of
+# r_K / (1.1 sqrt(t/T)): the neck on the first row above the film is measured
+# until the ejected lamella reaches that row (after t/T = 0.2 for the two
+# Re = 1000 impacts, 0.5 for Re = 200)
+SPLASH = {"splash2d_k56": ((0.25, 0.5), 0.78, 3.0), "splash2d_k83": ((0.15, 0.2), 0.78, 3.0),
+          "splash2d_k264": ((0.15, 0.2), 0.78, 3.0), "splash3d": ((0.1, 0.2), 0.5, 1.0)}
+
+
 @pytest.mark.parametrize("case,slice3d", [("splash2d_k56", False), ("splash2d_k83", False), ("splash2d_k264", False),
                                           ("splash3d", True)])
 def test_droplet_splash_spreading_radius(case, slice3d):
     """Sec. 3.4: after impact the neck radius grows like sqrt(t) at first; the
-    paper plots r_K/D = 1.1 sqrt(t/T).  On the three 2-D impacts (K = 55.7,
-    83.4, 263.8; D = 100, W = 8) at t/T = 0.2, 0.3 and on the reduced-size 3-D
-    impact (D = 64, W = 4) at t/T = 0.1, 0.2 the measured neck radius grows
-    monotonically and stays at 0.5-1.0 of that line (measured: 2-D 0.58/0.73,
-    0.74/0.82, 0.75/0.82; 3-D 0.56/0.77); later the lamella reaches the
-    measuring row.  Every run stays finite to t/T = 1 and keeps its mass."""
-    times = [0.2, 0.3, 1.0] if not slice3d else [0.1, 0.2, 1.0]
-    rows = spread(case, times, slice3d)
+    paper plots r_K/D = 1.1 sqrt(t/T).  The three 2-D impacts (K = 55.7,
+    83.4, 263.8; D = 100, W = 5, M = 0.1) run finite to t/T = 3 and their
+    measured neck radius stays within 22 % of that line while the row
+    measurement holds (measured 0.81 / 0.84 at t/T = 0.25 / 0.5 for K = 55.7,
+    0.82 / 0.80 at 0.15 / 0.2 for K = 83.4 and 263.8); the reduced-size 3-D
+    impact (D = 64, W = 4) grows monotonically at 0.5-1.0 of the line at
+    t/T = 0.1, 0.2 (measured 0.56 / 0.77) and runs finite to t/T = 1.  Every
+    run keeps its mass."""
+    (t1, t2), low, t_end = SPLASH[case]
+    rows = spread(case, [t1, t2, t_end], slice3d)
     assert all(h == 0 and abs(drift) <= 1e-6 for _, h, drift in rows)
     radii = [r for r, _, _ in rows[:2]]
     assert radii[1] > radii[0], radii
-    for tt, r in zip(times[:2], radii):
+    for tt, r in zip((t1, t2), radii):
         ratio = r / (1.1 * np.sqrt(tt))
-        assert 0.5 <= ratio <= 1.0, (case, tt, r, ratio)
+        assert low <= ratio <= (1.0 if slice3d else 1.2), (case, tt, r, ratio)
 
 
 def test_reduced_phase_lattice_physics():
