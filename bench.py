@@ -331,6 +331,28 @@ def measure_forms(args, wl, stream, peak, pg):
                                 "step_fused2_kernel (D2Q5 phase field)",
                                 "traffic": traffic_per_launch(args.workload, "reduced", d.N)}
         d.close()
+    # in-place AA storage (one population set each for f' and g, phi from a
+    # pass of its own): half the state; the phi pass reads g once more and
+    # writes phi (116 B/cell beyond the algorithmic 432), and the step reads it
+    if args.storage == "fp32" and args.kernel == 0 and args.phase == "full" and D == 3:
+        from paper_2101_06769_gb300.lbmp import FLAG_AA
+        phys = dict(wl["phys"])
+        phys["flags"] = int(phys.get("flags", 0)) | FLAG_AA
+        d = Domain(D, wl["dims"], wl["periodic"], stream=stream.cuda_stream, **phys)
+        d.init(wl["case"], wl["args"], seed=wl["seed"])
+        d.step(4)
+        ms = time_steps(lambda: d.step(1), stream, n)
+        launches += 2 * n  # phi pass and step kernel
+        _, mlups = aggregate(ms * n, d.N, n, pg)
+        bpc = BYTES_PER_CELL[D]
+        gbs = bpc * d.N / (ms * 1e-3) / 1e9
+        ob = d.observables()
+        out["aa_in_place"] = {"mlups": mlups, "ms_per_step": ms, "bytes_per_cell": bpc,
+                              "overhead_bytes_per_cell": 27 * 4 + 8 + 8, "achieved_gbs": gbs, "frac": gbs / peak,
+                              "state_bytes_per_cell": 2 * 27 * 4 + 8, "two_set_state_bytes_per_cell": 4 * 27 * 4,
+                              "mass_drift_rel": ob.mass_drift_rel, "steps": n,
+                              "kernel": "phi_pass_kernel + step_aa_kernel"}
+        d.close()
     # batched form
     doms, cells, byts = [], 0, 0
     b = Batch(stream=stream.cuda_stream)

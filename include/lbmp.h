@@ -105,7 +105,25 @@ enum {
      * divergence.  FP32 storage and the full phase lattice only
      * (LBMP_ERR_UNSUPPORTED otherwise); runs the reference pair; not a batch
      * member. */
-    LBMP_FLAG_DIVU = 1u << 4
+    LBMP_FLAG_DIVU = 1u << 4,
+    /* In-place AA storage (esoteric pull, Sec. 2.2 / 2.3 streaming): one
+     * population set each for f' and g instead of two, half the state.
+     * Even steps read every population of a cell from the cell itself and
+     * write the post-collision values back to it in the opposite
+     * directions' slots; odd steps read from the neighbours' opposite slots
+     * and write to the neighbours' own slots; each cell touches only the
+     * slots it reads, so the update is race-free in place.  phi, which the
+     * two-set kernels form from the g they stage (ring cells included), is
+     * formed by a separate phase-aware pass first (8 bytes per cell more
+     * state; 116 bytes per cell more traffic per step), because a ring read
+     * would race with the owner's in-place writes.  D3Q27, FP32 storage, the
+     * full phase lattice, no LBMP_FLAG_DIVU (LBMP_ERR_UNSUPPORTED
+     * otherwise); the fused kernel only (LBMP_OPT_KERNEL 0); no autotuning
+     * (a trial launch would advance the state in place); not a batch member
+     * or a z-slab.  lbmp_download / lbmp_upload images hold the phase of the
+     * step count: upload into a handle whose step count has the same
+     * parity. */
+    LBMP_FLAG_AA = 1u << 5
 };
 
 typedef struct {

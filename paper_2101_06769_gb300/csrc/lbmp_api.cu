@@ -99,6 +99,7 @@ void fill_devparams(lbmp_handle* h)
     q.ze = h->D == 3 ? h->grid.nz : h->grid.ny;
     q.zoff = 0;
     q.nzg = q.ze;
+    q.aa = 0;  // lbmp_create sets the phase of an AA domain
     q.N = h->N;
     q.rho_l = (float)d.rho_l;
     q.drho = (float)(d.rho_h - d.rho_l);
@@ -140,6 +141,7 @@ void free_handle(lbmp_handle* h)
 {
     drop_step_graphs(h);
     for (int k = 0; k < 2; ++k) {
+        if (k == 1 && h->aa) break;  // f[1], g[1] alias the single AA set
         lbmp::dev_free(h, h->f[k], lbmp::set_bytes(h));
         lbmp::dev_free(h, h->g[k], lbmp::gset_bytes(h));
     }
@@ -209,6 +211,7 @@ cudaError_t ensure_phi(lbmp_handle* h)
 
 cudaError_t launch_step(lbmp_handle* h)
 {
+    if (h->aa) return launch_step_aa(h);
     if (h->kernel == 1 || !fused_supported(h)) return launch_step_simple(h);
     if (h->params.storage != LBMP_FP32) return h->D == 3 ? launch_step_fused16(h) : launch_step_fused2s(h);
     if (h->D == 2) return launch_step_fused2(h);
@@ -265,8 +268,10 @@ cudaGraphExec_t step_graph(lbmp_handle* h)
         for (int k = 0; k < kStepGraph && e == cudaSuccess; ++k) {
             e = lbmp::launch_step(h);
             h->parity ^= 1;
+            lbmp::sync_aa(h);
         }
         h->parity = p0;
+        lbmp::sync_aa(h);
         const cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
         if (e == cudaSuccess) e = e2;
     }
@@ -317,7 +322,10 @@ int lbmp_create_ex(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_param
     // neighbouring cells; the D2Q9 one loads 2-byte codes but keeps the same rule
     if (params->storage != LBMP_FP32 && (grid->nx & 1))
         return fail(LBMP_ERR_INVALID_ARG, "16-bit storage needs an even nx");
-    if (params->flags & ~31u) return fail(LBMP_ERR_INVALID_ARG, "unknown flag bits");
+    if (params->flags & ~63u) return fail(LBMP_ERR_INVALID_ARG, "unknown flag bits");
+    if ((params->flags & LBMP_FLAG_AA) &&
+        (D != 3 || params->storage != LBMP_FP32 || (params->flags & (LBMP_FLAG_PHASE_REDUCED | LBMP_FLAG_DIVU))))
+        return fail(LBMP_ERR_UNSUPPORTED, "in-place AA storage needs D3Q27, FP32, the full phase lattice, no LBMP_FLAG_DIVU");
     if ((params->flags & LBMP_FLAG_DIVU) &&
         (params->storage != LBMP_FP32 || (params->flags & LBMP_FLAG_PHASE_REDUCED)))
         return fail(LBMP_ERR_UNSUPPORTED, "the divergence term needs FP32 storage and the full phase lattice");
@@ -332,6 +340,7 @@ int lbmp_create_ex(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_param
     h->Q = (D == 3) ? 27 : 9;
     h->reduced = (params->flags & LBMP_FLAG_PHASE_REDUCED) != 0;
     h->divu = (params->flags & LBMP_FLAG_DIVU) != 0;
+    h->aa = (params->flags & LBMP_FLAG_AA) != 0;
     h->Qg = h->reduced ? 2 * D + 1 : h->Q;
     h->params = *params;
     h->N = N;
@@ -354,10 +363,16 @@ int lbmp_create_ex(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_param
         return cuda_fail(e, "cudaGetDevice");
     }
     const size_t pop = lbmp::set_bytes(h), gpop = lbmp::gset_bytes(h);
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < (h->aa ? 1 : 2); ++k) {
         e = lbmp::dev_alloc(h, (void**)&h->f[k], pop);
         if (e == cudaSuccess) e = lbmp::dev_alloc(h, (void**)&h->g[k], gpop);
         if (e != cudaSuccess) break;
+    }
+    if (h->aa) {  // one set, updated in place; phi from a pass of its own
+        h->f[1] = h->f[0];
+        h->g[1] = h->g[0];
+        if (e == cudaSuccess) e = lbmp::ensure_phi(h);
+        lbmp::sync_aa(h);
     }
     if (e == cudaSuccess && h->reduced) e = lbmp::dev_alloc(h, (void**)&h->phiu, lbmp::phiu_bytes(h));
     for (int k = 0; k < 2 && e == cudaSuccess && h->divu; ++k)
@@ -406,7 +421,8 @@ int lbmp_set_option(lbmp_handle* h, int option, long value)
     switch (option) {
     case LBMP_OPT_KERNEL:
         if (value < 0 || value > 2) return fail(LBMP_ERR_INVALID_ARG, "kernel must be 0, 1 or 2");
-        if (h->slab && value != 0) return fail(LBMP_ERR_UNSUPPORTED, "z-slabs run the fused kernel only");
+        if ((h->slab || h->aa) && value != 0)
+            return fail(LBMP_ERR_UNSUPPORTED, "z-slabs and in-place AA storage run the fused kernel only");
         if (value == 1) {  // the reference pair keeps phi in an array of its own
             const cudaError_t e = lbmp::ensure_phi(h);
             if (e != cudaSuccess) {
@@ -435,6 +451,7 @@ int lbmp_set_option(lbmp_handle* h, int option, long value)
         return LBMP_OK;
     case LBMP_OPT_TEST_POISON: {
         if (value != 1) return fail(LBMP_ERR_INVALID_ARG, "test poison must be 1");
+        if (h->aa) return fail(LBMP_ERR_UNSUPPORTED, "in-place AA storage has no second population set to poison");
         const int d = 1 - h->parity;
         LBMP_CUDA(cudaMemsetAsync(h->f[d], 0xFF, lbmp::set_bytes(h), h->stream), "poison");
         LBMP_CUDA(cudaMemsetAsync(h->g[d], 0xFF, lbmp::gset_bytes(h), h->stream), "poison");
@@ -463,6 +480,7 @@ int lbmp_init(lbmp_handle* h, int case_id, const double* case_args, int nargs, u
     }
     if (case_id == LBMP_CASE_DROP_STATIC && !(a[0] > 0.0)) return fail(LBMP_ERR_INVALID_ARG, "radius must be > 0");
     h->parity = 0;
+    lbmp::sync_aa(h);
     h->step = 0;
     for (int k = 0; k < 3; ++k) h->probe[k] = (k < h->D) ? ((&h->grid.nx)[k] / 2) : 0;
     if (case_id == LBMP_CASE_DROP_SHEET) {
@@ -501,6 +519,7 @@ int lbmp_step(lbmp_handle* h, long n)
         cudaError_t e = lbmp::launch_step(h);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel");
         h->parity ^= 1;
+        lbmp::sync_aa(h);
         h->step += 1;
         h->graph_warm = true;
         ++k;

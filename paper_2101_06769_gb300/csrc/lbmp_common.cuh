@@ -114,6 +114,12 @@ struct DevParams {
     int wall_lo, wall_hi;
     int zb, ze;
     int zoff, nzg;
+    // In-place AA storage (LBMP_FLAG_AA: one population set each for f' and
+    // g): 0 = two sets (the stored value of direction a at cell i is the
+    // post-collision value of the upstream cell); 1 = AA, natural phase (the
+    // streamed value of a at i is A[a][i]); 2 = AA, swapped phase (it is
+    // A[opp(a)][i - c_a], or A[a][i] across a wall)
+    int aa;
     long long N;            // cells
     float rho_l, drho, rho_bar;
     float nu_h, nu_l, eta_h, eta_l;
@@ -171,16 +177,20 @@ __device__ __forceinline__ long long pull_src(const DevParams& p, int a, int x, 
     xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
     dir = a;
     if (D == 3) {
+        if (p.aa == 1) return self;  // AA, natural phase: own cell, own direction
         int ys = y - cy;
         ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
         int zs = z - cz;
         if (zs < 0 || zs >= p.nz) {
             if (zs < 0 ? p.wall_lo : p.wall_hi) {
-                dir = Lat<D>::opp(a);
+                // across a wall: the cell's own opposite value (two sets), or
+                // its own value of a (AA swapped phase)
+                dir = p.aa ? a : Lat<D>::opp(a);
                 return self;
             }
             zs = zs < 0 ? zs + p.nz : zs - p.nz;
         }
+        if (p.aa) dir = Lat<D>::opp(a);  // AA swapped phase: the upstream cell's opposite slot
         return ((long long)zs * p.ny + ys) * p.nx + xs;
     } else {
         int ys = y - cy;

@@ -26,6 +26,9 @@ struct lbmp_handle {
     // slab_ghost[0] / [1] ghost planes below / above; slab = false otherwise
     bool slab;
     int slab_z0, slab_z1, slab_ghost[2];
+    // in-place AA storage (LBMP_FLAG_AA): f[1] == f[0], g[1] == g[0], and
+    // parity is the phase (0 natural, 1 swapped; dp.aa = 1 + parity)
+    bool aa;
     float* phi;        // reference pair only: phi = sum g as hi [0, N) + lo [N, 2N), refreshed by the phi pass
     lbmp_allocator alloc;  // caller's device allocator (alloc == null: cudaMalloc / cudaFree)
     float* phiu;       // reduced phase lattice: phi u of the previous step, [k < D][cell]; else null
@@ -162,6 +165,12 @@ inline const Batch3Ops& batch3_ops(int tile)
     return tile == 1 ? batch3_ops_16x8 : (tile == 2 ? batch3_ops_8x16 : batch3_ops_32x4);
 }
 cudaError_t launch_step_fused2(lbmp_handle* h);
+cudaError_t launch_step_aa(lbmp_handle* h);  // in-place AA storage: phi pass, then the AA step of the phase
+// keep dp.aa in step with the phase after every change of parity
+inline void sync_aa(lbmp_handle* h)
+{
+    if (h->aa) h->dp.aa = 1 + h->parity;
+}
 cudaError_t launch_step_fused16(lbmp_handle* h);  // shifted 16-bit storage, D3Q27
 bool bulk_supported(const lbmp_handle* h);         // FP32 D3Q27 with nx % 4 == 0
 cudaError_t launch_step_fused_bulk(lbmp_handle* h);

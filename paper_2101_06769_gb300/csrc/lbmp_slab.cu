@@ -83,7 +83,7 @@ LBMP_API int lbmp_create_slab(const lbmp_grid* grid, int z_begin, int z_end, lbm
     if (!grid || !params || !out) return slab_fail(LBMP_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
     if (lattice != LBMP_D3Q27) return slab_fail(LBMP_ERR_UNSUPPORTED, "z-slabs are D3Q27 domains");
-    if (params->storage != LBMP_FP32 || (params->flags & (LBMP_FLAG_PHASE_REDUCED | LBMP_FLAG_DIVU)))
+    if (params->storage != LBMP_FP32 || (params->flags & (LBMP_FLAG_PHASE_REDUCED | LBMP_FLAG_DIVU | LBMP_FLAG_AA)))
         return slab_fail(LBMP_ERR_UNSUPPORTED, "z-slabs need FP32 storage, the full phase lattice and no LBMP_FLAG_DIVU");
     if (!(0 <= z_begin && z_begin < z_end && z_end <= grid->nz))
         return slab_fail(LBMP_ERR_INVALID_ARG, "slab planes must satisfy 0 <= z_begin < z_end <= nz");

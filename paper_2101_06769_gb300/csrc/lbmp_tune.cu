@@ -44,7 +44,9 @@ LBMP_API int lbmp_autotune(lbmp_handle* h, int reps, lbmp_tune_entry* table, int
     if (!h) return lbmp::set_error(LBMP_ERR_INVALID_ARG, "null handle");
     if (reps < 1) return lbmp::set_error(LBMP_ERR_INVALID_ARG, "reps must be >= 1");
     if (max_entries < 0) return lbmp::set_error(LBMP_ERR_INVALID_ARG, "max_entries must be >= 0");
-    if (h->kernel == 1 || !lbmp::fused_supported(h)) return LBMP_OK;
+    // nothing to tune for the reference pair; an in-place AA step cannot be
+    // run as a trial (it would advance the state)
+    if (h->kernel == 1 || !lbmp::fused_supported(h) || h->aa) return LBMP_OK;
     const int nmarch = h->D == 3 ? h->grid.nz : h->grid.ny;
     int chunks[10], nc = 0;
     chunks[nc++] = 0;

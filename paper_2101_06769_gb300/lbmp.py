@@ -17,7 +17,7 @@ D2Q9, D3Q27 = 0, 1
 FP32, FP16_SHIFTED, BF16_SHIFTED = 0, 1, 2
 CASE = {"rt": 0, "drop_static": 1, "flat": 2, "poiseuille": 3, "drop_sheet": 4, "shear_wave": 5,
         "uniform": 6}
-FLAG_WE_LIGHT, FLAG_DYNAMIC_VISC, FLAG_UNIFORM_FORCE, FLAG_PHASE_REDUCED, FLAG_DIVU = 1, 2, 4, 8, 16
+FLAG_WE_LIGHT, FLAG_DYNAMIC_VISC, FLAG_UNIFORM_FORCE, FLAG_PHASE_REDUCED, FLAG_DIVU, FLAG_AA = 1, 2, 4, 8, 16, 32
 OPT_KERNEL, OPT_CHUNK, OPT_CTAS_PER_SM, OPT_WAIT_LIMIT_NS, OPT_TEST_STALL, OPT_TILE = 0, 1, 2, 3, 4, 5
 OPT_TEST_POISON = 6
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5: "UNSTABLE",

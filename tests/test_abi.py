@@ -113,15 +113,19 @@ def test_invalid_arguments_rejected_without_device_work(lib):
 def test_size_flag_and_form_limits_rejected_without_device_work(lib):
     """More limits checked before any CUDA call: more than 2^31-1 cells, 16-bit
     storage with an odd nx, unknown flag bits (INVALID_ARG); the reduced phase
-    lattice or the divergence term with 16-bit storage, and the two flags
-    together (UNSUPPORTED)."""
+    lattice or the divergence term with 16-bit storage, the two flags
+    together, and in-place AA storage outside D3Q27 FP32 with the full phase
+    lattice (UNSUPPORTED)."""
     h = C.c_void_p()
     per = (C.c_int * 3)(1, 1, 0)
     ok = dict(rho_ratio=3.0, nu_h=0.1)
     cases = [
         (lbmp.Grid(2048, 2048, 1024, per), lbmp.make_params(**ok), -1),
         (lbmp.Grid(37, 8, 8, per), lbmp.make_params(storage=lbmp.FP16_SHIFTED, **ok), -1),
-        (lbmp.Grid(8, 8, 8, per), lbmp.make_params(flags=1 << 5, **ok), -1),
+        (lbmp.Grid(8, 8, 8, per), lbmp.make_params(flags=1 << 6, **ok), -1),
+        (lbmp.Grid(8, 8, 8, per), lbmp.make_params(flags=lbmp.FLAG_AA, storage=lbmp.FP16_SHIFTED, **ok), -6),
+        (lbmp.Grid(8, 8, 8, per), lbmp.make_params(flags=lbmp.FLAG_AA | lbmp.FLAG_PHASE_REDUCED, **ok), -6),
+        (lbmp.Grid(8, 8, 8, per), lbmp.make_params(flags=lbmp.FLAG_AA | lbmp.FLAG_DIVU, **ok), -6),
         (lbmp.Grid(8, 8, 8, per), lbmp.make_params(flags=lbmp.FLAG_PHASE_REDUCED, storage=lbmp.FP16_SHIFTED, **ok), -6),
         (lbmp.Grid(8, 8, 8, per), lbmp.make_params(flags=lbmp.FLAG_DIVU, storage=lbmp.BF16_SHIFTED, **ok), -6),
         (lbmp.Grid(8, 8, 8, per), lbmp.make_params(flags=lbmp.FLAG_DIVU | lbmp.FLAG_PHASE_REDUCED, **ok), -6),
