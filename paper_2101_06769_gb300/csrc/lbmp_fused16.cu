@@ -20,6 +20,8 @@
 //     reference planes are in place.
 //   * the ghost plane beyond a wall (mirrored phi, reading A17) is a copy of
 //     the wall plane's phi instead of a second staging of that plane.
+// the output pair loops keep their memory operations in order (lower register footprint)
+#define LBMP_OUT_ORDERED 1
 #include <stdint.h>
 
 #include "lbmp_internal.h"
@@ -33,8 +35,9 @@ using namespace tile;
 
 constexpr int C3 = 13;
 constexpr int GX = TX + 4, GY = TY + 4, GPLANE = GX * GY;  // g reference plane: tile + two rings
+// the moment differences are parked in the consumed g column: no array of their own
 constexpr size_t kSmem16 = sizeof(float2) * 3 * PLANE +
-                           sizeof(float) * ((2 + LBMP_FUSED_DHSMEM) * Q3 * NT + Q3 * NRING + 4 * GPLANE + 4 * PLANE) +
+                           sizeof(float) * (2 * Q3 * NT + Q3 * NRING + 4 * GPLANE + 4 * PLANE) +
                            sizeof(int) * (GPLANE + PLANE);
 
 struct DirPtrs16 {
@@ -246,8 +249,7 @@ __device__ __forceinline__ void fused_segment16(const DevParams& p, const DirPtr
     float* rS = gS + 2 * Q3 * NT;                // [27][NRING] ring cells
     float* RG = rS + Q3 * NRING;                 // [4][GPLANE] g references
     float* RF = RG + 4 * GPLANE;                 // [4][PLANE] f' references
-    float* dS = RF + 4 * PLANE;                  // [27][NT] dh (LBMP_FUSED_DHSMEM)
-    int* offG = (int*)(dS + LBMP_FUSED_DHSMEM * Q3 * NT);
+    int* offG = (int*)(RF + 4 * PLANE);
     int* offF = offG + GPLANE;
     const int tid = T.tid;
     Column own, ring;
@@ -311,21 +313,26 @@ __device__ __forceinline__ void fused_segment16(const DevParams& p, const DirPtr
             float grad[3], lap;
             stencil_from_nb<3>(nh, nl, grad, lap);
             CellState s;
-            float dh[27];
-            flow_collide<3>(p, nh[13], grad, lap, m, s, dh);
             const int self = P.zs[1] + own.ys[1] + own.xs[1];
-            const GFromStrided gin{gS + cur * Q3 * NT + tid, NT};
-            float off_f, off_g;
-            rest_offsets<3, St>(p, s, dh, gin, off_f, off_g);
-            const EncPtr<3, St> fo{Dp.fout, Dp.rfout, self, off_f, 0.f, code_seed(p, self, 0)};
-            const EncPtr<3, St> go{Dp.gout, Dp.rgout, self, off_g, 0.f, code_seed(p, self, 1)};
-#if LBMP_FUSED_DHSMEM
+            float* gcol = gS + cur * Q3 * NT + tid;  // this cell's decoded pre-collision g
+            const GFromStrided gin{gcol, NT};
+            // g first (it needs only the closure); its decoded column then
+            // holds the moment differences for the f' outputs.  The rest
+            // offsets of the encoders are those of rest_offsets.
+            float inv_rho, nu;
+            flow_closure<3>(p, nh[13], grad, lap, m, s, inv_rho, nu);
+            const float gd = gamma_dev<3>(s, C3);
+            const float kS = St::S / wint<3>(C3);
+            const EncPtr<3, St> go{Dp.gout, Dp.rgout, self, kS * phase_post<3>(p, s, C3, gin(C3), gd), 0.f,
+                                   code_seed(p, self, 1)};
+            phase_outputs<3>(p, s, gin, nh[13], nl[13], go);
+            float dh[27];
+            flow_relax<3>(m, s, inv_rho, nu, dh);
 #pragma unroll
-            for (int a = 0; a < Q3; ++a) dS[a * NT + tid] = dh[a];
-            collide_outputs<3>(p, s, DhStrided{dS + tid, NT}, m, gin, nh[13], nl[13], fo, go);
-#else
-            collide_outputs<3>(p, s, DhArray{dh}, m, gin, nh[13], nl[13], fo, go);
-#endif
+            for (int a = 0; a < Q3; ++a) gcol[a * NT] = dh[a];
+            const EncPtr<3, St> fo{Dp.fout, Dp.rfout, self, kS * flow_post<3>(s, dh, C3, gd), 0.f,
+                                   code_seed(p, self, 0)};
+            flow_outputs<3>(s, DhStrided{gcol, NT}, m, fo);
         }
         __syncthreads();
         const int t = sP;
