@@ -202,7 +202,9 @@ class SlabDomain:
         return (f[:, sl].reshape(27, -1, ny, nx), g[:, sl].reshape(27, -1, ny, nx))
 
     def observables(self):
-        """(mass, kinetic energy, max |u|, health) of the whole domain"""
+        """mass, kinetic energy, max |u| and health: of the whole domain when
+        the slab has a transport (reduced across ranks), else of this slab's
+        own planes"""
         o = self.backend.observables()
         vals = np.array([o.mass, o.kinetic_energy, o.max_u, float(o.health)])
         if self.transport is not None:
