@@ -5,8 +5,10 @@
 // first, the moment differences parked in the consumed g column, ring phi
 // from register loads, pair loops kept in order (measured on the
 // 128x128x512 RT workload: 0.852 ms per step against 0.894 ms for three
-// CTAs per SM with a separate moment-difference array)
+// CTAs per SM with a separate moment-difference array); column and plane
+// offsets in bytes (0.827 against 0.860 ms with element indices)
 #define LBMP_FUSED_MINB 4
+#define LBMP_FUSED_BYTEOFF 1
 #define LBMP_FUSED_SPLIT 1
 #define LBMP_FUSED_RINGREG 1
 #define LBMP_OUT_ORDERED 1

@@ -22,6 +22,7 @@
 //     the wall plane's phi instead of a second staging of that plane.
 // the output pair loops keep their memory operations in order (lower register footprint)
 #define LBMP_OUT_ORDERED 1
+#define LBMP_TILE_NS tile16
 #include <stdint.h>
 
 #include "lbmp_internal.h"
@@ -31,7 +32,7 @@ namespace lbmp {
 
 namespace {
 
-using namespace tile;
+using namespace LBMP_TILE_NS;
 
 constexpr int C3 = 13;
 constexpr int GX = TX + 4, GY = TY + 4, GPLANE = GX * GY;  // g reference plane: tile + two rings

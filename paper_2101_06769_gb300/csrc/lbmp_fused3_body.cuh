@@ -133,7 +133,7 @@ __device__ __forceinline__ void stage_issue(const DevParams& p, const DirPtrs& D
     Plane P;
     set_plane(P, p, plane_src(p, zz));
     if constexpr (PR) {
-        const int self = P.zs[1] + own.ys[1] + own.xs[1];
+        const int self = elem_index(P.zs[1] + own.ys[1] + own.xs[1]);
 #pragma unroll
         for (int k = 0; k < 3; ++k) cp_async4(ubuf + k * NT + tid, phiu + k * p.N + self);
     }
@@ -238,18 +238,18 @@ __device__ __forceinline__ void fused_segment(const DevParams& p, const DirPtrs&
                 },
                 centre, grad, lap);
             CellState s;
-            const int self = P.zs[1] + own.ys[1] + own.xs[1];
+            const cell_off self = P.zs[1] + own.ys[1] + own.xs[1];
             float* gcol = gS + cur * QG * NT + tid;  // this cell's staged pre-collision g
             if constexpr (kSplit) {
                 // g first; its staged column then holds the moment differences
                 float inv_rho, nu;
                 flow_closure<3>(p, centre.x, grad, lap, m, s, inv_rho, nu);
-                phase_outputs<3>(p, s, GFromStrided{gcol, NT}, centre.x, centre.y, PtrOut{Dp.gout, self});
+                phase_outputs<3>(p, s, GFromStrided{gcol, NT}, centre.x, centre.y, CellOut{Dp.gout, self});
                 float dh[27];
                 flow_relax<3>(m, s, inv_rho, nu, dh);
 #pragma unroll
                 for (int a = 0; a < Q3; ++a) gcol[a * NT] = dh[a];
-                flow_outputs<3>(s, DhStrided{gcol, NT}, m, PtrOut{Dp.fout, self});
+                flow_outputs<3>(s, DhStrided{gcol, NT}, m, CellOut{Dp.fout, self});
             } else {
                 float dh[27];
                 flow_collide<3>(p, centre.x, grad, lap, m, s, dh);
@@ -257,12 +257,12 @@ __device__ __forceinline__ void fused_segment(const DevParams& p, const DirPtrs&
 #pragma unroll
                     for (int a = 0; a < Q3; ++a) dS[a * NT + tid] = dh[a];
                     collide_outputs<3, PR>(p, s, DhStrided{dS + tid, NT}, m, GFromStrided{gcol, NT}, centre.x,
-                                           centre.y, PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self},
-                                           PhiUStaged<3>{p, phiu, self, uS + cur * 3 * NT + tid, NT});
+                                           centre.y, CellOut{Dp.fout, self}, CellOut{Dp.gout, self},
+                                           PhiUStaged<3>{p, phiu, elem_index(self), uS + cur * 3 * NT + tid, NT});
                 } else {
                     collide_outputs<3, PR>(p, s, DhArray{dh}, m, GFromStrided{gcol, NT}, centre.x, centre.y,
-                                           PtrOut{Dp.fout, self}, PtrOut{Dp.gout, self},
-                                           PhiUStaged<3>{p, phiu, self, uS + cur * 3 * NT + tid, NT});
+                                           CellOut{Dp.fout, self}, CellOut{Dp.gout, self},
+                                           PhiUStaged<3>{p, phiu, elem_index(self), uS + cur * 3 * NT + tid, NT});
                 }
             }
         }

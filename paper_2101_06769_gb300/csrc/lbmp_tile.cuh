@@ -2,6 +2,8 @@
 // step kernels (FP32 and shifted 16-bit storage forms).
 #pragma once
 
+#include <type_traits>
+
 #include "lbmp_internal.h"
 
 // The tile shape is fixed per translation unit (LBMP_FUSED_TX / _TY); a unit
@@ -49,6 +51,20 @@ namespace LBMP_TILE_NS {
 #ifndef LBMP_FUSED_RINGREG
 #define LBMP_FUSED_RINGREG 0
 #endif
+// 1: the column and plane offsets are unsigned byte offsets of 4-byte
+// populations, so a pulled value's address is its array base plus one
+// 32-bit sum (every array below 4 GiB: fewer than 2^30 cells); 0: signed
+// element indices, scaled to a 64-bit offset at every access
+#ifndef LBMP_FUSED_BYTEOFF
+#define LBMP_FUSED_BYTEOFF 0
+#endif
+#if LBMP_FUSED_BYTEOFF
+using cell_off = unsigned;
+constexpr unsigned kOffUnit = 4;
+#else
+using cell_off = int;
+constexpr int kOffUnit = 1;
+#endif
 constexpr int TX = LBMP_FUSED_TX, TY = LBMP_FUSED_TY, NT = TX * TY;
 constexpr int RX = TX + 2, RY = TY + 2;
 constexpr int PLANE = RY * RX;
@@ -82,25 +98,28 @@ __device__ __forceinline__ int pmod(int v, int n)
 // A column (x, y) and its upstream neighbours: xs[c+1] = x - c and
 // ys[c+1] = (y - c) nx, wrapped periodically.
 struct Column {
-    int xs[3], ys[3];
+    cell_off xs[3], ys[3];
 };
 
 __device__ __forceinline__ void set_column(Column& C, const DevParams& p, int x, int y)
 {
-    C.xs[0] = x + 1 == p.nx ? 0 : x + 1;
-    C.xs[1] = x;
-    C.xs[2] = x == 0 ? p.nx - 1 : x - 1;
-    C.ys[0] = (y + 1 == p.ny ? 0 : y + 1) * p.nx;
-    C.ys[1] = y * p.nx;
-    C.ys[2] = (y == 0 ? p.ny - 1 : y - 1) * p.nx;
+    C.xs[0] = (cell_off)(x + 1 == p.nx ? 0 : x + 1) * kOffUnit;
+    C.xs[1] = (cell_off)x * kOffUnit;
+    C.xs[2] = (cell_off)(x == 0 ? p.nx - 1 : x - 1) * kOffUnit;
+    C.ys[0] = (cell_off)((y + 1 == p.ny ? 0 : y + 1) * p.nx) * kOffUnit;
+    C.ys[1] = (cell_off)(y * p.nx) * kOffUnit;
+    C.ys[2] = (cell_off)((y == 0 ? p.ny - 1 : y - 1) * p.nx) * kOffUnit;
 }
+
+// element index of a cell offset
+__device__ __forceinline__ int elem_index(cell_off o) { return (int)(o / kOffUnit); }
 
 // A plane z and its upstream planes zs[c+1] = (z - c) nx ny; lo/hi flag the
 // bottom/top plane of a walled domain, where the population arriving across
 // the wall is the opposite population of the cell itself (half-way
 // bounce-back).
 struct Plane {
-    int zs[3];
+    cell_off zs[3];
     bool lo, hi;
 };
 
@@ -109,9 +128,22 @@ __device__ __forceinline__ void set_plane(Plane& P, const DevParams& p, int z)
     const int nxy = p.nx * p.ny;
     P.lo = p.wall_lo && z == 0;
     P.hi = p.wall_hi && z == p.nz - 1;
-    P.zs[0] = (z + 1 == p.nz ? 0 : z + 1) * nxy;
-    P.zs[1] = z * nxy;
-    P.zs[2] = (z == 0 ? p.nz - 1 : z - 1) * nxy;
+    P.zs[0] = (cell_off)((z + 1 == p.nz ? 0 : z + 1) * nxy) * kOffUnit;
+    P.zs[1] = (cell_off)(z * nxy) * kOffUnit;
+    P.zs[2] = (cell_off)((z == 0 ? p.nz - 1 : z - 1) * nxy) * kOffUnit;
+}
+
+// element of an array at cell offset o
+template <class E>
+__device__ __forceinline__ E* at_cell(E* base, cell_off o)
+{
+    if constexpr (LBMP_FUSED_BYTEOFF != 0) {
+        static_assert(sizeof(E) == 4, "byte offsets of 4-byte populations");
+        using B = typename std::conditional<std::is_const<E>::value, const char, char>::type;
+        return reinterpret_cast<E*>(reinterpret_cast<B*>(base) + o);
+    } else {
+        return base + o;
+    }
 }
 
 // pointer to the post-streaming population a of the cell (column C, plane P);
@@ -121,8 +153,8 @@ __device__ __forceinline__ const E* pulled(const E* const* base, const Column& C
 {
     constexpr int cx = Lat<3>::cx(a), cy = Lat<3>::cy(a), cz = Lat<3>::cz(a);
     if (Walls && ((cz == 1 && P.lo) || (cz == -1 && P.hi)))
-        return base[Lat<3>::opp(a)] + (P.zs[1] + C.ys[1] + C.xs[1]);
-    return base[a] + (P.zs[cz + 1] + C.ys[cy + 1] + C.xs[cx + 1]);
+        return at_cell(base[Lat<3>::opp(a)], P.zs[1] + C.ys[1] + C.xs[1]);
+    return at_cell(base[a], P.zs[cz + 1] + C.ys[cy + 1] + C.xs[cx + 1]);
 }
 
 // compile-time loop over the directions (keeps base[a] a constant-bank operand)
@@ -150,8 +182,8 @@ __device__ __forceinline__ const E* pulled_g(const E* const* base, const Column&
 {
     constexpr int a = PhaseLat<3, PR>::full(r);
     constexpr int cx = Lat<3>::cx(a), cy = Lat<3>::cy(a), cz = Lat<3>::cz(a);
-    if (Walls && ((cz == 1 && P.lo) || (cz == -1 && P.hi))) return base[QG - 1 - r] + (P.zs[1] + C.ys[1] + C.xs[1]);
-    return base[r] + (P.zs[cz + 1] + C.ys[cy + 1] + C.xs[cx + 1]);
+    if (Walls && ((cz == 1 && P.lo) || (cz == -1 && P.hi))) return at_cell(base[QG - 1 - r], P.zs[1] + C.ys[1] + C.xs[1]);
+    return at_cell(base[r], P.zs[cz + 1] + C.ys[cy + 1] + C.xs[cx + 1]);
 }
 
 // post-streaming values of the 27 directions of one cell into registers
@@ -180,6 +212,14 @@ struct PullLoadG {
     {
         v[r] = __ldg(pulled_g<Walls, r>(base, C, P));
     }
+};
+
+// stores of the outputs of one cell (per-direction array bases, one offset)
+struct CellOut {
+    static constexpr bool kTotal = false;
+    float* const* base;
+    cell_off self;
+    __device__ __forceinline__ void operator()(int a, float v) const { *at_cell(base[a], self) = v; }
 };
 
 // plane whose phi stands for plane zz: periodic wrap, or the mirrored ghost

@@ -114,8 +114,9 @@ def test_size_flag_and_form_limits_rejected_without_device_work(lib):
     """More limits checked before any CUDA call: more than 2^31-1 cells, 16-bit
     storage with an odd nx, unknown flag bits (INVALID_ARG); the reduced phase
     lattice or the divergence term with 16-bit storage, the two flags
-    together, and in-place AA storage outside D3Q27 FP32 with the full phase
-    lattice (UNSUPPORTED)."""
+    together, in-place AA storage outside D3Q27 FP32 with the full phase
+    lattice, and an FP32 D3Q27 two-set domain of 2^30 cells, whose arrays
+    its kernels could not address by 32-bit byte offsets (UNSUPPORTED)."""
     h = C.c_void_p()
     per = (C.c_int * 3)(1, 1, 0)
     ok = dict(rho_ratio=3.0, nu_h=0.1)
@@ -129,6 +130,8 @@ def test_size_flag_and_form_limits_rejected_without_device_work(lib):
         (lbmp.Grid(8, 8, 8, per), lbmp.make_params(flags=lbmp.FLAG_PHASE_REDUCED, storage=lbmp.FP16_SHIFTED, **ok), -6),
         (lbmp.Grid(8, 8, 8, per), lbmp.make_params(flags=lbmp.FLAG_DIVU, storage=lbmp.BF16_SHIFTED, **ok), -6),
         (lbmp.Grid(8, 8, 8, per), lbmp.make_params(flags=lbmp.FLAG_DIVU | lbmp.FLAG_PHASE_REDUCED, **ok), -6),
+        (lbmp.Grid(1024, 1024, 1024, per), lbmp.make_params(**ok), -6),
+        (lbmp.Grid(1024, 1024, 1024, per), lbmp.make_params(flags=lbmp.FLAG_PHASE_REDUCED, **ok), -6),
     ]
     for g, prm, want in cases:
         rc = lib.lbmp_create(C.byref(g), lbmp.D3Q27, C.byref(prm), None, C.byref(h))
