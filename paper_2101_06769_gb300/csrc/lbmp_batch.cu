@@ -6,7 +6,11 @@
 // epilogue flips the parities and counts the steps down.  Nothing a step
 // needs comes from the host, so the kernels of a run of steps are captured
 // once in a CUDA graph and the graph is replayed until the membership (or the
-// set of members with steps left) changes.  Members are grouped by kind --
+// set of members with steps left) changes.  The FP32 D3Q27 kinds run the
+// member-grid form of their kernel: the members are kernel parameters with
+// the population sets of the step's parity, so the graphs are captured for
+// both phases (even or odd number of steps since the capture) and the batch
+// replays the one of its current phase.  Members are grouped by kind --
 // FP32, FP16 and BF16 (shifted storage) D3Q27, FP32 D3Q27 with the reduced
 // phase lattice, then FP32, FP16 and BF16 D2Q9 and FP32 D2Q9 with the
 // reduced phase lattice --
@@ -71,7 +75,8 @@ struct lbmp_batch {
     std::vector<lbmp::BatchDomain> h_table;
     int dom0[kKinds], ndom[kKinds], nitems[kKinds];  // table segment and work items per kind
     bool dirty;
-    cudaGraphExec_t g_long, g_one;
+    int phase;  // steps taken since the graphs were captured, mod 2
+    cudaGraphExec_t g_long[2], g_one[2];
 };
 
 namespace {
@@ -84,9 +89,11 @@ size_t state_bytes(const lbmp_handle* h)
 
 void drop_graphs(lbmp_batch* b)
 {
-    if (b->g_long) cudaGraphExecDestroy(b->g_long);
-    if (b->g_one) cudaGraphExecDestroy(b->g_one);
-    b->g_long = b->g_one = nullptr;
+    for (int k = 0; k < 2; ++k) {
+        if (b->g_long[k]) cudaGraphExecDestroy(b->g_long[k]);
+        if (b->g_one[k]) cudaGraphExecDestroy(b->g_one[k]);
+        b->g_long[k] = b->g_one[k] = nullptr;
+    }
 }
 
 int total_dom(const lbmp_batch* b)
@@ -106,9 +113,25 @@ const lbmp::Batch3Ops& ops3_of(const lbmp_batch* b, int kind)
     return lbmp::batch3_ops(b->tile);
 }
 
+// the kernels of one kind of D3Q27 members: the member-grid form in groups
+// of as many members as its parameters hold, else the persistent form
+cudaError_t launch3(lbmp_batch* b, int kind, int flip, cudaStream_t stream)
+{
+    const lbmp::Batch3Ops& ops = ops3_of(b, kind);
+    const int d0 = b->dom0[kind], n = b->ndom[kind];
+    if (!ops.launch_grid) return ops.launch(b->d_table + d0, n, b->nitems[kind], b->device, stream);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < n && e == cudaSuccess; k += ops.grid_members) {
+        const int m = n - k < ops.grid_members ? n - k : ops.grid_members;
+        e = ops.launch_grid(b->h_table.data() + d0 + k, b->d_table + d0 + k, m, flip, b->device, stream);
+    }
+    return e;
+}
+
 // the step kernels of one step (no epilogue): D3Q27 kinds on the batch
-// stream, D2Q9 members on the side stream when both are present
-cudaError_t step_kernels(lbmp_batch* b)
+// stream, D2Q9 members on the side stream when both are present; flip: the
+// members' parities differ from the host table's by this step's phase
+cudaError_t step_kernels(lbmp_batch* b, int flip)
 {
     cudaError_t e = cudaSuccess;
     bool any3 = false;
@@ -120,8 +143,7 @@ cudaError_t step_kernels(lbmp_batch* b)
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
     }
     for (int k = kF32x3; k <= kLast3 && e == cudaSuccess; ++k)
-        if (b->ndom[k])
-            e = ops3_of(b, k).launch(b->d_table + b->dom0[k], b->ndom[k], b->nitems[k], b->device, b->stream);
+        if (b->ndom[k]) e = launch3(b, k, flip, b->stream);
     if (e == cudaSuccess && b->ndom[kF32x2])
         e = lbmp::launch_batch2(b->d_table + b->dom0[kF32x2], b->ndom[kF32x2], b->nitems[kF32x2], b->device,
                                 fork ? b->side : b->stream, false);
@@ -139,13 +161,13 @@ cudaError_t step_kernels(lbmp_batch* b)
     return e;
 }
 
-cudaError_t capture(lbmp_batch* b, int steps, cudaGraphExec_t* out)
+cudaError_t capture(lbmp_batch* b, int steps, int phase, cudaGraphExec_t* out)
 {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     for (int k = 0; k < steps && e == cudaSuccess; ++k) {
-        e = step_kernels(b);
+        e = step_kernels(b, (phase + k) & 1);
         if (e == cudaSuccess) e = lbmp::launch_batch_epilogue(b->d_table, total_dom(b), b->stream);
     }
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
@@ -207,9 +229,12 @@ cudaError_t rebuild(lbmp_batch* b, bool graphs = true)
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(b->d_table, b->h_table.data(), sizeof(lbmp::BatchDomain) * ndom,
                                 cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess && graphs) e = capture(b, kGraphSteps, &b->g_long);
-        if (e == cudaSuccess && graphs) e = capture(b, 1, &b->g_one);
+        for (int ph = 0; ph < 2 && e == cudaSuccess && graphs; ++ph) {
+            e = capture(b, kGraphSteps, ph, &b->g_long[ph]);
+            if (e == cudaSuccess) e = capture(b, 1, ph, &b->g_one[ph]);
+        }
     }
+    b->phase = 0;  // the host table holds the members' current parities
     if (e == cudaSuccess) b->dirty = !graphs;
     return e;
 }
@@ -243,7 +268,8 @@ LBMP_API int lbmp_batch_create(size_t hbm_budget, void* cuda_stream, lbmp_batch*
     b->d_table = nullptr;
     for (int k = 0; k < kKinds; ++k) b->dom0[k] = b->ndom[k] = b->nitems[k] = 0;
     b->dirty = true;
-    b->g_long = b->g_one = nullptr;
+    b->phase = 0;
+    b->g_long[0] = b->g_long[1] = b->g_one[0] = b->g_one[1] = nullptr;
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess && !b->stream) {
         e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
@@ -332,8 +358,13 @@ LBMP_API int lbmp_batch_step(lbmp_batch* b, long n, int* n_finished)
     long need = 0;
     for (const Member& m : b->members) need = m.left > need ? m.left : need;
     if (n > need) n = need;
-    for (long k = 0; k + kGraphSteps <= n && e == cudaSuccess; k += kGraphSteps) e = cudaGraphLaunch(b->g_long, b->stream);
-    for (long k = 0; k < n % kGraphSteps && e == cudaSuccess; ++k) e = cudaGraphLaunch(b->g_one, b->stream);
+    // a long graph takes an even number of steps: the phase stays
+    for (long k = 0; k + kGraphSteps <= n && e == cudaSuccess; k += kGraphSteps)
+        e = cudaGraphLaunch(b->g_long[b->phase], b->stream);
+    for (long k = 0; k < n % kGraphSteps && e == cudaSuccess; ++k) {
+        e = cudaGraphLaunch(b->g_one[b->phase], b->stream);
+        b->phase ^= 1;
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->h_table.data(), b->d_table, sizeof(lbmp::BatchDomain) * ndom, cudaMemcpyDeviceToHost,
                             b->stream);
@@ -383,9 +414,9 @@ LBMP_API int lbmp_batch_autotune(lbmp_batch* b, int reps, lbmp_tune_entry* table
             b->chunk = chunks[i];
             e = rebuild(b, false);  // table only; trial launches have no epilogue
             if (e != cudaSuccess || total_dom(b) == 0) break;
-            e = step_kernels(b);  // warm-up
+            e = step_kernels(b, 0);  // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = step_kernels(b);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = step_kernels(b, 0);
             if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;

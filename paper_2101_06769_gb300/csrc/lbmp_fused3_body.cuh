@@ -36,6 +36,8 @@
 // the stored previous phi u is read and replaced per cell).
 #pragma once
 
+#include <string.h>
+
 #include "lbmp_internal.h"
 #include "lbmp_tile.cuh"
 
@@ -287,65 +289,40 @@ __global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_fused3_kernel(DevPar
     }
 }
 
-// Batch form: the work items of every member (same order as above within a
-// member, members concatenated) are split over one persistent grid.  A CTA
-// stages the parameters and the 108 direction bases of its current member in
-// shared memory; members whose steps have run out are skipped.
-__global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_batch3_kernel(const BatchDomain* __restrict__ table,
-                                                                          int ndom, int nitems)
+// Batch form: the members are kernel parameters, one member per blockIdx.y,
+// so a member's parameters and direction bases are read from the constant
+// bank at an index common to the whole CTA, as in the single-domain kernel (a
+// persistent kernel that stages the current member's parameters and bases in
+// shared memory reads them from there at every use, and measured 8 % slower).  gridDim.x covers the largest member's work items; a smaller member's
+// spare CTAs return at once.  The parity of each member is fixed in the
+// parameters: a captured graph holds one launch per step with the parities of
+// that step.
+struct GridMember {
+    DevParams p;
+    DirPtrs D;
+    float* phiu;
+    const int* steps_left;  // the member's entry of the device table
+    int tiles_x, tiles_y, chunk, items;
+};
+constexpr int kGridMembers = (32000 - 16) / (int)sizeof(GridMember);
+struct BatchGrid {
+    int n;
+    GridMember m[kGridMembers];
+};
+static_assert(sizeof(BatchGrid) <= 32764, "kernel parameter space");
+
+__global__ void __launch_bounds__(NT, LBMP_FUSED_MINB) step_batchg3_kernel(const __grid_constant__ BatchGrid G)
 {
     extern __shared__ float smem[];
-    __shared__ DevParams sp;
-    __shared__ DirPtrs sd;
-    __shared__ int s_dom, s_tx, s_ty, s_chunk, s_begin, s_active;
-    __shared__ float* s_phiu;
+    const GridMember& M = G.m[blockIdx.y];
+    if ((int)blockIdx.x >= M.items || *M.steps_left <= 0) return;  // spare CTA, or the member has finished
     const ThreadGeo T = thread_geo();
-    int cur = -1;
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-        __syncthreads();  // every thread has read the previous item's shared values
-        if (threadIdx.x == 0) {
-            int lo = 0, hi = ndom - 1;  // last member with item_begin <= item
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (table[mid].item_begin <= item)
-                    lo = mid;
-                else
-                    hi = mid - 1;
-            }
-            s_dom = lo;
-        }
-        __syncthreads();
-        const int d = s_dom;
-        if (d != cur) {
-            const BatchDomain& B = table[d];
-            if (threadIdx.x == 0) {
-                sp = B.p;
-                s_tx = B.tiles_x;
-                s_ty = B.tiles_y;
-                s_chunk = B.chunk;
-                s_begin = B.item_begin;
-                s_active = B.steps_left > 0;
-                s_phiu = B.phiu;
-            }
-            const int par = B.parity;
-            for (int k = threadIdx.x; k < 4 * Q3; k += blockDim.x) {
-                const int set = k / Q3, a = k % Q3;
-                const size_t off = (size_t)a * (size_t)B.p.N;
-                if (set == 0) sd.fin[a] = B.f[par] + off;
-                if (set == 1 && a < QG) sd.gin[a] = B.g[par] + off;
-                if (set == 2) sd.fout[a] = B.f[par ^ 1] + off;
-                if (set == 3 && a < QG) sd.gout[a] = B.g[par ^ 1] + off;
-            }
-            cur = d;
-            __syncthreads();
-        }
-        if (!s_active) continue;  // uniform
-        const int local = item - s_begin;
-        const int tiles = s_tx * s_ty;
-        const int tile = local % tiles;
-        const int z0 = sp.zb + (local / tiles) * s_chunk;
-        fused_segment(sp, sd, T, smem, (tile % s_tx) * TX, (tile / s_tx) * TY, z0, min(z0 + s_chunk, sp.ze),
-                      s_phiu);
+    const int tiles = M.tiles_x * M.tiles_y;
+    for (int item = blockIdx.x; item < M.items; item += gridDim.x) {
+        const int tile = item % tiles;
+        const int z0 = M.p.zb + (item / tiles) * M.chunk;
+        fused_segment(M.p, M.D, T, smem, (tile % M.tiles_x) * TX, (tile / M.tiles_x) * TY, z0,
+                      min(z0 + M.chunk, M.p.ze), M.phiu);
     }
 }
 
@@ -383,38 +360,62 @@ cudaError_t launch_batch_epilogue(BatchDomain* table, int ndom, cudaStream_t str
 
 namespace {
 
-int g_batch_dev = -1, g_batch_cap = 0;
+int g_batch_dev = -1;
 
-// attributes and occupancy of the batch kernel (not capturable: call before capture)
+// attributes of the batch kernel (not capturable: call before capture)
 cudaError_t prepare_batch(int device)
 {
     if (g_batch_dev != device) {
-        cudaError_t e = cudaFuncSetAttribute(step_batch3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kSmemBytes);
+        const cudaError_t e =
+            cudaFuncSetAttribute(step_batchg3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
         if (e != cudaSuccess) return e;
-        int per_sm = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_batch3_kernel, NT, kSmemBytes);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-        if (e != cudaSuccess) return e;
-        g_batch_cap = (per_sm > 0 ? per_sm : 1) * sms;
         g_batch_dev = device;
     }
     return cudaSuccess;
 }
 
-cudaError_t launch_batch(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream)
+cudaError_t launch_batch_grid(const BatchDomain* host, const BatchDomain* dev, int n, int flip, int device,
+                              cudaStream_t stream)
 {
     if (g_batch_dev != device) return cudaErrorNotReady;  // prepare first
-    if (nitems <= 0) return cudaSuccess;
-    const int grid = nitems < g_batch_cap ? nitems : g_batch_cap;
-    step_batch3_kernel<<<grid, NT, kSmemBytes, stream>>>(table, ndom, nitems);
+    if (n <= 0) return cudaSuccess;
+    if (n > kGridMembers) return cudaErrorInvalidValue;
+    BatchGrid G;
+    memset(&G, 0, sizeof G);
+    G.n = n;
+    int xmax = 0;
+    for (int k = 0; k < n; ++k) {
+        const BatchDomain& B = host[k];
+        GridMember& M = G.m[k];
+        M.p = B.p;
+        const int par = B.parity ^ flip;
+        for (int a = 0; a < Q3; ++a) {
+            const size_t off = (size_t)a * (size_t)B.p.N;
+            M.D.fin[a] = B.f[par] + off;
+            M.D.fout[a] = B.f[par ^ 1] + off;
+        }
+        for (int r = 0; r < QG; ++r) {
+            const size_t off = (size_t)r * (size_t)B.p.N;
+            M.D.gin[r] = B.g[par] + off;
+            M.D.gout[r] = B.g[par ^ 1] + off;
+        }
+        M.phiu = B.phiu;
+        M.steps_left = &dev[k].steps_left;
+        M.tiles_x = B.tiles_x;
+        M.tiles_y = B.tiles_y;
+        M.chunk = B.chunk;
+        M.items = B.items;
+        xmax = B.items > xmax ? B.items : xmax;
+    }
+    if (xmax == 0) return cudaSuccess;
+    const int gx = xmax < 65535 ? xmax : 65535;  // larger members loop over their items
+    step_batchg3_kernel<<<dim3((unsigned)gx, (unsigned)n), NT, kSmemBytes, stream>>>(G);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-const Batch3Ops LBMP_BATCH3_OPS = {TX, TY, prepare_batch, launch_batch};
+const Batch3Ops LBMP_BATCH3_OPS = {TX, TY, prepare_batch, nullptr, launch_batch_grid, kGridMembers};
 
 cudaError_t LBMP_FUSED3_LAUNCH(lbmp_handle* h)
 {

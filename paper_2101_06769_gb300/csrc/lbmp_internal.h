@@ -153,7 +153,17 @@ bool fused_supported(const lbmp_handle* h);
 struct Batch3Ops {
     int tile_x, tile_y;
     cudaError_t (*prepare)(int device);  // attributes and occupancy (not capturable)
+    // persistent form (null where a kind has the member-grid form): the
+    // members' work items walked by one grid, members read from the device table
     cudaError_t (*launch)(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream);
+    // member-grid form (null where a kind has none): members [0, n) of the
+    // host table `host` passed as kernel parameters, each with its population
+    // sets for the parity host[k].parity ^ flip; blockIdx.y selects the member,
+    // whose steps_left the kernel reads from the device table `dev`.  At most
+    // grid_members members per launch.
+    cudaError_t (*launch_grid)(const BatchDomain* host, const BatchDomain* dev, int n, int flip, int device,
+                               cudaStream_t stream);
+    int grid_members;
 };
 extern const Batch3Ops batch3_ops_32x4, batch3_ops_16x8, batch3_ops_8x16;
 extern const Batch3Ops batch3_ops_f16, batch3_ops_bf16;  // shifted 16-bit members (32 x 4 tiles)

@@ -205,6 +205,33 @@ def test_batch_autotune_keeps_reduced_members():
     b.close()
 
 
+def test_batch_phases_are_bitwise_stepping_alone():
+    """An odd number of single steps leaves the batch in its other phase; the
+    graphs of that phase (16-step and single-step) must then step every
+    member on the population sets of its current parity.  Runs of 3, 20, 1,
+    33 and 5 steps use both phases of both graphs; FP32 members on both
+    phase lattices (the member-grid kernels) equal twins stepped alone
+    bitwise after every run."""
+    from paper_2101_06769_gb300.lbmp import FLAG_PHASE_REDUCED
+    ms = list(MEMBERS)
+    for m in MEMBERS[:2]:
+        r = dict(m)
+        r["phys"] = dict(m["phys"], flags=FLAG_PHASE_REDUCED)
+        ms.append(r)
+    b = Batch()
+    doms = [make(m) for m in ms]
+    twins = [make(m) for m in ms]
+    for d in doms:
+        b.add(d, 1000)
+    for n in (3, 20, 1, 33, 5):
+        b.step(n)
+        for t in twins:
+            t.step(n)
+        for d, t in zip(doms, twins):
+            assert all(np.array_equal(x, y) for x, y in zip(d.get_state(), t.get_state())), n
+    b.close()
+
+
 def test_batch_writes_every_slot():
     """Every member's target set is poisoned with NaN before each batch step;
     no NaN survives."""
