@@ -355,7 +355,8 @@ LBMP_API int lbmp_batch_members(const lbmp_batch *b, lbmp_handle **members, long
  * step of the current members' kernels (the D3Q27 and D2Q9 batch kernels,
  * no epilogue) for each D3Q27 tile shape {32 x 4, 16 x 8, 8 x 16} and
  * planes (rows) per work item {8, 16, 32, 64}, over `reps` launches after a
- * warm-up, and keeps the fastest for the batch; the graphs are re-captured at
+ * warm-up, in two passes (each shape's time the smaller of its two), and
+ * keeps the fastest for the batch; the graphs are re-captured at
  * the next lbmp_batch_step.  Trial launches read each member's current
  * population set and write the other one: no member advances and results
  * are unchanged.  table / n_entries as in lbmp_autotune (entry.tile and
