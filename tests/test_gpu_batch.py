@@ -232,6 +232,34 @@ def test_batch_phases_are_bitwise_stepping_alone():
     b.close()
 
 
+def test_batch_of_more_members_than_one_launch_holds():
+    """35 FP32 D3Q27 members (more than the kernel parameters of one launch
+    hold, so each step takes two launches of the batch kernel) with uneven
+    sizes and step counts equal their runs alone bitwise."""
+    base = MEMBERS[3]  # Rayleigh-Taylor, walled z
+    ms, steps = [], []
+    for k in range(35):
+        m = dict(base)
+        m["dims"] = (6 + 2 * (k % 5), 4 + (k % 3), 5 + (k % 4))
+        m["seed"] = 50 + k
+        ms.append(m)
+        steps.append(5 + (k % 7))
+    alone = []
+    for m, n in zip(ms, steps):
+        d = make(m)
+        d.step(n)
+        alone.append(d.get_state())
+    b = Batch()
+    doms = [make(m) for m in ms]
+    for d, n in zip(doms, steps):
+        b.add(d, n)
+    b.step(3)
+    b.step(20)
+    for d, ref in zip(doms, alone):
+        assert all(np.array_equal(x, y) for x, y in zip(d.get_state(), ref))
+    b.close()
+
+
 def test_batch_writes_every_slot():
     """Every member's target set is poisoned with NaN before each batch step;
     no NaN survives."""
