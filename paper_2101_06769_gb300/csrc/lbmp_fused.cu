@@ -8,7 +8,7 @@
 // CTAs per SM with a separate moment-difference array); column and plane
 // offsets in bytes (0.827 against 0.860 ms with element indices)
 #define LBMP_FUSED_MINB 4
-#define LBMP_FUSED_BYTEOFF 1
+#define LBMP_FUSED_BYTEOFF 4
 #define LBMP_FUSED_SPLIT 1
 #define LBMP_FUSED_RINGREG 1
 #define LBMP_OUT_ORDERED 1

@@ -23,6 +23,9 @@
 // the output pair loops keep their memory operations in order (lower register footprint)
 #define LBMP_OUT_ORDERED 1
 #define LBMP_TILE_NS tile16
+#ifndef LBMP_FUSED_BYTEOFF
+#define LBMP_FUSED_BYTEOFF 2
+#endif
 #include <stdint.h>
 
 #include "lbmp_internal.h"
@@ -33,6 +36,30 @@ namespace lbmp {
 namespace {
 
 using namespace LBMP_TILE_NS;
+
+// the encoder of one cell's outputs (as EncPtr) at a cell offset of the tile
+// geometry: the codes at base + offset, the reference at its 4-byte slot
+template <class St>
+struct EncCell {
+    static constexpr bool kTotal = true;
+    unsigned short* const* qb;
+    float* R;
+    cell_off self;
+    float off;
+    mutable float sq;
+    unsigned seed;  // code_seed of the writer cell (stochastic rounding)
+    __device__ __forceinline__ void operator()(int a, float v) const
+    {
+        const float W = wint<3>(a);
+        const unsigned short c = enc_code<St>(fmaf(v, St::S / W, -off), seed, a);
+        *at_cell(qb[a], self) = c;
+        sq += St::dec(c) * (W * St::s);
+    }
+    __device__ __forceinline__ void finish(float th, float tl) const
+    {
+        R[elem_index(self)] = ref_from_total<3>(th, tl, sq);
+    }
+};
 
 constexpr int C3 = 13;
 constexpr int GX = TX + 4, GY = TY + 4, GPLANE = GX * GY;  // g reference plane: tile + two rings
@@ -314,7 +341,7 @@ __device__ __forceinline__ void fused_segment16(const DevParams& p, const DirPtr
             float grad[3], lap;
             stencil_from_nb<3>(nh, nl, grad, lap);
             CellState s;
-            const int self = P.zs[1] + own.ys[1] + own.xs[1];
+            const cell_off self = P.zs[1] + own.ys[1] + own.xs[1];
             float* gcol = gS + cur * Q3 * NT + tid;  // this cell's decoded pre-collision g
             const GFromStrided gin{gcol, NT};
             // g first (it needs only the closure); its decoded column then
@@ -324,15 +351,15 @@ __device__ __forceinline__ void fused_segment16(const DevParams& p, const DirPtr
             flow_closure<3>(p, nh[13], grad, lap, m, s, inv_rho, nu);
             const float gd = gamma_dev<3>(s, C3);
             const float kS = St::S / wint<3>(C3);
-            const EncPtr<3, St> go{Dp.gout, Dp.rgout, self, kS * phase_post<3>(p, s, C3, gin(C3), gd), 0.f,
-                                   code_seed(p, self, 1)};
+            const EncCell<St> go{Dp.gout, Dp.rgout, self, kS * phase_post<3>(p, s, C3, gin(C3), gd), 0.f,
+                                 code_seed(p, elem_index(self), 1)};
             phase_outputs<3>(p, s, gin, nh[13], nl[13], go);
             float dh[27];
             flow_relax<3>(m, s, inv_rho, nu, dh);
 #pragma unroll
             for (int a = 0; a < Q3; ++a) gcol[a * NT] = dh[a];
-            const EncPtr<3, St> fo{Dp.fout, Dp.rfout, self, kS * flow_post<3>(s, dh, C3, gd), 0.f,
-                                   code_seed(p, self, 0)};
+            const EncCell<St> fo{Dp.fout, Dp.rfout, self, kS * flow_post<3>(s, dh, C3, gd), 0.f,
+                                 code_seed(p, elem_index(self), 0)};
             flow_outputs<3>(s, DhStrided{gcol, NT}, m, fo);
         }
         __syncthreads();

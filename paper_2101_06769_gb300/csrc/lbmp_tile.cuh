@@ -51,16 +51,16 @@ namespace LBMP_TILE_NS {
 #ifndef LBMP_FUSED_RINGREG
 #define LBMP_FUSED_RINGREG 0
 #endif
-// 1: the column and plane offsets are unsigned byte offsets of 4-byte
+// E > 0: the column and plane offsets are unsigned byte offsets of E-byte
 // populations, so a pulled value's address is its array base plus one
-// 32-bit sum (every array below 4 GiB: fewer than 2^30 cells); 0: signed
-// element indices, scaled to a 64-bit offset at every access
+// 32-bit sum (every array below 4 GiB); 0: signed element indices, scaled
+// to a 64-bit offset at every access
 #ifndef LBMP_FUSED_BYTEOFF
 #define LBMP_FUSED_BYTEOFF 0
 #endif
 #if LBMP_FUSED_BYTEOFF
 using cell_off = unsigned;
-constexpr unsigned kOffUnit = 4;
+constexpr unsigned kOffUnit = LBMP_FUSED_BYTEOFF;
 #else
 using cell_off = int;
 constexpr int kOffUnit = 1;
@@ -138,7 +138,7 @@ template <class E>
 __device__ __forceinline__ E* at_cell(E* base, cell_off o)
 {
     if constexpr (LBMP_FUSED_BYTEOFF != 0) {
-        static_assert(sizeof(E) == 4, "byte offsets of 4-byte populations");
+        static_assert(sizeof(E) == kOffUnit, "byte offsets of the unit's population size");
         using B = typename std::conditional<std::is_const<E>::value, const char, char>::type;
         return reinterpret_cast<E*>(reinterpret_cast<B*>(base) + o);
     } else {
@@ -219,7 +219,11 @@ struct CellOut {
     static constexpr bool kTotal = false;
     float* const* base;
     cell_off self;
-    __device__ __forceinline__ void operator()(int a, float v) const { *at_cell(base[a], self) = v; }
+    template <class V>  // instantiated only by the units that store through it
+    __device__ __forceinline__ void operator()(int a, V v) const
+    {
+        *at_cell(base[a], self) = v;
+    }
 };
 
 // plane whose phi stands for plane zz: periodic wrap, or the mirrored ghost
