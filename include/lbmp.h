@@ -128,8 +128,8 @@ enum {
 
 typedef struct {
     int nx, ny, nz;  /* nz = 1 for D2Q9; nx even with FP16/BF16 storage; at most 2^31-1 cells,
-                        2^30-1 for an FP32 D3Q27 domain with two population sets (the default:
-                        its kernels address each population array by 32-bit byte offsets) */
+                        2^30-1 for an FP32 domain with two population sets (the default: its
+                        kernels address each population array by 32-bit byte offsets) */
     int periodic[3]; /* 1 = periodic; 0 = half-way bounce-back walls (vertical axis only) */
 } lbmp_grid;
 

@@ -331,9 +331,9 @@ int lbmp_create_ex(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_param
         return fail(LBMP_ERR_UNSUPPORTED, "the divergence term needs FP32 storage and the full phase lattice");
     if ((params->flags & LBMP_FLAG_PHASE_REDUCED) && params->storage != LBMP_FP32)
         return fail(LBMP_ERR_UNSUPPORTED, "the reduced phase lattice is stored in FP32 only");
-    // the fused FP32 D3Q27 kernels address each population array by 32-bit byte offsets
-    if (D == 3 && params->storage == LBMP_FP32 && !(params->flags & LBMP_FLAG_AA) && N > (1LL << 30) - 1)
-        return fail(LBMP_ERR_UNSUPPORTED, "an FP32 D3Q27 domain with two population sets holds at most 2^30-1 cells");
+    // the fused FP32 kernels address each population array by 32-bit byte offsets
+    if (params->storage == LBMP_FP32 && !(params->flags & LBMP_FLAG_AA) && N > (1LL << 30) - 1)
+        return fail(LBMP_ERR_UNSUPPORTED, "an FP32 domain with two population sets holds at most 2^30-1 cells");
 
     lbmp_handle* h = new (std::nothrow) lbmp_handle();
     if (!h) return fail(LBMP_ERR_NOMEM, "host allocation failed");

@@ -44,29 +44,59 @@ __device__ __forceinline__ int pmod(int v, int n)
     return r < 0 ? r + n : r;
 }
 
+// 1: column and row offsets held as unsigned byte offsets (a pulled or
+// stored address is the array base plus one 32-bit sum; arrays below
+// 4 GiB); 0: signed element indices scaled to 64 bits at every access
+#ifndef LBMP_F2_BYTEOFF
+#define LBMP_F2_BYTEOFF 1
+#endif
+#if LBMP_F2_BYTEOFF
+using off2 = unsigned;
+constexpr unsigned kUnit2 = 4;
+#else
+using off2 = int;
+constexpr int kUnit2 = 1;
+#endif
+__device__ __forceinline__ const float* at2(const float* base, off2 o)
+{
+    if constexpr (LBMP_F2_BYTEOFF != 0)
+        return reinterpret_cast<const float*>(reinterpret_cast<const char*>(base) + o);
+    else
+        return base + o;
+}
+__device__ __forceinline__ int elem2(off2 o) { return (int)(o / kUnit2); }
+
+// stores of one cell's outputs (per-direction array bases, one cell offset)
+struct Out2 {
+    static constexpr bool kTotal = false;
+    float* const* base;
+    off2 self;
+    __device__ __forceinline__ void operator()(int a, float v) const { *const_cast<float*>(at2(base[a], self)) = v; }
+};
+
 // upstream x coordinates xs[c+1] = x - c (periodic)
 struct Col2 {
-    int xs[3];
+    off2 xs[3];
 };
 __device__ __forceinline__ void set_col2(Col2& C, int x, int nx)
 {
-    C.xs[0] = x + 1 == nx ? 0 : x + 1;
-    C.xs[1] = x;
-    C.xs[2] = x == 0 ? nx - 1 : x - 1;
+    C.xs[0] = (off2)(x + 1 == nx ? 0 : x + 1) * kUnit2;
+    C.xs[1] = (off2)x * kUnit2;
+    C.xs[2] = (off2)(x == 0 ? nx - 1 : x - 1) * kUnit2;
 }
 
 // upstream rows ys[c+1] = (y - c) nx; lo/hi: bottom/top row of a walled domain
 struct Row2 {
-    int ys[3];
+    off2 ys[3];
     bool lo, hi;
 };
 __device__ __forceinline__ void set_row2(Row2& R, const DevParams& p, int y)
 {
     R.lo = !p.vert_periodic && y == 0;
     R.hi = !p.vert_periodic && y == p.ny - 1;
-    R.ys[0] = (y + 1 == p.ny ? 0 : y + 1) * p.nx;
-    R.ys[1] = y * p.nx;
-    R.ys[2] = (y == 0 ? p.ny - 1 : y - 1) * p.nx;
+    R.ys[0] = (off2)((y + 1 == p.ny ? 0 : y + 1) * p.nx) * kUnit2;
+    R.ys[1] = (off2)(y * p.nx) * kUnit2;
+    R.ys[2] = (off2)((y == 0 ? p.ny - 1 : y - 1) * p.nx) * kUnit2;
 }
 
 // post-streaming population a of the cell (C, R): pulled from upstream, or
@@ -74,8 +104,8 @@ __device__ __forceinline__ void set_row2(Row2& R, const DevParams& p, int y)
 __device__ __forceinline__ const float* pulled2(const float* const* base, int a, const Col2& C, const Row2& R)
 {
     const int cx = Lat<2>::cx(a), cy = Lat<2>::cy(a);
-    if ((cy == 1 && R.lo) || (cy == -1 && R.hi)) return base[Lat<2>::opp(a)] + (R.ys[1] + C.xs[1]);
-    return base[a] + (R.ys[cy + 1] + C.xs[cx + 1]);
+    if ((cy == 1 && R.lo) || (cy == -1 && R.hi)) return at2(base[Lat<2>::opp(a)], R.ys[1] + C.xs[1]);
+    return at2(base[a], R.ys[cy + 1] + C.xs[cx + 1]);
 }
 
 // the same for slot r of the phase lattice (PR: D2Q5 slots, opposite QG-1-r)
@@ -88,8 +118,8 @@ __device__ __forceinline__ const float* pulled2_g(const float* const* base, int 
         constexpr int QG = PhaseLat<2, true>::Q;
         const int a = PhaseLat<2, true>::full(r);
         const int cx = Lat<2>::cx(a), cy = Lat<2>::cy(a);
-        if ((cy == 1 && R.lo) || (cy == -1 && R.hi)) return base[QG - 1 - r] + (R.ys[1] + C.xs[1]);
-        return base[r] + (R.ys[cy + 1] + C.xs[cx + 1]);
+        if ((cy == 1 && R.lo) || (cy == -1 && R.hi)) return at2(base[QG - 1 - r], R.ys[1] + C.xs[1]);
+        return at2(base[r], R.ys[cy + 1] + C.xs[cx + 1]);
     }
 }
 
@@ -118,7 +148,7 @@ __device__ __forceinline__ void stage_row(const DevParams& p, const DirPtrs2& D,
         for (int r = 0; r < QG; ++r) cp_async4(sbuf + r * 2 + tid, pulled2_g<PR>(D.gin, r, side, R));
     }
     if constexpr (PR) {
-        const int self = R.ys[1] + own.xs[1];
+        const int self = elem2(R.ys[1] + own.xs[1]);
         cp_async4(ubuf + tid, phiu + self);
         cp_async4(ubuf + TX2 + tid, phiu + p.N + self);
     }
@@ -183,14 +213,14 @@ __device__ __forceinline__ void fused2_segment(const DevParams& p, const DirPtrs
             CellState s;
             float dh[27];
             flow_collide<2>(p, nh[4], grad, lap, m, s, dh);
-            const int self = R.ys[1] + own.xs[1];
+            const off2 self = R.ys[1] + own.xs[1];
             if constexpr (PR)
                 collide_outputs<2, true>(p, s, DhArray{dh}, m, GFromStrided{gS + cur * QG * TX2 + tid, TX2}, nh[4],
-                                         nl[4], PtrOut{D.fout, self}, PtrOut{D.gout, self},
-                                         PhiUStaged<2>{p, phiu, self, uS + cur * 2 * TX2 + tid, TX2});
+                                         nl[4], Out2{D.fout, self}, Out2{D.gout, self},
+                                         PhiUStaged<2>{p, phiu, elem2(self), uS + cur * 2 * TX2 + tid, TX2});
             else
                 collide_outputs<2>(p, s, DhArray{dh}, m, GFromStrided{gS + cur * Q2 * TX2 + tid, TX2}, nh[4], nl[4],
-                                   PtrOut{D.fout, self}, PtrOut{D.gout, self});
+                                   Out2{D.fout, self}, Out2{D.gout, self});
         }
     }
     __syncthreads();

@@ -115,8 +115,8 @@ def test_size_flag_and_form_limits_rejected_without_device_work(lib):
     storage with an odd nx, unknown flag bits (INVALID_ARG); the reduced phase
     lattice or the divergence term with 16-bit storage, the two flags
     together, in-place AA storage outside D3Q27 FP32 with the full phase
-    lattice, and an FP32 D3Q27 two-set domain of 2^30 cells, whose arrays
-    its kernels could not address by 32-bit byte offsets (UNSUPPORTED)."""
+    lattice, and FP32 two-set domains of 2^30 cells, whose arrays their
+    kernels could not address by 32-bit byte offsets (UNSUPPORTED)."""
     h = C.c_void_p()
     per = (C.c_int * 3)(1, 1, 0)
     ok = dict(rho_ratio=3.0, nu_h=0.1)
@@ -136,4 +136,9 @@ def test_size_flag_and_form_limits_rejected_without_device_work(lib):
     for g, prm, want in cases:
         rc = lib.lbmp_create(C.byref(g), lbmp.D3Q27, C.byref(prm), None, C.byref(h))
         assert rc == want, (rc, lib.lbmp_last_error())
+        assert not h.value
+    per2 = (C.c_int * 3)(1, 0, 1)
+    for prm in (lbmp.make_params(**ok), lbmp.make_params(flags=lbmp.FLAG_PHASE_REDUCED, **ok)):
+        rc = lib.lbmp_create(C.byref(lbmp.Grid(32768, 32768, 1, per2)), lbmp.D2Q9, C.byref(prm), None, C.byref(h))
+        assert rc == -6, (rc, lib.lbmp_last_error())
         assert not h.value
