@@ -16,6 +16,8 @@
 // values (phi_sum_shifted) and keeps the decoded own values for the
 // collision.  Decoding, the collision and the encoding are those of the
 // reference pair (lbmp_kernels.cu), in the same order.
+#include <type_traits>
+
 #include "lbmp_internal.h"
 
 namespace lbmp {
@@ -80,22 +82,72 @@ __device__ __forceinline__ void load_ref_row(const DevParams& p, const float* sr
 
 // columns x-1, x, x+1 (periodic) and rows y+1, y, y-1 (periodic, or flagged
 // at a wall) of a cell, as offsets: index [c+1] is the upstream neighbour x - c
+// 1: the offsets are unsigned byte offsets of the 2-byte codes (a pulled or
+// stored code's address is its array base plus one 32-bit sum); 0: signed
+// element indices scaled to 64 bits at every access
+#ifndef LBMP_F2S_BYTEOFF
+#define LBMP_F2S_BYTEOFF 1
+#endif
+#if LBMP_F2S_BYTEOFF
+using off2s = unsigned;
+constexpr unsigned kUnit2s = 2;
+#else
+using off2s = int;
+constexpr int kUnit2s = 1;
+#endif
+template <class E>
+__device__ __forceinline__ E* at2s(E* base, off2s o)
+{
+    if constexpr (LBMP_F2S_BYTEOFF != 0) {
+        static_assert(sizeof(E) == 2, "byte offsets of the 2-byte codes");
+        using B = typename std::conditional<std::is_const<E>::value, const char, char>::type;
+        return reinterpret_cast<E*>(reinterpret_cast<B*>(base) + o);
+    } else {
+        return base + o;
+    }
+}
+__device__ __forceinline__ int elem2s(off2s o) { return (int)(o / kUnit2s); }
+
 struct Cell2 {
-    int xs[3], ys[3];
+    off2s xs[3], ys[3];
     bool lo, hi;
 };
 
 __device__ __forceinline__ void set_cell2(Cell2& C, const DevParams& p, int x, int y)
 {
-    C.xs[0] = x + 1 == p.nx ? 0 : x + 1;
-    C.xs[1] = x;
-    C.xs[2] = x == 0 ? p.nx - 1 : x - 1;
+    C.xs[0] = (off2s)(x + 1 == p.nx ? 0 : x + 1) * kUnit2s;
+    C.xs[1] = (off2s)x * kUnit2s;
+    C.xs[2] = (off2s)(x == 0 ? p.nx - 1 : x - 1) * kUnit2s;
     C.lo = !p.vert_periodic && y == 0;
     C.hi = !p.vert_periodic && y == p.ny - 1;
-    C.ys[0] = (y + 1 == p.ny ? 0 : y + 1) * p.nx;
-    C.ys[1] = y * p.nx;
-    C.ys[2] = (y == 0 ? p.ny - 1 : y - 1) * p.nx;
+    C.ys[0] = (off2s)((y + 1 == p.ny ? 0 : y + 1) * p.nx) * kUnit2s;
+    C.ys[1] = (off2s)(y * p.nx) * kUnit2s;
+    C.ys[2] = (off2s)((y == 0 ? p.ny - 1 : y - 1) * p.nx) * kUnit2s;
 }
+
+// the encoder of one cell's outputs (as EncPtr) at a cell offset: the codes
+// at base + offset, the reference at its 4-byte slot
+template <class St>
+struct EncCell2 {
+    static constexpr bool kTotal = true;
+    unsigned short* const* qb;
+    float* R;
+    off2s self;
+    float off;
+    mutable float sq;
+    unsigned seed;  // code_seed of the writer cell (stochastic rounding)
+    __device__ __forceinline__ void operator()(int a, float v) const
+    {
+        const float W = wint<2>(a);
+        const unsigned short c = enc_code<St>(fmaf(v, St::S / W, -off), seed, a);
+        *at2s(qb[a], self) = c;
+        sq += St::dec(c) * (W * St::s);
+    }
+    __device__ __forceinline__ void finish(float th, float tl) const
+    {
+        R[elem2s(self)] = ref_from_total<2>(th, tl, sq);
+    }
+};
 
 // code of the pulled population a of cell C, and whether it bounced at a wall
 // (then it is the opposite population of the cell itself); a is a
@@ -105,8 +157,8 @@ __device__ __forceinline__ unsigned short pulled_code(const unsigned short* cons
 {
     const int cx = Lat<2>::cx(a), cy = Lat<2>::cy(a);
     bounced = (cy == 1 && C.lo) || (cy == -1 && C.hi);
-    if (bounced) return __ldg(q[Lat<2>::opp(a)] + (C.ys[1] + C.xs[1]));
-    return __ldg(q[a] + (C.ys[cy + 1] + C.xs[cx + 1]));
+    if (bounced) return __ldg(at2s(q[Lat<2>::opp(a)], C.ys[1] + C.xs[1]));
+    return __ldg(at2s(q[a], C.ys[cy + 1] + C.xs[cx + 1]));
 }
 
 // Decode the pulled g of one cell of row yy and sum its phi (hi, lo); Keep:
@@ -241,12 +293,12 @@ __device__ __forceinline__ void fused2s_segment(const DevParams& p, const DirPtr
             CellState s;
             float dh[27];
             flow_collide<2>(p, nh[C2], grad, lap, m, s, dh);
-            const int self = C.ys[1] + C.xs[1];
+            const off2s self = C.ys[1] + C.xs[1];
             const GFromStrided gi{gS + cur * Q2 * TX2 + tid, TX2};
             float off_f, off_g;
             rest_offsets<2, St>(p, s, dh, gi, off_f, off_g);
-            const EncPtr<2, St> fo{D.fout, D.rfout, self, off_f, 0.f, code_seed(p, self, 0)};
-            const EncPtr<2, St> go{D.gout, D.rgout, self, off_g, 0.f, code_seed(p, self, 1)};
+            const EncCell2<St> fo{D.fout, D.rfout, self, off_f, 0.f, code_seed(p, elem2s(self), 0)};
+            const EncCell2<St> go{D.gout, D.rgout, self, off_g, 0.f, code_seed(p, elem2s(self), 1)};
             collide_outputs<2>(p, s, DhArray{dh}, m, gi, nh[C2], nl[C2], fo, go);
         }
     }
