@@ -55,3 +55,38 @@ def test_full_size_splash_properties(name, storage):
             assert _max_asymmetry(d.get_phi()) < 1e-3
     finally:
         d.close()
+
+
+def test_d2q9_arrays_beyond_2gib():
+    """A 2-D FP32 domain whose population arrays are larger than 2 GiB
+    (8192 x 73728 = 604M cells, 2.4 GB per array, 87 GB of state): the step
+    kernels address them by unsigned 32-bit byte offsets, and the
+    Rayleigh-Taylor interface sits at y = 70000, beyond the 2^31-byte mark
+    (cell 2^29 is row 65536).  An offset that wrapped or was read signed there
+    would pull populations from another region or out of the array: the mass
+    would change and the interface lose its mirror symmetry x -> nx - x,
+    which the noise-free initial state and every step of the method keep."""
+    import torch
+    nx, ny = 8192, 73728
+    free, _ = torch.cuda.mem_get_info()
+    if free < 110e9:
+        pytest.skip("needs about 95 GB of free device memory")
+    # gravity scaled with the height, so that the hydrostatic pressure over
+    # the column stays as small as in the 256-row workload
+    d = Domain(2, (nx, ny, 1), (1, 0, 1), atwood=0.5, nu_ratio=1.0, Re=256.0, g_accel=2.5e-5 * 256 / ny,
+               L_ref=64.0, mobility=0.02, width=5.0)
+    try:
+        d.init("rt", [70000.0, 64.0, 0.0, 1.0], seed=3)
+        d.step(STEPS)
+        ob = d.observables()
+        assert ob.health == 0
+        assert abs(ob.mass_drift_rel) < 1e-6
+        assert 0.0 < ob.max_u < 0.05
+        phi = d.get_phi().reshape(ny, nx)
+        band = phi[69800:70200]
+        assert band.min() < 0.05 and band.max() > 0.95  # the interface is in the band
+        mx = (-np.arange(nx)) % nx
+        assert np.abs(band - band[:, mx]).max() < 1e-3
+        assert np.abs(phi[65530:65542] - phi[65530:65542][:, mx]).max() < 1e-3
+    finally:
+        d.close()
