@@ -27,6 +27,11 @@
  *   A15 F_b = -(rho - (rho_h+rho_l)/2) g e_vertical
  *   A16 We = rho_h L U^2/sigma   A17 half-way bounce-back, mirrored phi ghosts
  *   A18 tanh initial profiles    A21 D2Q9 restriction of the 3-D relations
+ *   A28 symmetry boundary of the 2-D splash (Sec. 3.4): half-way specular
+ *       reflection -- a population leaving across the face of a symmetry
+ *       axis returns to the same cell along that axis with its velocity
+ *       component along the axis reversed (it still moves along the other
+ *       axes); the phi ghost beyond the face equals the boundary cell
  * and, for the reduced phase lattice of Sec. 2.2 (LBMO_FLAG_PHASE_REDUCED):
  *   P1  D3Q7 (w 1/4 rest, 1/8 faces, cs2 = 1/4) / D2Q5 (1/3, 1/6, cs2 = 1/3)
  *   P2  d/dt(phi u) = (phi u)^n - (phi u)^(n-1); before the first step the
@@ -218,10 +223,16 @@ lbmo *lbmo_create(int D, const int dims[3], const int periodic[3], const lbmo_ph
     s->Qg = s->Lg.Q;
     for (int i = 0; i < 3; ++i) {
         s->n[i] = dims[i];
-        s->per[i] = periodic[i] ? 1 : 0;
+        s->per[i] = periodic[i] == 2 ? 2 : (periodic[i] ? 1 : 0);
     }
     if (D == 2) s->per[2] = 1;
     s->vert = (D == 3) ? 2 : 1;
+    for (int i = 0; i < 3; ++i)
+        if (s->per[i] == 2 && (i == s->vert || (p->flags & LBMO_FLAG_DIVU))) {
+            set_err("a symmetry axis is horizontal and excludes the divergence term");
+            free(s);
+            return NULL;
+        }
     s->N = (long)dims[0] * dims[1] * dims[2];
     s->phys = *p;
     if (lbmo_derive(D, p, &s->d) != 0) { free(s); return NULL; }
@@ -299,8 +310,8 @@ static int ghost_coord(int x, int d, int n, int periodic)
 {
     int y = x + d;
     if (y >= 0 && y < n) return y;
-    if (periodic) return ((y % n) + n) % n;
-    return y < 0 ? 0 : n - 1;
+    if (periodic == 1) return ((y % n) + n) % n;
+    return y < 0 ? 0 : n - 1; /* wall or symmetry face */
 }
 
 /* ------------------------------------------------ isotropic differences */
@@ -345,7 +356,7 @@ static double div_cell(const lbmo *s, const double *u, int x, int y, int z)
         int q[3], sign = 1;
         for (int k = 0; k < 3; ++k) {
             int v = xyz[k] + L->c[a][k];
-            if ((v < 0 || v >= s->n[k]) && !s->per[k]) sign = -1;
+            if ((v < 0 || v >= s->n[k]) && s->per[k] == 0) sign = -1;
             q[k] = ghost_coord(xyz[k], L->c[a][k], s->n[k], s->per[k]);
         }
         long j = cell_index(s, q[0], q[1], q[2]);
@@ -698,26 +709,48 @@ static void update_phi(lbmo *s)
     }
 }
 
-/* push population value v of direction a (velocity c) of the cell at xyz into
- * the array set out (Q directions): to the downstream cell, or back into the
- * same cell in the opposite direction across a half-way wall (A17) */
-static void push(const lbmo *s, double *out, int Q, const int c[3], int a, const int xyz[3], long i, double v)
+/* direction of the lattice whose velocity is that of a with the components
+ * flagged in flip reversed */
+static int mirror_dir(const lattice *L, int a, const int flip[3])
 {
-    int dst[3], wall = 0;
+    for (int b = 0; b < L->Q; ++b) {
+        int same = 1;
+        for (int k = 0; k < 3; ++k) same &= L->c[b][k] == (flip[k] ? -L->c[a][k] : L->c[a][k]);
+        if (same) return b;
+    }
+    return a;
+}
+
+/* push population value v of direction a of the cell at xyz into the array
+ * set out (lattice Lx): to the downstream cell; back into the same cell in
+ * the opposite direction across a half-way wall (A17); across the face of a
+ * symmetry axis, into the cell that is downstream along the other axes only,
+ * with the velocity component along the symmetry axis reversed (A28).  A
+ * link that crosses a wall bounces back whatever else it crosses. */
+static void push(const lbmo *s, const lattice *Lx, double *out, int a, const int xyz[3], long i, double v)
+{
+    const int *c = Lx->c[a];
+    int dst[3], wall = 0, flip[3] = {0, 0, 0}, mirrored = 0;
     for (int k = 0; k < 3; ++k) {
         int p = xyz[k] + c[k];
         if (p < 0 || p >= s->n[k]) {
-            if (s->per[k])
+            if (s->per[k] == 1) {
                 p = (p + s->n[k]) % s->n[k];
-            else
+            } else if (s->per[k] == 2) {
+                p = xyz[k];
+                flip[k] = mirrored = 1;
+            } else {
                 wall = 1;
+            }
         }
         dst[k] = p;
     }
-    if (wall)
-        out[(size_t)(Q - 1 - a) * s->N + i] = v;
-    else
-        out[(size_t)a * s->N + cell_index(s, dst[0], dst[1], dst[2])] = v;
+    if (wall) {
+        out[(size_t)(Lx->Q - 1 - a) * s->N + i] = v;
+    } else {
+        const int b = mirrored ? mirror_dir(Lx, a, flip) : a;
+        out[(size_t)b * s->N + cell_index(s, dst[0], dst[1], dst[2])] = v;
+    }
 }
 
 static void step_once(lbmo *s)
@@ -743,8 +776,8 @@ static void step_once(lbmo *s)
         for (int k = 0; k < 3; ++k) s->u_next[(size_t)k * N + i] = diag[1 + k];
         /* push streaming; half-way bounce-back at walls */
         int xyz[3] = {x, y, z};
-        for (int a = 0; a < Q; ++a) push(s, s->fn, Q, L->c[a], a, xyz, i, fo[a]);
-        for (int a = 0; a < Qg; ++a) push(s, s->gn, Qg, Lg->c[a], a, xyz, i, go[a]);
+        for (int a = 0; a < Q; ++a) push(s, L, s->fn, a, xyz, i, fo[a]);
+        for (int a = 0; a < Qg; ++a) push(s, Lg, s->gn, a, xyz, i, go[a]);
     }
     double *t = s->f;
     s->f = s->fn;
@@ -896,7 +929,9 @@ int lbmo_init(lbmo *s, int case_id, const double *args, int nargs, unsigned long
             double zc = sheet + 0.5 * Dd + 2.0 * d->W;
             double r2 = 0.0;
             for (int k = 0; k < D; ++k) {
-                double c0 = (k == v) ? zc : (double)(s->n[k] / 2);
+                /* the drop's axis: at n/2, or at the coordinate given (on a
+                 * symmetry face, -0.5, for a half domain) */
+                double c0 = (k == v) ? zc : (nargs > 4 ? A[4] : (double)(s->n[k] / 2));
                 double dx = pos[k] - c0;
                 r2 += dx * dx;
             }

@@ -45,7 +45,8 @@ enum {
     LBMO_CASE_DROP_STATIC = 1, /* args: R, p_init(0/1), noise                */
     LBMO_CASE_FLAT = 2,        /* args: x0, x1, noise   (heavy slab x0<x<x1)  */
     LBMO_CASE_POISEUILLE = 3,  /* args: noise           (heavy lower half)   */
-    LBMO_CASE_DROP_SHEET = 4,  /* args: D, sheet_h, U0, noise                */
+    LBMO_CASE_DROP_SHEET = 4,  /* args: D, sheet_h, U0, noise [, axis]: the drop's
+                                  horizontal axis coordinate (default n/2) */
     LBMO_CASE_SHEAR_WAVE = 5,  /* args: U, noise        (phi = 1)            */
     LBMO_CASE_UNIFORM = 6      /* args: phi0, p0, ux, uy, uz                 */
 };
@@ -91,8 +92,10 @@ typedef struct {
 typedef struct lbmo lbmo;
 
 /* dims = {nx, ny, nz} (nz = 1 for D = 2); periodic = {px, py, pz}, 1 = periodic,
- * 0 = half-way bounce-back walls at both ends of that axis.  Returns NULL on
- * invalid input (message via lbmo_last_error). */
+ * 0 = half-way bounce-back walls at both ends of that axis, 2 = a symmetry
+ * axis (horizontal axes only, not with LBMO_FLAG_DIVU): half-way specular
+ * reflection at both of its faces, the phi ghost equal to the boundary cell
+ * (reading A28).  Returns NULL on invalid input (message via lbmo_last_error). */
 lbmo *lbmo_create(int D, const int dims[3], const int periodic[3], const lbmo_phys *p);
 void lbmo_destroy(lbmo *s);
 const char *lbmo_last_error(void);

@@ -55,6 +55,14 @@ MUTATIONS = {
     "stored_phi_u": ("for (int k = 0; k < 3; ++k) s->phiu_prev[(size_t)k * N + i] = diag[14 + k];",
                      "for (int k = 0; k < 3; ++k) s->phiu_prev[(size_t)k * N + i] = 0.0;",
                      "test_oracle_phase_reduced.py::test_reduced_interface_galilean_invariance"),
+    # symmetry axis of the 2-D splash (Sec. 3.4, reading A28)
+    "symmetry_bounces_back": ("                p = xyz[k];\n                flip[k] = mirrored = 1;",
+                              "                wall = 1;",
+                              "test_oracle_symmetry.py::test_half_domain_equals_half_of_the_symmetric_full_domain"),
+    "symmetry_keeps_direction": ("const int b = mirrored ? mirror_dir(Lx, a, flip) : a;", "const int b = a;",
+                                 "test_oracle_symmetry.py::test_half_domain_equals_half_of_the_symmetric_full_domain"),
+    "symmetry_ghost_wraps": ("    if (periodic == 1) return ((y % n) + n) % n;", "    if (periodic) return ((y % n) + n) % n;",
+                             "test_oracle_symmetry.py::test_half_domain_equals_half_of_the_symmetric_full_domain"),
     # observables and initial states
     "kinetic_energy_half": ("ke_c[i] = 0.5 * m.rho * uu;", "ke_c[i] = m.rho * uu;",
                             "test_oracle_observables.py::test_kinetic_energy_closed_forms"),
@@ -84,8 +92,8 @@ MUTATIONS = {
                           "if (D == 3) h += A[1] * sin(2.0 * PI * y / s->n[1]);",
                           "test_oracle_observables.py::test_rt_start_interface_and_tips"),
     # divergence term (reading V1)
-    "wall_ghost_sign": ("if ((v < 0 || v >= s->n[k]) && !s->per[k]) sign = -1;",
-                        "if ((v < 0 || v >= s->n[k]) && !s->per[k]) sign = 1;",
+    "wall_ghost_sign": ("if ((v < 0 || v >= s->n[k]) && s->per[k] == 0) sign = -1;",
+                        "if ((v < 0 || v >= s->n[k]) && s->per[k] == 0) sign = 1;",
                         "test_oracle_divu.py::test_divergence_wall_ghost_closed_form"),
     "divergence_factor": ("Xi[a] += L->w[a] * CS2 * c.rho * divu;", "Xi[a] += 0.5 * L->w[a] * CS2 * c.rho * divu;",
                           "test_oracle_divu.py::test_divergence_term_moments"),
