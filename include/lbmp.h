@@ -75,9 +75,11 @@ enum {
                                   p_h = (D-1) sigma/R phi */
     LBMP_CASE_FLAT = 2,        /* args: x0, x1, noise. Heavy slab x0 < x < x1 */
     LBMP_CASE_POISEUILLE = 3,  /* args: noise. Heavy lower half of the vertical axis */
-    LBMP_CASE_DROP_SHEET = 4,  /* args: D, sheet_h, U0, noise. Heavy sheet below vertical
-                                  coordinate sheet_h and a drop of diameter D centred
-                                  sheet_h + D/2 + 2W above the bottom, falling at U0 */
+    LBMP_CASE_DROP_SHEET = 4,  /* args: D, sheet_h, U0, noise [, axis]. Heavy sheet below
+                                  vertical coordinate sheet_h and a drop of diameter D
+                                  centred sheet_h + D/2 + 2W above the bottom, falling at
+                                  U0; its horizontal axis at n/2, or at the coordinate
+                                  axis (-0.5: on the left face of a symmetry axis) */
     LBMP_CASE_SHEAR_WAVE = 5,  /* args: U, noise. phi = 1, u_x = U sin(2 pi y/ny) */
     LBMP_CASE_UNIFORM = 6      /* args: phi0, p0, ux, uy, uz */
 };
@@ -130,7 +132,11 @@ typedef struct {
     int nx, ny, nz;  /* nz = 1 for D2Q9; nx even with FP16/BF16 storage; at most 2^31-1 cells,
                         2^30-1 for an FP32 domain with two population sets (the default: its
                         kernels address each population array by 32-bit byte offsets) */
-    int periodic[3]; /* 1 = periodic; 0 = half-way bounce-back walls (vertical axis only) */
+    int periodic[3]; /* 1 = periodic; 0 = half-way bounce-back walls (vertical axis only);
+                        2 = symmetry axis (x of a D2Q9 FP32 domain only; not with
+                        LBMP_FLAG_DIVU, not a batch member): half-way specular reflection
+                        at both faces, the phi ghost equal to the boundary cell -- the
+                        symmetry boundary of the 2-D splash, Sec. 3.4 */
 } lbmp_grid;
 
 /* problem statement (lattice units, heavy density rho_h = 1, Sec. 3) */

@@ -93,6 +93,7 @@ void fill_devparams(lbmp_handle* h)
     q.ny = h->grid.ny;
     q.nz = h->grid.nz;
     q.vert_periodic = h->grid.periodic[h->D - 1] ? 1 : 0;
+    q.sym_x = (h->D == 2 && h->grid.periodic[0] == 2) ? 1 : 0;
     // a plain domain; lbmp_create_slab overrides these for one rank's slab
     q.wall_lo = q.wall_hi = q.vert_periodic ? 0 : 1;
     q.zb = 0;
@@ -312,8 +313,12 @@ int lbmp_create_ex(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_param
     if (D == 3 && (grid->nx < 2 || grid->ny < 2 || grid->nz < 2))
         return fail(LBMP_ERR_INVALID_ARG, "D3Q27 needs every size >= 2");
     if (D == 2 && (grid->nx < 2 || grid->ny < 2)) return fail(LBMP_ERR_INVALID_ARG, "D2Q9 needs nx, ny >= 2");
+    const bool sym_x = D == 2 && grid->periodic[0] == 2;
     for (int k = 0; k < D - 1; ++k)
-        if (!grid->periodic[k]) return fail(LBMP_ERR_INVALID_ARG, "horizontal axes must be periodic");
+        if (grid->periodic[k] != 1 && !(k == 0 && sym_x))
+            return fail(LBMP_ERR_INVALID_ARG, "horizontal axes must be periodic (or, in 2-D, x a symmetry axis: 2)");
+    if (grid->periodic[D - 1] != 0 && grid->periodic[D - 1] != 1)
+        return fail(LBMP_ERR_INVALID_ARG, "the vertical axis is periodic (1) or walled (0)");
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
     if (N > (1LL << 31) - 1) return fail(LBMP_ERR_INVALID_ARG, "more than 2^31-1 cells");
     if (params->storage != LBMP_FP32 && params->storage != LBMP_FP16_SHIFTED && params->storage != LBMP_BF16_SHIFTED)
@@ -331,6 +336,8 @@ int lbmp_create_ex(const lbmp_grid* grid, lbmp_lattice lattice, const lbmp_param
         return fail(LBMP_ERR_UNSUPPORTED, "the divergence term needs FP32 storage and the full phase lattice");
     if ((params->flags & LBMP_FLAG_PHASE_REDUCED) && params->storage != LBMP_FP32)
         return fail(LBMP_ERR_UNSUPPORTED, "the reduced phase lattice is stored in FP32 only");
+    if (sym_x && (params->storage != LBMP_FP32 || (params->flags & LBMP_FLAG_DIVU)))
+        return fail(LBMP_ERR_UNSUPPORTED, "a symmetry axis needs FP32 storage and no LBMP_FLAG_DIVU");
     // the fused FP32 kernels address each population array by 32-bit byte offsets
     if (params->storage == LBMP_FP32 && !(params->flags & LBMP_FLAG_AA) && N > (1LL << 30) - 1)
         return fail(LBMP_ERR_UNSUPPORTED, "an FP32 domain with two population sets holds at most 2^30-1 cells");
@@ -493,7 +500,7 @@ int lbmp_init(lbmp_handle* h, int case_id, const double* case_args, int nargs, u
         h->probe[h->D - 1] = pv < 0 ? 0 : (pv >= nv ? nv - 1 : pv);
     }
     LBMP_CUDA(cudaMemsetAsync(h->red_out + kStatusSlot, 0, sizeof(double), h->stream), "status reset");
-    LBMP_CUDA(lbmp::launch_init(h, case_id, a, seed), "init kernel");
+    LBMP_CUDA(lbmp::launch_init(h, case_id, a, nargs, seed), "init kernel");
     LBMP_CUDA(lbmp::launch_mass(h, h->red_out + 12), "reference mass");
     return LBMP_OK;
 }

@@ -313,6 +313,7 @@ LBMP_API int lbmp_batch_add(lbmp_batch* b, lbmp_handle* h, long steps)
     if ((int)b->members.size() >= kMaxMembers) return batch_fail(LBMP_ERR_INVALID_ARG, "batch is full");
     if (h->divu) return batch_fail(LBMP_ERR_UNSUPPORTED, "divergence-term domains are not batch members");
     if (h->slab || h->aa) return batch_fail(LBMP_ERR_UNSUPPORTED, "z-slabs and in-place AA domains are not batch members");
+    if (h->dp.sym_x) return batch_fail(LBMP_ERR_UNSUPPORTED, "domains with a symmetry axis are not batch members");
     size_t used = 0;
     for (const Member& m : b->members) {
         if (m.h == h) return batch_fail(LBMP_ERR_INVALID_ARG, "domain is already a member");

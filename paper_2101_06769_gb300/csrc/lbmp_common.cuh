@@ -53,6 +53,7 @@ struct Lat<3> {
     __host__ __device__ static constexpr int cz(int a) { return a / 9 - 1; }
     __host__ __device__ static constexpr float w(int a) { return (float)(w1d(cx(a)) * w1d(cy(a)) * w1d(cz(a))); }
     __host__ __device__ static constexpr int opp(int a) { return 26 - a; }
+    __host__ __device__ static constexpr int mx(int a) { return a - 2 * cx(a); }  // x velocity reversed
 };
 
 template <>
@@ -63,6 +64,7 @@ struct Lat<2> {
     __host__ __device__ static constexpr int cz(int) { return 0; }
     __host__ __device__ static constexpr float w(int a) { return (float)(w1d(cx(a)) * w1d(cy(a))); }
     __host__ __device__ static constexpr int opp(int a) { return 8 - a; }
+    __host__ __device__ static constexpr int mx(int a) { return a - 2 * cx(a); }  // x velocity reversed
 };
 
 constexpr float kCs2 = 1.0f / 3.0f;
@@ -120,6 +122,10 @@ struct DevParams {
     // streamed value of a at i is A[a][i]); 2 = AA, swapped phase (it is
     // A[opp(a)][i - c_a], or A[a][i] across a wall)
     int aa;
+    // D2Q9 only: the x axis is a symmetry axis (reading A28: half-way
+    // specular reflection at both faces, the phi ghost equal to the boundary
+    // cell) instead of periodic
+    int sym_x;
     long long N;            // cells
     float rho_l, drho, rho_bar;
     float nu_h, nu_l, eta_h, eta_l;
@@ -201,6 +207,12 @@ __device__ __forceinline__ long long pull_src(const DevParams& p, int a, int x, 
             }
             ys = ys < 0 ? ys + p.ny : ys - p.ny;
         }
+        if (p.sym_x && (x - cx < 0 || x - cx >= p.nx)) {
+            // across a symmetry face: the cell's own column, the value that
+            // left it with the mirrored x velocity
+            dir = Lat<D>::mx(a);
+            return (long long)ys * p.nx + x;
+        }
         return (long long)ys * p.nx + xs;
     }
 }
@@ -276,6 +288,10 @@ __device__ __forceinline__ long long push_dst(const DevParams& p, int a, int x, 
                 return self;
             }
             yd = yd < 0 ? yd + p.ny : yd - p.ny;
+        }
+        if (p.sym_x && (x + cx < 0 || x + cx >= p.nx)) {
+            dir = Lat<D>::mx(a);
+            return (long long)yd * p.nx + x;
         }
         return (long long)yd * p.nx + xd;
     }
@@ -577,7 +593,7 @@ __device__ __forceinline__ long long nbr_index(const DevParams& p, int a, int x,
         return ((long long)zz * p.ny + yy) * p.nx + xx;
     } else {
         const int yy = wrap_v(y + Lat<D>::cy(a), p.ny, p.vert_periodic);
-        return (long long)yy * p.nx + xx;
+        return (long long)yy * p.nx + (p.sym_x ? wrap_v(x + Lat<D>::cx(a), p.nx, 0) : xx);
     }
 }
 

@@ -74,15 +74,34 @@ struct Out2 {
     __device__ __forceinline__ void operator()(int a, float v) const { *const_cast<float*>(at2(base[a], self)) = v; }
 };
 
-// upstream x coordinates xs[c+1] = x - c (periodic)
+// upstream x coordinates xs[c+1] = x - c (periodic); with a symmetry x axis
+// (reading A28) the column's own neighbours, clamped, and slo / shi flag the
+// columns next to the left / right symmetry face
 struct Col2 {
     off2 xs[3];
+    bool slo, shi;
 };
 __device__ __forceinline__ void set_col2(Col2& C, int x, int nx)
 {
     C.xs[0] = (off2)(x + 1 == nx ? 0 : x + 1) * kUnit2;
     C.xs[1] = (off2)x * kUnit2;
     C.xs[2] = (off2)(x == 0 ? nx - 1 : x - 1) * kUnit2;
+    C.slo = C.shi = false;
+}
+__device__ __forceinline__ void set_col2_sym(Col2& C, int x, int nx)
+{
+    C.xs[0] = (off2)(x + 1 == nx ? x : x + 1) * kUnit2;
+    C.xs[1] = (off2)x * kUnit2;
+    C.xs[2] = (off2)(x == 0 ? 0 : x - 1) * kUnit2;
+    C.slo = x == 0;
+    C.shi = x == nx - 1;
+}
+// column x of the lattice or its mirror image across a symmetry face (clamped:
+// the columns further out than the first ghost feed no stencil)
+__device__ __forceinline__ int reflect_col(int x, int nx)
+{
+    const int r = x < 0 ? -1 - x : (x >= nx ? 2 * nx - 1 - x : x);
+    return r < 0 ? 0 : (r >= nx ? nx - 1 : r);
 }
 
 // upstream rows ys[c+1] = (y - c) nx; lo/hi: bottom/top row of a walled domain
@@ -99,26 +118,32 @@ __device__ __forceinline__ void set_row2(Row2& R, const DevParams& p, int y)
     R.ys[2] = (off2)((y == 0 ? p.ny - 1 : y - 1) * p.nx) * kUnit2;
 }
 
-// post-streaming population a of the cell (C, R): pulled from upstream, or
-// bounced back at a wall
+// post-streaming population a of the cell (C, R): pulled from upstream,
+// bounced back at a wall, or (SX) reflected at a symmetry face: the value
+// that left the cell's own column, one row upstream, with the mirrored x
+// velocity
+template <bool SX>
 __device__ __forceinline__ const float* pulled2(const float* const* base, int a, const Col2& C, const Row2& R)
 {
     const int cx = Lat<2>::cx(a), cy = Lat<2>::cy(a);
     if ((cy == 1 && R.lo) || (cy == -1 && R.hi)) return at2(base[Lat<2>::opp(a)], R.ys[1] + C.xs[1]);
+    if (SX && ((cx == 1 && C.slo) || (cx == -1 && C.shi))) return at2(base[Lat<2>::mx(a)], R.ys[cy + 1] + C.xs[1]);
     return at2(base[a], R.ys[cy + 1] + C.xs[cx + 1]);
 }
 
 // the same for slot r of the phase lattice (PR: D2Q5 slots, opposite QG-1-r)
-template <bool PR>
+// (a face population's mirror image is its opposite slot)
+template <bool PR, bool SX>
 __device__ __forceinline__ const float* pulled2_g(const float* const* base, int r, const Col2& C, const Row2& R)
 {
     if constexpr (!PR) {
-        return pulled2(base, r, C, R);
+        return pulled2<SX>(base, r, C, R);
     } else {
         constexpr int QG = PhaseLat<2, true>::Q;
         const int a = PhaseLat<2, true>::full(r);
         const int cx = Lat<2>::cx(a), cy = Lat<2>::cy(a);
         if ((cy == 1 && R.lo) || (cy == -1 && R.hi)) return at2(base[QG - 1 - r], R.ys[1] + C.xs[1]);
+        if (SX && ((cx == 1 && C.slo) || (cx == -1 && C.shi))) return at2(base[QG - 1 - r], R.ys[1] + C.xs[1]);
         return at2(base[r], R.ys[cy + 1] + C.xs[cx + 1]);
     }
 }
@@ -132,7 +157,7 @@ __device__ __forceinline__ int row_src(const DevParams& p, int yy)
 
 // stage row yy: own g into gbuf, side cells' g into sbuf, then phi into
 // prow; PR: also the own cells' stored phi u of that row into ubuf [2][TX2]
-template <bool PR>
+template <bool PR, bool SX>
 __device__ __forceinline__ void stage_row(const DevParams& p, const DirPtrs2& D, const Col2& own, const Col2& side,
                                           int tid, int yy, float* __restrict__ gbuf, float* __restrict__ sbuf,
                                           float2* __restrict__ prow, const float* __restrict__ phiu,
@@ -142,10 +167,10 @@ __device__ __forceinline__ void stage_row(const DevParams& p, const DirPtrs2& D,
     Row2 R;
     set_row2(R, p, row_src(p, yy));
 #pragma unroll
-    for (int r = 0; r < QG; ++r) cp_async4(gbuf + r * TX2 + tid, pulled2_g<PR>(D.gin, r, own, R));
+    for (int r = 0; r < QG; ++r) cp_async4(gbuf + r * TX2 + tid, pulled2_g<PR, SX>(D.gin, r, own, R));
     if (tid < 2) {
 #pragma unroll
-        for (int r = 0; r < QG; ++r) cp_async4(sbuf + r * 2 + tid, pulled2_g<PR>(D.gin, r, side, R));
+        for (int r = 0; r < QG; ++r) cp_async4(sbuf + r * 2 + tid, pulled2_g<PR, SX>(D.gin, r, side, R));
     }
     if constexpr (PR) {
         const int self = elem2(R.ys[1] + own.xs[1]);
@@ -170,7 +195,7 @@ __device__ __forceinline__ void stage_row(const DevParams& p, const DirPtrs2& D,
 // one (a thread is at most one iteration ahead: it must pass that
 // iteration's barrier first).  Ends with a barrier, so the caller may reuse
 // shared memory afterwards.
-template <bool PR>
+template <bool PR, bool SX>
 __device__ __forceinline__ void fused2_segment(const DevParams& p, const DirPtrs2& D, float* smem, int x0, int y0,
                                                int y1, float* __restrict__ phiu)
 {
@@ -181,11 +206,17 @@ __device__ __forceinline__ void fused2_segment(const DevParams& p, const DirPtrs
     float* uS = (float*)(phiS + 4 * RW);            // [2][2][TX2] phi u (PR)
     const int tid = threadIdx.x;
     Col2 own, side;
-    set_col2(own, pmod(x0 + tid, p.nx), p.nx);
-    set_col2(side, pmod(tid == 0 ? x0 - 1 : x0 + TX2, p.nx), p.nx);
+    if (SX) {
+        // ghost columns mirror the boundary columns instead of wrapping
+        set_col2_sym(own, reflect_col(x0 + tid, p.nx), p.nx);
+        set_col2_sym(side, reflect_col(tid == 0 ? x0 - 1 : x0 + TX2, p.nx), p.nx);
+    } else {
+        set_col2(own, pmod(x0 + tid, p.nx), p.nx);
+        set_col2(side, pmod(tid == 0 ? x0 - 1 : x0 + TX2, p.nx), p.nx);
+    }
     const bool valid = x0 + tid < p.nx;
-    stage_row<PR>(p, D, own, side, tid, y0 - 1, gS + QG * TX2, sS, phiS, phiu, uS + 2 * TX2);
-    stage_row<PR>(p, D, own, side, tid, y0, gS, sS, phiS + RW, phiu, uS);
+    stage_row<PR, SX>(p, D, own, side, tid, y0 - 1, gS + QG * TX2, sS, phiS, phiu, uS + 2 * TX2);
+    stage_row<PR, SX>(p, D, own, side, tid, y0, gS, sS, phiS + RW, phiu, uS);
     for (int y = y0; y < y1; ++y) {
         const int cur = (y - y0) & 1;
         const int sP = (y - y0) & 3, sC = (y - y0 + 1) & 3, sN = (y - y0 + 2) & 3;
@@ -193,8 +224,8 @@ __device__ __forceinline__ void fused2_segment(const DevParams& p, const DirPtrs
         set_row2(R, p, y);
         float fr[Q2];
 #pragma unroll
-        for (int a = 0; a < Q2; ++a) fr[a] = __ldg(pulled2(D.fin, a, own, R));
-        stage_row<PR>(p, D, own, side, tid, y + 1, gS + (cur ^ 1) * QG * TX2, sS, phiS + sN * RW, phiu,
+        for (int a = 0; a < Q2; ++a) fr[a] = __ldg(pulled2<SX>(D.fin, a, own, R));
+        stage_row<PR, SX>(p, D, own, side, tid, y + 1, gS + (cur ^ 1) * QG * TX2, sS, phiS + sN * RW, phiu,
                       uS + (cur ^ 1) * 2 * TX2);
         FlowMoments m;
         flow_moments<2>(m, fr);
@@ -231,14 +262,14 @@ struct Fused2Args {
     float* phiu;  // reduced phase lattice: stored previous phi u; else null
 };
 
-template <bool PR>
+template <bool PR, bool SX>
 __global__ void __launch_bounds__(TX2, 7) step_fused2_kernel(DevParams p, Fused2Args A, DirPtrs2 D)
 {
     extern __shared__ float smem[];
     for (int item = blockIdx.x; item < A.nitems; item += gridDim.x) {
         const int tile = item % A.tiles_x;
         const int y0 = (item / A.tiles_x) * A.chunk;
-        fused2_segment<PR>(p, D, smem, tile * TX2, y0, min(y0 + A.chunk, p.ny), A.phiu);
+        fused2_segment<PR, SX>(p, D, smem, tile * TX2, y0, min(y0 + A.chunk, p.ny), A.phiu);
     }
 }
 
@@ -294,13 +325,14 @@ __global__ void __launch_bounds__(TX2) step_batch2_kernel(const BatchDomain* __r
         const int local = item - s_begin;
         const int tile = local % s_tx;
         const int y0 = (local / s_tx) * s_chunk;
-        fused2_segment<PR>(sp, sd, smem, tile * TX2, y0, min(y0 + s_chunk, sp.ny), s_phiu);
+        fused2_segment<PR, false>(sp, sd, smem, tile * TX2, y0, min(y0 + s_chunk, sp.ny), s_phiu);
     }
 }
 
-// launch configuration per phase lattice [PR]
-int g_f2_dev[2] = {-1, -1}, g_f2_per_sm[2] = {0, 0}, g_f2_sms[2] = {0, 0}, g_b2_dev[2] = {-1, -1},
-    g_b2_cap[2] = {0, 0};
+// launch configuration per phase lattice and x boundary [PR + 2 SX] of the
+// single-domain kernel, per phase lattice [PR] of the batch kernel
+int g_f2_dev[4] = {-1, -1, -1, -1}, g_f2_per_sm[4] = {0, 0, 0, 0}, g_f2_sms[4] = {0, 0, 0, 0},
+    g_b2_dev[2] = {-1, -1}, g_b2_cap[2] = {0, 0};
 
 cudaError_t setup_kernel(const void* fn, int device, int& dev_cached, int& per_sm_out, int& sms_out)
 {
@@ -324,9 +356,11 @@ int batch2_tile_x() { return TX2; }
 
 cudaError_t launch_step_fused2(lbmp_handle* h)
 {
-    const int k = h->reduced ? 1 : 0;
-    const void* fn = h->reduced ? (const void*)step_fused2_kernel<true> : (const void*)step_fused2_kernel<false>;
-    cudaError_t e = setup_kernel(fn, h->device, g_f2_dev[k], g_f2_per_sm[k], g_f2_sms[k]);
+    const bool sx = h->dp.sym_x != 0;
+    const int k = (h->reduced ? 1 : 0) + (sx ? 2 : 0);
+    const void* fns[4] = {(const void*)step_fused2_kernel<false, false>, (const void*)step_fused2_kernel<true, false>,
+                          (const void*)step_fused2_kernel<false, true>, (const void*)step_fused2_kernel<true, true>};
+    cudaError_t e = setup_kernel(fns[k], h->device, g_f2_dev[k], g_f2_per_sm[k], g_f2_sms[k]);
     if (e != cudaSuccess) return e;
     DirPtrs2 D;
     const int s = h->parity, d = 1 - h->parity;
@@ -343,10 +377,12 @@ cudaError_t launch_step_fused2(lbmp_handle* h)
     A.chunk = L.chunk;
     A.nitems = L.nitems;
     A.phiu = h->phiu;
-    if (h->reduced)
-        step_fused2_kernel<true><<<L.grid, TX2, kSmem2, h->stream>>>(h->dp, A, D);
-    else
-        step_fused2_kernel<false><<<L.grid, TX2, kSmem2, h->stream>>>(h->dp, A, D);
+    switch (k) {
+    case 0: step_fused2_kernel<false, false><<<L.grid, TX2, kSmem2, h->stream>>>(h->dp, A, D); break;
+    case 1: step_fused2_kernel<true, false><<<L.grid, TX2, kSmem2, h->stream>>>(h->dp, A, D); break;
+    case 2: step_fused2_kernel<false, true><<<L.grid, TX2, kSmem2, h->stream>>>(h->dp, A, D); break;
+    default: step_fused2_kernel<true, true><<<L.grid, TX2, kSmem2, h->stream>>>(h->dp, A, D); break;
+    }
     return cudaGetLastError();
 }
 

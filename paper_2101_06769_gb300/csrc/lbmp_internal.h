@@ -141,7 +141,7 @@ cudaError_t launch_step_fused3(lbmp_handle* h);        // FP32 D3Q27, 32 x 4 til
 cudaError_t launch_step_fused3_t16x8(lbmp_handle* h);  // FP32 D3Q27, 16 x 8 tiles
 cudaError_t launch_step_fused3_t8x16(lbmp_handle* h);  // FP32 D3Q27, 8 x 16 tiles
 cudaError_t launch_step_fused3_red(lbmp_handle* h);    // FP32 D3Q27 flow, D3Q7 phase field, 32 x 4 tiles
-cudaError_t launch_init(lbmp_handle* h, int case_id, const double* args, unsigned long long seed);
+cudaError_t launch_init(lbmp_handle* h, int case_id, const double* args, int nargs, unsigned long long seed);
 cudaError_t launch_set_state(lbmp_handle* h, const double* dev_f, const double* dev_g);
 cudaError_t launch_get_state(lbmp_handle* h, double* dev_f, double* dev_g);
 // dev_out: [0..3] mass, kinetic energy, max|u|, non-finite count; [4..5] probe

@@ -232,6 +232,7 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed
 
 struct InitArgs {
     double a[8];
+    int nargs;
     double W, rho_l, rho_h, sigma, U_ref, g;
     unsigned long long seed;
     int case_id;
@@ -305,7 +306,9 @@ __global__ void init_kernel(DevParams p, InitArgs A, float* __restrict__ f, floa
         const double zc = sheet + 0.5 * Dd + 2.0 * A.W;
         double r2 = 0.0;
         for (int k = 0; k < D; ++k) {
-            const double c0 = (k == v) ? zc : (double)(n[k] / 2);
+            // the drop's axis: at n/2, or at the coordinate given (on a
+            // symmetry face, -0.5, for a half domain)
+            const double c0 = (k == v) ? zc : (A.nargs > 4 ? A.a[4] : (double)(n[k] / 2));
             const double dx = pos[k] - c0;
             r2 += dx * dx;
         }
@@ -391,10 +394,11 @@ __global__ void phiu_reset_kernel(DevParams p, Pop<D, StoreF32> f, const float* 
     }
 }
 
-cudaError_t launch_init(lbmp_handle* h, int case_id, const double* args, unsigned long long seed)
+cudaError_t launch_init(lbmp_handle* h, int case_id, const double* args, int nargs, unsigned long long seed)
 {
     InitArgs A;
     for (int k = 0; k < 8; ++k) A.a[k] = args[k];
+    A.nargs = nargs;
     A.W = h->der.W;
     A.rho_l = h->der.rho_l;
     A.rho_h = h->der.rho_h;

@@ -42,6 +42,22 @@ def spreading_radius(phi_xy, sheet_h, axis_x):
     return 0.5 * (radii[0] + radii[1])
 
 
+def spreading_radius_half(phi_xy, sheet_h):
+    """r_K of the half domain of a symmetric impact: phi_xy[y][x] with the
+    drop's axis on the symmetry face x = -1/2 before column 0 (reading A28),
+    film surface at height sheet_h.  Column k's centre lies k + 1/2 from the
+    axis.  Returns NaN before contact."""
+    phi_xy = np.asarray(phi_xy, dtype=np.float64)
+    ny, nx = phi_xy.shape
+    row = phi_xy[int(math.floor(sheet_h)) + 1]
+    if row[0] < 0.5:
+        return float("nan")
+    for k in range(1, nx):
+        if row[k] < 0.5:
+            return (k - 0.5) + (row[k - 1] - 0.5) / (row[k - 1] - row[k])
+    return float("nan")
+
+
 def contact_time(width, U0):
     """Steps from the initial state to the geometric contact of the drop with
     the film: the drop's phi = 1/2 surface starts 2W above the film's."""

@@ -142,3 +142,21 @@ def test_size_flag_and_form_limits_rejected_without_device_work(lib):
         rc = lib.lbmp_create(C.byref(lbmp.Grid(32768, 32768, 1, per2)), lbmp.D2Q9, C.byref(prm), None, C.byref(h))
         assert rc == -6, (rc, lib.lbmp_last_error())
         assert not h.value
+
+
+def test_symmetry_axis_limits_rejected_without_device_work(lib):
+    """A symmetry axis (periodic = 2) is the x axis of a D2Q9 FP32 domain
+    without the divergence term: elsewhere creation fails before any CUDA
+    call (INVALID_ARG for the axis, UNSUPPORTED for the form)."""
+    h = C.c_void_p()
+    ok = dict(rho_ratio=3.0, nu_ratio=1.0, nu_h=0.05)
+    cases = [
+        (lbmp.Grid(8, 8, 8, (C.c_int * 3)(2, 1, 0)), lbmp.D3Q27, lbmp.make_params(**ok), -1),
+        (lbmp.Grid(8, 8, 1, (C.c_int * 3)(1, 2, 1)), lbmp.D2Q9, lbmp.make_params(**ok), -1),
+        (lbmp.Grid(8, 8, 1, (C.c_int * 3)(2, 0, 1)), lbmp.D2Q9, lbmp.make_params(storage=lbmp.FP16_SHIFTED, **ok), -6),
+        (lbmp.Grid(8, 8, 1, (C.c_int * 3)(2, 0, 1)), lbmp.D2Q9, lbmp.make_params(flags=lbmp.FLAG_DIVU, **ok), -6),
+    ]
+    for g, lat, prm, want in cases:
+        rc = lib.lbmp_create(C.byref(g), lat, C.byref(prm), None, C.byref(h))
+        assert rc == want, (rc, lib.lbmp_last_error())
+        assert not h.value

@@ -56,6 +56,19 @@ CASES = {
                    phys=dict(rho_ratio=10.0, nu_ratio=5.0, nu_h=0.02, sigma=5e-3, g_accel=1e-5,
                              mobility=0.03, width=4.0),
                    case="rt", args=[11.0, 3.0, 1e-2, 1.0], seed=8),
+    # half of a symmetric 2-D drop impact: x a symmetry axis (reading A28: half-way
+    # specular reflection, the phi ghost equal to the boundary cell), walls in y,
+    # the drop's axis on the left face; 150 columns, so the second 128-lane
+    # segment is ragged and ends on the right face
+    "sym2d": dict(D=2, dims=(150, 60, 1), periodic=(2, 0, 1),
+                  phys=dict(rho_ratio=100.0, nu_ratio=5.0, We=200.0, Re=200.0, U0=0.05, L_ref=20.0,
+                            mobility=0.05, width=4.0),
+                  case="drop_sheet", args=[20.0, 6.0, 0.05, 1e-3, -0.5], seed=9),
+    # the same on the reduced phase lattice (D2Q5 g)
+    "sym2d_red": dict(D=2, dims=(150, 60, 1), periodic=(2, 0, 1),
+                      phys=dict(rho_ratio=100.0, nu_ratio=5.0, We=200.0, Re=200.0, U0=0.05, L_ref=20.0,
+                                mobility=0.05, width=4.0, flags=8),
+                      case="drop_sheet", args=[20.0, 6.0, 0.05, 1e-3, -0.5], seed=9),
     # thin 3-D with walls: every thread block touches a wall plane
     "thin3d": dict(D=3, dims=(8, 6, 5), periodic=(1, 1, 0),
                    phys=dict(rho_ratio=3.0, nu_ratio=1.0, nu_h=0.05, sigma=1e-2, g_accel=1e-4,
@@ -108,7 +121,7 @@ def test_step_parity_100(name, kernel):
 
 
 @pytest.mark.parametrize("steps", [1, 2, 7])
-@pytest.mark.parametrize("name", ["rt2d", "thin3d", "ragged3d"])
+@pytest.mark.parametrize("name", ["rt2d", "thin3d", "ragged3d", "sym2d"])
 def test_step_parity_odd_even(name, steps):
     c, o, d = make_pair(name)
     o.init(c["case"], c["args"], seed=c["seed"])
@@ -230,7 +243,7 @@ def test_errors_are_reported():
 
 
 @pytest.mark.parametrize("kernel,tile", [(0, 0), (1, 0), (2, 0), (0, 1), (0, 2)])
-@pytest.mark.parametrize("name", ["wide3d", "ragged3d", "thin3d", "ragged2d", "rt2d"])
+@pytest.mark.parametrize("name", ["wide3d", "ragged3d", "thin3d", "ragged2d", "rt2d", "sym2d", "sym2d_red"])
 def test_every_slot_written(name, kernel, tile):
     """Poison (NaN) the population set a step is about to write: after the
     step no NaN is left, so every kernel writes every slot of every cell
@@ -250,7 +263,7 @@ def test_every_slot_written(name, kernel, tile):
     assert d.observables().health == 0
 
 
-@pytest.mark.parametrize("name", ["splash3d", "rt2d", "ragged3d"])
+@pytest.mark.parametrize("name", ["splash3d", "rt2d", "ragged3d", "sym2d"])
 def test_checkpoint_resume_is_bitwise(name):
     """Run N steps, save the state (native bytes through lbmp_download, and
     the exchange format through get_state), restore it into fresh domains and
@@ -278,7 +291,8 @@ def test_checkpoint_resume_is_bitwise(name):
         assert all(np.array_equal(x, y) for x, y in zip(got, want))
 
 
-@pytest.mark.parametrize("name,flags", [("rt3d", 0), ("rt2d", 0), ("ragged3d", 8), ("ragged2d", 8), ("drop2d", 16)])
+@pytest.mark.parametrize("name,flags", [("rt3d", 0), ("rt2d", 0), ("ragged3d", 8), ("ragged2d", 8), ("drop2d", 16),
+                                        ("sym2d", 0), ("sym2d", 8)])
 def test_step_graphs_are_bitwise_plain_steps(name, flags):
     """lbmp_step replays runs of 16 steps from a captured CUDA graph on a
     caller's stream (FP32 storage); the result equals plain launches bitwise,

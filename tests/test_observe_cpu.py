@@ -41,3 +41,14 @@ def test_asymmetric_neck_averages_sides():
 
 def test_contact_time():
     assert observe.contact_time(4.0, 0.05) == 160.0
+
+
+def test_known_neck_radius_half_domain():
+    """The half domain of a symmetric impact: the axis on the face before
+    column 0, so a neck of radius r crosses phi = 1/2 at x = r - 1/2."""
+    for r in (3.0, 7.5, 20.25, 41.0):
+        full = field(400, 60, 20.0, r, 199.5)  # axis on the face between columns 199 and 200
+        half = full[:, 200:]
+        got = observe.spreading_radius_half(half, 20.0)
+        assert abs(got - r) < 0.05, (r, got)
+    assert math.isnan(observe.spreading_radius_half(field(400, 60, 20.0, 5.0, 199.5, drop=False)[:, 200:], 20.0))
