@@ -537,8 +537,8 @@ Cfg16 g_cfg_f16, g_cfg_bf16;
 
 }  // namespace
 
-const Batch3Ops batch3_ops_f16 = {TX, TY, BatchCfg16<StoreF16>::prepare, BatchCfg16<StoreF16>::launch};
-const Batch3Ops batch3_ops_bf16 = {TX, TY, BatchCfg16<StoreBF16>::prepare, BatchCfg16<StoreBF16>::launch};
+const Batch3Ops batch3_ops_f16 = {TX, TY, BatchCfg16<StoreF16>::prepare, BatchCfg16<StoreF16>::launch, nullptr, 0};
+const Batch3Ops batch3_ops_bf16 = {TX, TY, BatchCfg16<StoreBF16>::prepare, BatchCfg16<StoreBF16>::launch, nullptr, 0};
 
 cudaError_t launch_step_fused16(lbmp_handle* h)
 {

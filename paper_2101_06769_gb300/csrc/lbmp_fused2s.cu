@@ -447,8 +447,8 @@ Cfg2s Ops2s<St>::batch_cfg;
 
 }  // namespace
 
-const Batch3Ops batch2_ops_f16 = {TX2, 1, Ops2s<StoreF16>::prepare, Ops2s<StoreF16>::launch};
-const Batch3Ops batch2_ops_bf16 = {TX2, 1, Ops2s<StoreBF16>::prepare, Ops2s<StoreBF16>::launch};
+const Batch3Ops batch2_ops_f16 = {TX2, 1, Ops2s<StoreF16>::prepare, Ops2s<StoreF16>::launch, nullptr, 0};
+const Batch3Ops batch2_ops_bf16 = {TX2, 1, Ops2s<StoreBF16>::prepare, Ops2s<StoreBF16>::launch, nullptr, 0};
 
 cudaError_t launch_step_fused2s(lbmp_handle* h)
 {
