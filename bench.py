@@ -49,11 +49,11 @@ STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 # reported as null once those sources change.
 TRAFFIC = {
     # 128x128x512 rt3d, one launch of step_fused3_kernel: 1891902208 B read + 1768638208 B written
-    ("rt3d", "fp32"): {"bytes_per_cell": 3660540416 / 8388608, "sources": "5294682ba867ca82"},
+    ("rt3d", "fp32"): {"bytes_per_cell": 3660540416 / 8388608, "sources": "b37d9ad5b72f47e6"},
     # same workload, step_fused3s_kernel<StoreF16>: 977621760 B read + 900893952 B written
-    ("rt3d", "fp16"): {"bytes_per_cell": 1878515712 / 8388608, "sources": "5294682ba867ca82"},
+    ("rt3d", "fp16"): {"bytes_per_cell": 1878515712 / 8388608, "sources": "b37d9ad5b72f47e6"},
     # same workload, reduced phase lattice (step_fused3_kernel, D3Q7 g): 1270872320 B read + 1197077760 B written
-    ("rt3d", "reduced"): {"bytes_per_cell": 2467950080 / 8388608, "sources": "5294682ba867ca82"},
+    ("rt3d", "reduced"): {"bytes_per_cell": 2467950080 / 8388608, "sources": "b37d9ad5b72f47e6"},
 }
 TRAFFIC_SOURCES = ["lbmp_common.cuh", "lbmp_tile.cuh", "lbmp_fused3_body.cuh", "lbmp_fused.cu", "lbmp_fused16.cu",
                    "lbmp_fused_r.cu"]
