@@ -134,7 +134,7 @@ typedef struct {
                         kernels address each population array by 32-bit byte offsets) */
     int periodic[3]; /* 1 = periodic; 0 = half-way bounce-back walls (vertical axis only);
                         2 = symmetry axis (x of a D2Q9 FP32 domain only; not with
-                        LBMP_FLAG_DIVU, not a batch member): half-way specular reflection
+                        LBMP_FLAG_DIVU): half-way specular reflection
                         at both faces, the phi ghost equal to the boundary cell -- the
                         symmetry boundary of the 2-D splash, Sec. 3.4 */
 } lbmp_grid;

@@ -12,8 +12,8 @@
 // both phases (even or odd number of steps since the capture) and the batch
 // replays the one of its current phase.  Members are grouped by kind --
 // FP32, FP16 and BF16 (shifted storage) D3Q27, FP32 D3Q27 with the reduced
-// phase lattice, then FP32, FP16 and BF16 D2Q9 and FP32 D2Q9 with the
-// reduced phase lattice --
+// phase lattice, then FP32, FP16 and BF16 D2Q9, FP32 D2Q9 with the reduced
+// phase lattice, and FP32 D2Q9 with a symmetry x axis on either lattice --
 // each kind a contiguous segment of the table with its own work numbering
 // and its own persistent kernel.  Within a step the D3Q27 kernels run on the
 // batch stream and the D2Q9 kernels on a forked second stream, joined before
@@ -46,14 +46,17 @@ enum Kind {
     kF32x2 = 4,
     kF16x2 = 5,
     kBF16x2 = 6,
-    kF32x2R = 7,  // FP32 D2Q9 flow, D2Q5 phase field
-    kKinds = 8
+    kF32x2R = 7,   // FP32 D2Q9 flow, D2Q5 phase field
+    kF32x2S = 8,   // FP32 D2Q9 with a symmetry x axis
+    kF32x2RS = 9,  // the same with the D2Q5 phase field
+    kKinds = 10
 };
 constexpr int kLast3 = kF32x3R;  // the D3Q27 kinds are kF32x3 .. kLast3
 
 int kind_of(const lbmp_handle* h)
 {
     const int st = h->params.storage;
+    if (h->D == 2 && h->dp.sym_x) return h->reduced ? kF32x2RS : kF32x2S;
     if (h->D == 2 && h->reduced) return kF32x2R;
     if (h->D == 2) return st == LBMP_FP16_SHIFTED ? kF16x2 : (st == LBMP_BF16_SHIFTED ? kBF16x2 : kF32x2);
     if (h->reduced) return kF32x3R;
@@ -136,7 +139,8 @@ cudaError_t step_kernels(lbmp_batch* b, int flip)
     cudaError_t e = cudaSuccess;
     bool any3 = false;
     for (int k = kF32x3; k <= kLast3; ++k) any3 = any3 || b->ndom[k];
-    const bool any2 = b->ndom[kF32x2] || b->ndom[kF16x2] || b->ndom[kBF16x2] || b->ndom[kF32x2R];
+    bool any2 = false;
+    for (int k = kF32x2; k < kKinds; ++k) any2 = any2 || b->ndom[k];
     const bool fork = any3 && any2;
     if (fork) {
         e = cudaEventRecord(b->fork, b->stream);
@@ -144,12 +148,12 @@ cudaError_t step_kernels(lbmp_batch* b, int flip)
     }
     for (int k = kF32x3; k <= kLast3 && e == cudaSuccess; ++k)
         if (b->ndom[k]) e = launch3(b, k, flip, b->stream);
-    if (e == cudaSuccess && b->ndom[kF32x2])
-        e = lbmp::launch_batch2(b->d_table + b->dom0[kF32x2], b->ndom[kF32x2], b->nitems[kF32x2], b->device,
-                                fork ? b->side : b->stream, false);
-    if (e == cudaSuccess && b->ndom[kF32x2R])
-        e = lbmp::launch_batch2(b->d_table + b->dom0[kF32x2R], b->ndom[kF32x2R], b->nitems[kF32x2R], b->device,
-                                fork ? b->side : b->stream, true);
+    // FP32 D2Q9 kinds: phase lattice and x boundary as template parameters
+    static const int k2[4] = {kF32x2, kF32x2R, kF32x2S, kF32x2RS};
+    for (int j = 0; j < 4 && e == cudaSuccess; ++j)
+        if (b->ndom[k2[j]])
+            e = lbmp::launch_batch2(b->d_table + b->dom0[k2[j]], b->ndom[k2[j]], b->nitems[k2[j]], b->device,
+                                    fork ? b->side : b->stream, (j & 1) != 0, j >= 2);
     for (int k = kF16x2; k <= kBF16x2 && e == cudaSuccess; ++k)
         if (b->ndom[k])
             e = ops3_of(b, k).launch(b->d_table + b->dom0[k], b->ndom[k], b->nitems[k], b->device,
@@ -187,7 +191,8 @@ cudaError_t rebuild(lbmp_batch* b, bool graphs = true)
     b->dom0[kind] = (int)b->h_table.size();
     const int D = kind >= kF32x2 ? 2 : 3;
     int item = 0;
-    const int TX = (kind == kF32x2 || kind == kF32x2R) ? lbmp::batch2_tile_x() : ops3_of(b, kind).tile_x;
+    const bool fp32_2d = kind == kF32x2 || kind == kF32x2R || kind == kF32x2S || kind == kF32x2RS;
+    const int TX = fp32_2d ? lbmp::batch2_tile_x() : ops3_of(b, kind).tile_x;
     const int TY = D == 3 ? ops3_of(b, kind).tile_y : 1;
     const int chunk = b->chunk > 0 ? b->chunk : 16;
     for (const Member& m : b->members) {
@@ -222,8 +227,10 @@ cudaError_t rebuild(lbmp_batch* b, bool graphs = true)
     if (ndom > 0) {
         for (int k = kF32x3; k <= kLast3 && e == cudaSuccess; ++k)
             if (b->ndom[k]) e = ops3_of(b, k).prepare(b->device);
-        if (e == cudaSuccess && b->ndom[kF32x2]) e = lbmp::prepare_batch2(b->device, false);
-        if (e == cudaSuccess && b->ndom[kF32x2R]) e = lbmp::prepare_batch2(b->device, true);
+        if (e == cudaSuccess && b->ndom[kF32x2]) e = lbmp::prepare_batch2(b->device, false, false);
+        if (e == cudaSuccess && b->ndom[kF32x2R]) e = lbmp::prepare_batch2(b->device, true, false);
+        if (e == cudaSuccess && b->ndom[kF32x2S]) e = lbmp::prepare_batch2(b->device, false, true);
+        if (e == cudaSuccess && b->ndom[kF32x2RS]) e = lbmp::prepare_batch2(b->device, true, true);
         for (int k = kF16x2; k <= kBF16x2 && e == cudaSuccess; ++k)
             if (b->ndom[k]) e = ops3_of(b, k).prepare(b->device);
         if (e == cudaSuccess)
@@ -313,7 +320,6 @@ LBMP_API int lbmp_batch_add(lbmp_batch* b, lbmp_handle* h, long steps)
     if ((int)b->members.size() >= kMaxMembers) return batch_fail(LBMP_ERR_INVALID_ARG, "batch is full");
     if (h->divu) return batch_fail(LBMP_ERR_UNSUPPORTED, "divergence-term domains are not batch members");
     if (h->slab || h->aa) return batch_fail(LBMP_ERR_UNSUPPORTED, "z-slabs and in-place AA domains are not batch members");
-    if (h->dp.sym_x) return batch_fail(LBMP_ERR_UNSUPPORTED, "domains with a symmetry axis are not batch members");
     size_t used = 0;
     for (const Member& m : b->members) {
         if (m.h == h) return batch_fail(LBMP_ERR_INVALID_ARG, "domain is already a member");

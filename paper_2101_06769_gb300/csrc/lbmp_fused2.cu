@@ -195,7 +195,9 @@ __device__ __forceinline__ void stage_row(const DevParams& p, const DirPtrs2& D,
 // one (a thread is at most one iteration ahead: it must pass that
 // iteration's barrier first).  Ends with a barrier, so the caller may reuse
 // shared memory afterwards.
-template <bool PR, bool SX>
+// SXM: kSymOff (periodic x) or kSymOn (x a symmetry axis)
+constexpr int kSymOff = 0, kSymOn = 1;
+template <bool PR, int SXM>
 __device__ __forceinline__ void fused2_segment(const DevParams& p, const DirPtrs2& D, float* smem, int x0, int y0,
                                                int y1, float* __restrict__ phiu)
 {
@@ -206,7 +208,8 @@ __device__ __forceinline__ void fused2_segment(const DevParams& p, const DirPtrs
     float* uS = (float*)(phiS + 4 * RW);            // [2][2][TX2] phi u (PR)
     const int tid = threadIdx.x;
     Col2 own, side;
-    if (SX) {
+    constexpr bool SX = SXM != kSymOff;
+    if (SXM == kSymOn) {
         // ghost columns mirror the boundary columns instead of wrapping
         set_col2_sym(own, reflect_col(x0 + tid, p.nx), p.nx);
         set_col2_sym(side, reflect_col(tid == 0 ? x0 - 1 : x0 + TX2, p.nx), p.nx);
@@ -269,11 +272,11 @@ __global__ void __launch_bounds__(TX2, 7) step_fused2_kernel(DevParams p, Fused2
     for (int item = blockIdx.x; item < A.nitems; item += gridDim.x) {
         const int tile = item % A.tiles_x;
         const int y0 = (item / A.tiles_x) * A.chunk;
-        fused2_segment<PR, SX>(p, D, smem, tile * TX2, y0, min(y0 + A.chunk, p.ny), A.phiu);
+        fused2_segment<PR, SX ? kSymOn : kSymOff>(p, D, smem, tile * TX2, y0, min(y0 + A.chunk, p.ny), A.phiu);
     }
 }
 
-template <bool PR>
+template <bool PR, bool SX>
 __global__ void __launch_bounds__(TX2) step_batch2_kernel(const BatchDomain* __restrict__ table, int ndom,
                                                           int nitems)
 {
@@ -325,14 +328,14 @@ __global__ void __launch_bounds__(TX2) step_batch2_kernel(const BatchDomain* __r
         const int local = item - s_begin;
         const int tile = local % s_tx;
         const int y0 = (local / s_tx) * s_chunk;
-        fused2_segment<PR, false>(sp, sd, smem, tile * TX2, y0, min(y0 + s_chunk, sp.ny), s_phiu);
+        fused2_segment<PR, SX ? kSymOn : kSymOff>(sp, sd, smem, tile * TX2, y0, min(y0 + s_chunk, sp.ny), s_phiu);
     }
 }
 
 // launch configuration per phase lattice and x boundary [PR + 2 SX] of the
-// single-domain kernel, per phase lattice [PR] of the batch kernel
+// single-domain and of the batch kernel
 int g_f2_dev[4] = {-1, -1, -1, -1}, g_f2_per_sm[4] = {0, 0, 0, 0}, g_f2_sms[4] = {0, 0, 0, 0},
-    g_b2_dev[2] = {-1, -1}, g_b2_cap[2] = {0, 0};
+    g_b2_dev[4] = {-1, -1, -1, -1}, g_b2_cap[4] = {0, 0, 0, 0};
 
 cudaError_t setup_kernel(const void* fn, int device, int& dev_cached, int& per_sm_out, int& sms_out)
 {
@@ -386,12 +389,13 @@ cudaError_t launch_step_fused2(lbmp_handle* h)
     return cudaGetLastError();
 }
 
-cudaError_t prepare_batch2(int device, bool reduced)
+cudaError_t prepare_batch2(int device, bool reduced, bool sym)
 {
-    const int k = reduced ? 1 : 0;
-    const void* fn = reduced ? (const void*)step_batch2_kernel<true> : (const void*)step_batch2_kernel<false>;
+    const int k = (reduced ? 1 : 0) + (sym ? 2 : 0);
+    const void* fns[4] = {(const void*)step_batch2_kernel<false, false>, (const void*)step_batch2_kernel<true, false>,
+                          (const void*)step_batch2_kernel<false, true>, (const void*)step_batch2_kernel<true, true>};
     int per_sm = 0, sms = 0, dev = g_b2_dev[k];
-    cudaError_t e = setup_kernel(fn, device, dev, per_sm, sms);
+    cudaError_t e = setup_kernel(fns[k], device, dev, per_sm, sms);
     if (e == cudaSuccess && g_b2_dev[k] != device) {
         g_b2_cap[k] = per_sm * sms;
         g_b2_dev[k] = device;
@@ -400,16 +404,18 @@ cudaError_t prepare_batch2(int device, bool reduced)
 }
 
 cudaError_t launch_batch2(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream,
-                          bool reduced)
+                          bool reduced, bool sym)
 {
-    const int k = reduced ? 1 : 0;
+    const int k = (reduced ? 1 : 0) + (sym ? 2 : 0);
     if (g_b2_dev[k] != device) return cudaErrorNotReady;  // prepare_batch2 first
     if (nitems <= 0) return cudaSuccess;
     const int grid = nitems < g_b2_cap[k] ? nitems : g_b2_cap[k];
-    if (reduced)
-        step_batch2_kernel<true><<<grid, TX2, kSmem2, stream>>>(table, ndom, nitems);
-    else
-        step_batch2_kernel<false><<<grid, TX2, kSmem2, stream>>>(table, ndom, nitems);
+    switch (k) {
+    case 0: step_batch2_kernel<false, false><<<grid, TX2, kSmem2, stream>>>(table, ndom, nitems); break;
+    case 1: step_batch2_kernel<true, false><<<grid, TX2, kSmem2, stream>>>(table, ndom, nitems); break;
+    case 2: step_batch2_kernel<false, true><<<grid, TX2, kSmem2, stream>>>(table, ndom, nitems); break;
+    default: step_batch2_kernel<true, true><<<grid, TX2, kSmem2, stream>>>(table, ndom, nitems); break;
+    }
     return cudaGetLastError();
 }
 

@@ -187,9 +187,9 @@ cudaError_t launch_step_fused_bulk(lbmp_handle* h);
 // the step kernel(s) selected by LBMP_OPT_KERNEL for this handle (no parity flip)
 cudaError_t launch_step(lbmp_handle* h);
 int batch2_tile_x();
-cudaError_t prepare_batch2(int device, bool reduced);  // reduced: the D2Q5 phase-field members
+cudaError_t prepare_batch2(int device, bool reduced, bool sym);  // reduced: D2Q5 phase field; sym: x symmetry axis
 cudaError_t launch_batch2(const BatchDomain* table, int ndom, int nitems, int device, cudaStream_t stream,
-                          bool reduced);
+                          bool reduced, bool sym);
 cudaError_t launch_batch_epilogue(BatchDomain* table, int ndom, cudaStream_t stream);
 // record a message for lbmp_last_error() and return code
 int set_error(int code, const char* msg);

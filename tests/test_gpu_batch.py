@@ -277,3 +277,35 @@ def test_batch_writes_every_slot():
         f, g, phi = d.get_state()
         assert np.isfinite(f).all() and np.isfinite(g).all() and np.isfinite(phi).all()
     b.close()
+
+
+def test_batch_with_symmetry_axis_members_is_bitwise_stepping_alone():
+    """D2Q9 members with a symmetry x axis (reading A28), on both phase
+    lattices, next to periodic ones: the batch kernel takes each member's
+    boundary from its parameters, and every member equals its run alone
+    bitwise."""
+    from test_gpu_parity import CASES as P
+    names = ["sym2d", "sym2d_red", "rt2d", "ragged2d"]
+    steps = [23, 17, 30, 9]
+
+    def mk(name):
+        c = P[name]
+        d = Domain(c["D"], c["dims"], c["periodic"], **c["phys"])
+        d.init(c["case"], c["args"], seed=c["seed"])
+        return d
+
+    alone = []
+    for name, n in zip(names, steps):
+        d = mk(name)
+        d.step(n)
+        alone.append(d.get_state())
+        d.close()
+    b = Batch()
+    doms = [mk(name) for name in names]
+    for d, n in zip(doms, steps):
+        b.add(d, n)
+    b.step(5)
+    b.step(30)
+    for d, ref in zip(doms, alone):
+        assert all(np.array_equal(x, y) for x, y in zip(d.get_state(), ref))
+    b.close()
