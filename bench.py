@@ -282,11 +282,64 @@ BATCH_MIX_DESC = ("6x64^3, 4x96^3, 2x128^3 D3Q27 + 4x128^2, 4x256^2, 2x512^2 D2Q
                   "(sizes of the serving stream)")
 
 
+def measure_batched(args, stream, peak, pg, n):
+    """The batched form: one batch of the serving-size mix (BATCH_MIX), tuned
+    and advanced by 16-step graph replays, next to the same members stepped
+    one launch each.  Returns its record and the kernel launches it made."""
+    from paper_2101_06769_gb300 import Batch, Domain
+    doms, cells, byts, launches = [], 0, 0, 0
+    b = Batch(stream=stream.cuda_stream)
+    for k, (Dm, dims) in enumerate(BATCH_MIX):
+        L = float(dims[0])
+        per = (1, 1, 0) if Dm == 3 else (1, 0, 1)
+        d = Domain(Dm, dims, per, stream=stream.cuda_stream, atwood=0.5, nu_ratio=1.0, Re=1024.0,
+                   g_accel=0.04 ** 2 / L, L_ref=L, mobility=0.02, width=5.0)
+        d.init("rt", [dims[Dm - 1] / 2.0, 0.1 * L, 1e-4, 1.0], seed=100 + k)
+        b.add(d, 10 ** 6)
+        doms.append(d)
+        cells += d.N
+        byts += BYTES_PER_CELL[Dm] * d.N
+    if not args.no_autotune:
+        b.autotune(reps=2)  # tile shape and planes per item of the batch kernels
+    b.step(16)  # rebuild, capture and warm the graphs
+    nb = 4 * max(1, n // 16)  # graph replays of 16 steps
+    ms16 = time_steps(lambda: b.step(16), stream, nb)
+    ms = ms16 / 16
+    launches += nb * 16 * 3  # per step: 3-D batch kernel, 2-D batch kernel, epilogue
+    _, mlups = aggregate(ms * nb * 16, cells, nb * 16, pg)
+    gbs = byts / (ms * 1e-3) / 1e9
+    res = {"mlups": mlups, "ms_per_step": ms, "members": len(doms), "cells": cells, "bytes_per_step": byts,
+           "achieved_gbs": gbs, "frac": gbs / peak, "mix": BATCH_MIX_DESC, "steps": nb * 16}
+    for d in doms:
+        b.remove(d)
+    b.close()
+    # the same members stepped one domain at a time (one launch per member and
+    # step, each with its own tuned launch shape): the plain one-domain form
+    for d in doms:
+        if not args.no_autotune:
+            d.autotune(reps=2, cache=False)
+    na = max(4, n // 4)
+
+    def alone_round():
+        for d in doms:
+            d.step(1)
+
+    ms_alone = time_steps(alone_round, stream, na)
+    launches += na * len(doms)
+    _, mlups_alone = aggregate(ms_alone * na, cells, na, pg)
+    res["alone_mlups"] = mlups_alone
+    res["alone_ms_per_step"] = ms_alone
+    res["speedup_vs_alone"] = mlups / mlups_alone
+    for d in doms:
+        d.close()
+    return res, launches
+
+
 def measure_forms(args, wl, stream, peak, pg):
     """The other forms of the step on the same device: the workload with
     FP16 and BF16 shifted storage (fused kernel), and a batch of uneven
     domains advanced by the persistent batch kernels and CUDA graphs."""
-    from paper_2101_06769_gb300 import Batch, Domain
+    from paper_2101_06769_gb300 import Domain
     D = wl["D"]
     out, launches = {}, 0
     n = max(3, args.form_steps)
@@ -354,53 +407,9 @@ def measure_forms(args, wl, stream, peak, pg):
                               "kernel": "phi_pass_kernel + step_aa_kernel"}
         d.close()
     # batched form
-    doms, cells, byts = [], 0, 0
-    b = Batch(stream=stream.cuda_stream)
-    for k, (Dm, dims) in enumerate(BATCH_MIX):
-        L = float(dims[0])
-        per = (1, 1, 0) if Dm == 3 else (1, 0, 1)
-        d = Domain(Dm, dims, per, stream=stream.cuda_stream, atwood=0.5, nu_ratio=1.0, Re=1024.0,
-                   g_accel=0.04 ** 2 / L, L_ref=L, mobility=0.02, width=5.0)
-        d.init("rt", [dims[Dm - 1] / 2.0, 0.1 * L, 1e-4, 1.0], seed=100 + k)
-        b.add(d, 10 ** 6)
-        doms.append(d)
-        cells += d.N
-        byts += BYTES_PER_CELL[Dm] * d.N
-    if not args.no_autotune:
-        b.autotune(reps=2)  # tile shape and planes per item of the batch kernels
-    b.step(16)  # rebuild, capture and warm the graphs
-    nb = 4 * max(1, n // 16)  # graph replays of 16 steps
-    ms16 = time_steps(lambda: b.step(16), stream, nb)
-    ms = ms16 / 16
-    launches += nb * 16 * 3  # per step: 3-D batch kernel, 2-D batch kernel, epilogue
-    _, mlups = aggregate(ms * nb * 16, cells, nb * 16, pg)
-    gbs = byts / (ms * 1e-3) / 1e9
-    out["batched"] = {"mlups": mlups, "ms_per_step": ms, "members": len(doms), "cells": cells,
-                      "bytes_per_step": byts, "achieved_gbs": gbs, "frac": gbs / peak,
-                      "mix": BATCH_MIX_DESC,
-                      "steps": nb * 16}
-    for d in doms:
-        b.remove(d)
-    b.close()
-    # the same members stepped one domain at a time (one launch per member and
-    # step, each with its own tuned launch shape): the plain one-domain form
-    for d in doms:
-        if not args.no_autotune:
-            d.autotune(reps=2, cache=False)
-    na = max(4, n // 4)
-
-    def alone_round():
-        for d in doms:
-            d.step(1)
-
-    ms_alone = time_steps(alone_round, stream, na)
-    launches += na * len(doms)
-    _, mlups_alone = aggregate(ms_alone * na, cells, na, pg)
-    out["batched"]["alone_mlups"] = mlups_alone
-    out["batched"]["alone_ms_per_step"] = ms_alone
-    out["batched"]["speedup_vs_alone"] = mlups / mlups_alone
-    for d in doms:
-        d.close()
+    out["batched"], lb = measure_batched(args, stream, peak, pg, n)
+    launches += lb
+    mlups = out["batched"]["mlups"]
     out["serving"] = measure_serving(stream, mlups)
     # the same stream under a cap on the resident state: FP32 against 16-bit
     # storage of the D3Q27 requests (224 instead of 432 B/cell: more requests
@@ -543,6 +552,8 @@ def main():
     ap.add_argument("--phase", default="full", choices=["full", "reduced"],
                     help="phase-field lattice: the flow lattice, or D3Q7 / D2Q5 (FP32 only)")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16/batched form measurements")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="measure the batched form alone (one JSON line), for profiling it")
     ap.add_argument("--form-steps", type=int, default=50)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--configs", action="store_true",
@@ -569,6 +580,11 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("no CUDA device: the benchmark measures the GPU path only")
     torch.cuda.set_device(local)
+    if args.batched_only:
+        peak, _ = load_peaks()
+        res, _ = measure_batched(args, torch.cuda.Stream(), peak, None, max(3, args.form_steps))
+        print(json.dumps(dict(res, form="batched")), flush=True)
+        return 0
     pg = None
     if ws > 1:
         import torch.distributed as dist
