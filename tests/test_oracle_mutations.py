@@ -63,6 +63,9 @@ MUTATIONS = {
                                  "test_oracle_symmetry.py::test_half_domain_equals_half_of_the_symmetric_full_domain"),
     "symmetry_ghost_wraps": ("    if (periodic == 1) return ((y % n) + n) % n;", "    if (periodic) return ((y % n) + n) % n;",
                              "test_oracle_symmetry.py::test_half_domain_equals_half_of_the_symmetric_full_domain"),
+    "drop_axis_ignored": ("double c0 = (k == v) ? zc : (nargs > 4 ? A[4] : (double)(s->n[k] / 2));",
+                          "double c0 = (k == v) ? zc : (double)(s->n[k] / 2);",
+                          "test_oracle_symmetry.py::test_half_domain_equals_half_of_the_symmetric_full_domain"),
     # observables and initial states
     "kinetic_energy_half": ("ke_c[i] = 0.5 * m.rho * uu;", "ke_c[i] = m.rho * uu;",
                             "test_oracle_observables.py::test_kinetic_energy_closed_forms"),
