@@ -69,6 +69,12 @@ CASES = {
                       phys=dict(rho_ratio=100.0, nu_ratio=5.0, We=200.0, Re=200.0, U0=0.05, L_ref=20.0,
                                 mobility=0.05, width=4.0, flags=8),
                       case="drop_sheet", args=[20.0, 6.0, 0.05, 1e-3, -0.5], seed=9),
+    # a narrow symmetric domain: 37 columns in one 128-lane segment, so most
+    # lanes lie beyond the right face and take the mirrored (clamped) columns
+    "sym2d_narrow": dict(D=2, dims=(37, 41, 1), periodic=(2, 0, 1),
+                         phys=dict(rho_ratio=10.0, nu_ratio=5.0, nu_h=0.02, sigma=5e-3, g_accel=1e-5,
+                                   mobility=0.03, width=4.0),
+                         case="rt", args=[20.0, 3.0, 1e-2, 1.0], seed=10),
     # thin 3-D with walls: every thread block touches a wall plane
     "thin3d": dict(D=3, dims=(8, 6, 5), periodic=(1, 1, 0),
                    phys=dict(rho_ratio=3.0, nu_ratio=1.0, nu_h=0.05, sigma=1e-2, g_accel=1e-4,
@@ -243,7 +249,7 @@ def test_errors_are_reported():
 
 
 @pytest.mark.parametrize("kernel,tile", [(0, 0), (1, 0), (2, 0), (0, 1), (0, 2)])
-@pytest.mark.parametrize("name", ["wide3d", "ragged3d", "thin3d", "ragged2d", "rt2d", "sym2d", "sym2d_red"])
+@pytest.mark.parametrize("name", ["wide3d", "ragged3d", "thin3d", "ragged2d", "rt2d", "sym2d", "sym2d_red", "sym2d_narrow"])
 def test_every_slot_written(name, kernel, tile):
     """Poison (NaN) the population set a step is about to write: after the
     step no NaN is left, so every kernel writes every slot of every cell
