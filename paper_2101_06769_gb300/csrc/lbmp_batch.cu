@@ -123,6 +123,7 @@ cudaError_t launch3(lbmp_batch* b, int kind, int flip, cudaStream_t stream)
     const lbmp::Batch3Ops& ops = ops3_of(b, kind);
     const int d0 = b->dom0[kind], n = b->ndom[kind];
     if (!ops.launch_grid) return ops.launch(b->d_table + d0, n, b->nitems[kind], b->device, stream);
+    if (ops.grid_members <= 0) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < n && e == cudaSuccess; k += ops.grid_members) {
         const int m = n - k < ops.grid_members ? n - k : ops.grid_members;
